@@ -1,0 +1,192 @@
+/*
+ * igg.h - C ABI of the GB300 (sm_103a) implementation of the heat-diffusion
+ * hot path of "Distributed Parallelization of xPU Stencil Computations in
+ * Julia" (Omlin, Raess, Utkin; arXiv 2211.15716):
+ *   - the implicit global grid of subdomains (Sec. Approach; Fig. 1
+ *     init_global_grid, nx_g/ny_g/nz_g, finalize_global_grid),
+ *   - the halo update that keeps it consistent (update_halo!),
+ *   - the explicit 7-point diffusion step (Fig. 1 step!),
+ *   - the boundary/inner split that hides the halo update behind the
+ *     inner-block computation (Fig. 1 @hide_communication (16, 2, 2);
+ *     Sec. Approach: transfers on high-priority streams),
+ *   - and three reshaped forms of the step: reduced-precision storage,
+ *     batches of independent uneven problems, and the adjoint step.
+ *
+ * On one GPU the process topology is virtual: all nsub subdomains live in
+ * one device's memory and a field is ONE contiguous device buffer laid out
+ * [nsub][nz][ny][nx] (x fastest; subdomain number x fastest over dims).
+ * The linear index of local point (ix, iy, iz) of subdomain s is
+ *   ix + nx*(iy + ny*(iz + nz*s)),  0-based.
+ *
+ * Conventions for every function:
+ *   - Return value: IGG_OK (0) or a negative error code; igg_last_error()
+ *     gives a message for the calling thread. No function aborts or traps.
+ *   - Field pointers are DEVICE pointers on the grid's device, owned by the
+ *     caller, 16-byte aligned, holding nsub*nx*ny*nz elements of the dtype.
+ *     Misaligned or NULL pointers give IGG_EINVAL.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All device work of a call is ordered after the work already
+ *     queued on `stream`, and work queued on `stream` afterwards is ordered
+ *     after it; calls return without synchronising unless stated.
+ *   - The library owns its handles, descriptor tables, streams, events and
+ *     CUDA graphs, and frees them in the matching finalize/destroy call.
+ */
+#ifndef IGG_H
+#define IGG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IGG_ABI_VERSION 1
+
+/* status codes */
+#define IGG_OK 0
+#define IGG_EINVAL (-1) /* invalid argument (sizes, overlap, widths, dims, pointers) */
+#define IGG_ECUDA (-2)  /* a CUDA runtime call failed; message has the CUDA error text */
+#define IGG_ENOMEM (-3) /* device or host allocation failed */
+#define IGG_ESTATE (-4) /* handle used in a wrong state */
+
+/* element types of the fields (Fig. 1's @init_parallel_stencil(CUDA,
+ * Float64, 3) picks FP64; FP32 and BF16 storage are the reduced-precision
+ * forms). F64 computes in FP64, F32 in FP32, BF16 loads BF16, computes in
+ * FP32 and rounds the result to BF16 (nearest-even). */
+typedef enum { IGG_F64 = 0, IGG_F32 = 1, IGG_BF16 = 2 } igg_dtype;
+
+typedef struct igg_grid igg_grid;
+typedef struct igg_batch igg_batch;
+
+/* Message of the last failing call on this thread ("" if none). The pointer
+ * stays valid until the next call on this thread. */
+const char *igg_last_error(void);
+
+/* IGG_ABI_VERSION of the library. */
+int igg_abi_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Implicit global grid (Sec. Approach; Fig. 1 init_global_grid).
+ *
+ * Creates a virtual Cartesian topology of subdomains, each a local array of
+ * nx*ny*nz points, on the CURRENT CUDA device.
+ *   dims[3]    : subdomains per dimension; entries equal to 0 are chosen so
+ *                that dims[0]*dims[1]*dims[2] == nsub, as balanced as
+ *                possible and non-increasing over the free entries
+ *                (MPI_Dims_create's rule). NULL = all free.
+ *   nsub       : number of subdomains (used when dims has zeros; must equal
+ *                the product otherwise).
+ *   overlap[3] : planes shared by neighbouring subdomains, >= 2 (halo width
+ *                1). NULL = (2, 2, 2).
+ *   periods[3] : nonzero = periodic dimension. NULL = none.
+ * Global size per dimension: n_g = dims*(n - o) + o, or dims*(n - o) when
+ * periodic. Requires n >= 3 and 2 <= o <= n - 1 per dimension, so that both
+ * send planes (indices o-1 and n-o) are inner points.
+ * Creates the library's high- and low-priority streams and events.
+ * On success *out owns the grid; release it with igg_finalize_global_grid.
+ * ------------------------------------------------------------------------- */
+int igg_init_global_grid(int nx, int ny, int nz, const int dims[3], int nsub,
+                         const int overlap[3], const int periods[3],
+                         igg_grid **out);
+
+/* Fig. 1 finalize_global_grid: frees every resource of the grid. NULL is
+ * accepted. The caller must not use the handle afterwards. Waits for the
+ * grid's outstanding work before freeing. */
+int igg_finalize_global_grid(igg_grid *grid);
+
+/* Fig. 1 nx_g(), ny_g(), nz_g(): the global grid size. */
+int igg_global_size(const igg_grid *grid, int n_g[3]);
+
+/* Local size, dims, overlap, periods and subdomain count of the grid (any
+ * output pointer may be NULL). */
+int igg_grid_shape(const igg_grid *grid, int n[3], int dims[3], int overlap[3],
+                   int periods[3], int *nsub);
+
+/* Subdomain `sub`: its Cartesian coordinates (x fastest numbering), its
+ * left/right neighbours per dimension (-1 at a physical boundary) and the
+ * global index of its local point 0 per dimension (coords*(n - o); the
+ * global index of local point i is offset + i, modulo n_g when periodic).
+ * Any output pointer may be NULL. */
+int igg_subdomain_info(const igg_grid *grid, int sub, int coords[3],
+                       int left[3], int right[3], int offset[3]);
+
+/* ---------------------------------------------------------------------------
+ * Halo update (update_halo!, Sec. Approach; Fig. 1 update_halo!(T2)).
+ *
+ * For each of the nfields fields (device pointers of `dtype`, layout above)
+ * and for the dimensions in the order x, y, z: every subdomain's first
+ * plane (index 0) receives plane n-o of its left neighbour, and its last
+ * plane (index n-1) receives plane o-1 of its right neighbour. Whole planes
+ * are copied, including points in other dimensions' halos, so edges and
+ * corners end up exactly as after the sequential x, y, z exchange. The copy
+ * is bit exact. Work is ordered on `stream` (the library's high-priority
+ * stream runs it and `stream` waits for it).
+ * ------------------------------------------------------------------------- */
+int igg_update_halo(igg_grid *grid, void *const fields[], int nfields,
+                    igg_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Diffusion step (Fig. 1 step!) on every subdomain:
+ *   T2 = T + dt*(lam*Ci*(d2x/dx^2 + d2y/dy^2 + d2z/dz^2))
+ * on every inner point (local index 1..n-2 in each dimension), where d2x is
+ * the second difference T[x+1] - 2 T[x] + T[x-1]. Points on a subdomain's
+ * array boundary are NOT written (Fig. 1's T2 = copy(T) makes them fixed).
+ * T2 must not alias T or Ci. No halo update is done.
+ * The arithmetic is the same in every kernel of the library (full step,
+ * boundary slabs, inner block, batched form), so all of them produce
+ * identical bits for the same point.
+ * ------------------------------------------------------------------------- */
+int igg_step(igg_grid *grid, void *T2, const void *T, const void *Ci,
+             igg_dtype dtype, double lam, double dt, double dx, double dy,
+             double dz, void *stream);
+
+/* Fig. 1 @hide_communication widths begin step!(T2,T,...); update_halo!(T2)
+ * end: the step on the boundary set of every subdomain (inner points whose
+ * 1-based index i has i <= w or i >= n - w + 1 in some dimension, w =
+ * widths[d]) runs first on the library's high-priority stream, followed
+ * there by the halo update of T2; the inner block runs concurrently on the
+ * low-priority stream; `stream` waits for both. Requires widths[d] >=
+ * overlap[d] (so all sent planes are in the boundary set). The result is
+ * bit-identical to igg_step followed by igg_update_halo(T2). */
+int igg_step_hidden(igg_grid *grid, const int widths[3], void *T2,
+                    const void *T, const void *Ci, igg_dtype dtype, double lam,
+                    double dt, double dx, double dy, double dz, void *stream);
+
+/* Fig. 1's time loop: nt times { step (hidden when widths != NULL, else
+ * plain step then halo update) of T2 from T; swap T and T2 }. The loop is
+ * captured once into a CUDA graph (two steps per graph launch) and cached
+ * on the grid for the same pointers, dtype, widths and coefficients.
+ * T2 must hold a copy of T's boundary values on entry (Fig. 1 T2 =
+ * copy(T)). After the call the newest state is in T when nt is even and in
+ * T2 when nt is odd (the buffers swap roles every step, as in Fig. 1). */
+int igg_run(igg_grid *grid, int nt, const int widths[3], void *T, void *T2,
+            const void *Ci, igg_dtype dtype, double lam, double dt, double dx,
+            double dy, double dz, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * FP64 reductions over n elements of device arrays of `dtype` (used for
+ * Fig. 1's maximum(Ci) in the time-step rule and for the checks and the
+ * misfit loss):
+ *   IGG_RED_MAX      : max_i a[i]                     (b unused)
+ *   IGG_RED_SUM      : sum_i a[i]
+ *   IGG_RED_SUM_DIV  : sum_i a[i]/b[i]                 (heat content T/Ci)
+ *   IGG_RED_SUM_SQDIFF: sum_i (a[i]-b[i])^2
+ * Every term is formed and accumulated in FP64 with a fixed order (per-block
+ * partial sums in a scratch buffer, then one block combines them), so the
+ * result is deterministic. *out_dev is a device pointer to one double that
+ * receives the result. The partial sums go to a scratch buffer of at most
+ * 1024 doubles taken from the stream-ordered allocator (cudaMallocAsync on
+ * `stream`) and released on `stream` after use.
+ * ------------------------------------------------------------------------- */
+#define IGG_RED_MAX 0
+#define IGG_RED_SUM 1
+#define IGG_RED_SUM_DIV 2
+#define IGG_RED_SUM_SQDIFF 3
+int igg_reduce(int op, const void *a, const void *b, size_t n, igg_dtype dtype,
+               double *out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGG_H */

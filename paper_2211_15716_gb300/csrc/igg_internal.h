@@ -1,0 +1,70 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdarg>
+
+#include "../../include/igg.h"
+
+namespace igg {
+
+// Tile of work for one CTA of the stencil kernels: the columns x0 <= x < xe,
+// y0 <= y < ye (at most kTileX x kTileY of them) of one local array, swept
+// over z0 <= z < z1. All indices are local to the array; `base` is the
+// element offset of the array inside the field buffer. Every point of a tile
+// is an inner point of its array.
+struct Tile {
+  long long base;
+  int nx, ny;
+  int x0, y0, xe, ye;
+  int z0, z1;
+  int param;  // row of the coefficient table (batched form), else 0
+  int pad;
+};
+static_assert(sizeof(Tile) == 48, "Tile layout");
+
+// Tile extents (threads of a CTA are kTileX x kTileY, one column each).
+constexpr int kTileX = 32;
+constexpr int kTileY = 8;
+
+// Coefficients of the update T2 = T + Ci*(wx*(Txm+Txp) + wy*(Tym+Typ) +
+// wz*(Tzm+Tzp) + wc*T), with w_d = dt*lam/dd^2 and wc = -2*(wx+wy+wz),
+// all formed on the host in FP64.
+struct Coef {
+  double wx, wy, wz, wc;
+};
+
+Coef make_coef(double lam, double dt, double dx, double dy, double dz);
+
+// One face-plane copy of the halo update: the plane whose point with both
+// in-plane indices 0 is at element offset `src` is copied onto the plane at
+// `dst` (same in-plane geometry).
+struct PlaneCopy {
+  long long dst, src;
+};
+
+// error reporting (thread-local message)
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+void clear_error();
+
+size_t dtype_size(igg_dtype t);
+
+// kernel launchers (no synchronisation; errors from cudaGetLastError)
+cudaError_t launch_stencil(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
+                           const void *T, const void *Ci, const Coef &c,
+                           const Coef *table, cudaStream_t s);
+
+// One dimension of the halo update for one field: ncopies plane copies,
+// each plane having na x nb points with element strides sa, sb.
+cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
+                        void *field, int na, int nb, long long sa, long long sb,
+                        cudaStream_t s);
+
+cudaError_t launch_reduce(int op, const void *a, const void *b, size_t n,
+                          igg_dtype dt, double *scratch, int nblocks,
+                          double *out, cudaStream_t s);
+
+}  // namespace igg

@@ -1,0 +1,668 @@
+// Host runtime of the library: the implicit global grid (Sec. Approach;
+// Fig. 1 init_global_grid / nx_g / finalize_global_grid), its halo-copy
+// descriptor tables, the tile tables of the full step and of the
+// boundary/inner split, the high- and low-priority streams of the hidden
+// step, and the CUDA graphs of the time loop.
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "igg_internal.h"
+
+namespace igg {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+  return set_error(IGG_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { g_err.clear(); }
+
+size_t dtype_size(igg_dtype t) {
+  switch (t) {
+    case IGG_F64: return 8;
+    case IGG_F32: return 4;
+    case IGG_BF16: return 2;
+  }
+  return 0;
+}
+
+Coef make_coef(double lam, double dt, double dx, double dy, double dz) {
+  const double k = dt * lam;
+  Coef c;
+  c.wx = k / (dx * dx);
+  c.wy = k / (dy * dy);
+  c.wz = k / (dz * dz);
+  c.wc = -2.0 * (c.wx + c.wy + c.wz);
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+struct TileSet {
+  Tile *dev = nullptr;
+  int n = 0;
+};
+
+struct SplitTiles {
+  TileSet boundary, inner;
+};
+
+using GraphKey = std::tuple<const void *, const void *, const void *, int, int, int, int, int,
+                            double, double, double, double>;
+
+bool aligned16(const void *p) { return p != nullptr && ((uintptr_t)p & 15u) == 0; }
+
+// MPI_Dims_create's rule: the free entries multiply to the remaining factor,
+// are as balanced as possible (smallest largest factor, then smallest spread)
+// and non-increasing.
+bool dims_create(int nsub, int dims[3]) {
+  int fixed = 1, nfree = 0, free_idx[3];
+  for (int d = 0; d < 3; ++d) {
+    if (dims[d] < 0) return false;
+    if (dims[d] == 0) free_idx[nfree++] = d;
+    else fixed *= dims[d];
+  }
+  if (nsub <= 0 || nsub % fixed) return false;
+  const int rest = nsub / fixed;
+  if (nfree == 0) return rest == 1;
+  int best[3] = {0, 0, 0}, best_max = 0, best_spread = 0;
+  bool found = false;
+  const int lim1 = nfree >= 2 ? rest : 1, lim2 = nfree >= 3 ? rest : 1;
+  for (int a = 1; a <= rest; ++a) {
+    if (rest % a) continue;
+    for (int b = 1; b <= lim1; ++b) {
+      if ((rest / a) % b) continue;
+      for (int c = 1; c <= lim2; ++c) {
+        const long long prod = (long long)a * b * c;
+        if (prod != rest) continue;
+        const int f[3] = {a, b, c};
+        bool nonincr = true;
+        for (int i = 1; i < nfree; ++i) nonincr = nonincr && f[i - 1] >= f[i];
+        if (!nonincr) continue;
+        int mx = 0, mn = 1 << 30;
+        for (int i = 0; i < nfree; ++i) mx = std::max(mx, f[i]), mn = std::min(mn, f[i]);
+        if (!found || mx < best_max || (mx == best_max && mx - mn < best_spread)) {
+          found = true;
+          best_max = mx;
+          best_spread = mx - mn;
+          for (int i = 0; i < 3; ++i) best[i] = f[i];
+        }
+      }
+    }
+  }
+  if (!found) return false;
+  for (int i = 0; i < nfree; ++i) dims[free_idx[i]] = best[i];
+  return true;
+}
+
+// Rows of z planes per tile: enough tiles to fill the GPU several times over,
+// but long z sweeps (each tile re-reads two extra planes).
+int choose_zb(long long xy_tiles, int zext) {
+  int zb = 64;
+  while (zb > 8 && xy_tiles * ((zext + zb - 1) / zb) < 8 * 152 * 4) zb /= 2;
+  return std::max(1, std::min(zb, zext));
+}
+
+void add_box(std::vector<Tile> &v, long long base, int nx, int ny, int x0, int x1, int y0,
+             int y1, int z0, int z1, int zb, int param) {
+  if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;
+  for (int zc = z0; zc < z1; zc += zb)
+    for (int y = y0; y < y1; y += kTileY)
+      for (int x = x0; x < x1; x += kTileX) {
+        Tile t;
+        t.base = base;
+        t.nx = nx;
+        t.ny = ny;
+        t.x0 = x;
+        t.y0 = y;
+        t.xe = x1;
+        t.ye = y1;
+        t.z0 = zc;
+        t.z1 = std::min(zc + zb, z1);
+        t.param = param;
+        t.pad = 0;
+        v.push_back(t);
+      }
+}
+
+long long xy_tiles_of(int x0, int x1, int y0, int y1) {
+  if (x0 >= x1 || y0 >= y1) return 0;
+  return (long long)((x1 - x0 + kTileX - 1) / kTileX) * ((y1 - y0 + kTileY - 1) / kTileY);
+}
+
+int upload_tiles(const std::vector<Tile> &v, TileSet *out) {
+  out->n = (int)v.size();
+  out->dev = nullptr;
+  if (v.empty()) return IGG_OK;
+  cudaError_t e = cudaMalloc(&out->dev, v.size() * sizeof(Tile));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(tiles)");
+  e = cudaMemcpy(out->dev, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(tiles)");
+  return IGG_OK;
+}
+
+}  // namespace
+}  // namespace igg
+
+using namespace igg;
+
+struct igg_grid {
+  int n[3], dims[3], overlap[3], periods[3], ng[3];
+  int nsub = 0;
+  int device = 0;
+  long long nloc = 0;
+  std::vector<int> left, right;  // [nsub*3]
+  cudaStream_t hi = nullptr, lo = nullptr, cap = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
+  TileSet full;
+  std::map<std::array<int, 3>, SplitTiles> split;
+  PlaneCopy *copies[3] = {nullptr, nullptr, nullptr};
+  int ncopies[3] = {0, 0, 0};
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+int check_grid(const igg_grid *g) {
+  if (!g) return set_error(IGG_EINVAL, "grid handle is NULL");
+  return IGG_OK;
+}
+
+int check_field(const igg_grid *g, const void *p, const char *name) {
+  if (!p) return set_error(IGG_EINVAL, "%s is NULL", name);
+  if (!aligned16(p)) return set_error(IGG_EINVAL, "%s is not 16-byte aligned", name);
+  (void)g;
+  return IGG_OK;
+}
+
+int check_dtype(igg_dtype t) {
+  if (dtype_size(t) == 0) return set_error(IGG_EINVAL, "unknown dtype %d", (int)t);
+  return IGG_OK;
+}
+
+int check_coef(double lam, double dt, double dx, double dy, double dz) {
+  if (!(dx > 0) || !(dy > 0) || !(dz > 0))
+    return set_error(IGG_EINVAL, "grid spacings must be positive");
+  if (!(lam == lam) || !(dt == dt)) return set_error(IGG_EINVAL, "lam or dt is NaN");
+  return IGG_OK;
+}
+
+// Tiles of one box per subdomain, for the full step or a split part.
+int build_full_tiles(igg_grid *g) {
+  if (g->full.dev || g->full.n) return IGG_OK;
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const long long xy = xy_tiles_of(1, nx - 1, 1, ny - 1) * g->nsub;
+  const int zb = choose_zb(xy, nz - 2);
+  std::vector<Tile> v;
+  for (int s = 0; s < g->nsub; ++s)
+    add_box(v, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
+  return upload_tiles(v, &g->full);
+}
+
+int build_split_tiles(igg_grid *g, const int w[3], SplitTiles **out) {
+  std::array<int, 3> key = {w[0], w[1], w[2]};
+  auto it = g->split.find(key);
+  if (it != g->split.end()) {
+    *out = &it->second;
+    return IGG_OK;
+  }
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  // 0-based ranges: boundary-low [1, w-1], inner block [w, n-w-1],
+  // boundary-high [n-w, n-2]; clamp so that empty ranges stay empty.
+  auto lo_end = [](int wd, int nd) { return std::min(wd, nd - 1); };      // end of low slab
+  auto hi_beg = [](int wd, int nd) { return std::max(nd - wd, 1); };      // start of high slab
+  const int xl = lo_end(w[0], nx), xh = std::max(hi_beg(w[0], nx), xl);
+  const int yl = lo_end(w[1], ny), yh = std::max(hi_beg(w[1], ny), yl);
+  const int zl = lo_end(w[2], nz), zh = std::max(hi_beg(w[2], nz), zl);
+  std::vector<Tile> vb, vi;
+  // z slabs: all inner x, y; y slabs: z in the inner block range; x slabs:
+  // y and z in the inner block ranges. The six boxes are disjoint and their
+  // union with the inner block is the set of inner points.
+  long long xy_b = 0, xy_i = 0;
+  xy_b += 2 * xy_tiles_of(1, nx - 1, 1, ny - 1);
+  xy_b += 2 * xy_tiles_of(1, nx - 1, 1, yl) + 2 * xy_tiles_of(1, xl, yl, yh);
+  xy_i += xy_tiles_of(xl, xh, yl, yh);
+  const int zb_b = choose_zb(xy_b * g->nsub, zh - zl > 0 ? zh - zl : 1);
+  const int zb_i = choose_zb(xy_i * g->nsub, zh - zl > 0 ? zh - zl : 1);
+  for (int s = 0; s < g->nsub; ++s) {
+    const long long base = (long long)s * g->nloc;
+    add_box(vb, base, nx, ny, 1, nx - 1, 1, ny - 1, 1, zl, 64, 0);          // z low
+    add_box(vb, base, nx, ny, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, 0);     // z high
+    add_box(vb, base, nx, ny, 1, nx - 1, 1, yl, zl, zh, zb_b, 0);           // y low
+    add_box(vb, base, nx, ny, 1, nx - 1, yh, ny - 1, zl, zh, zb_b, 0);      // y high
+    add_box(vb, base, nx, ny, 1, xl, yl, yh, zl, zh, zb_b, 0);              // x low
+    add_box(vb, base, nx, ny, xh, nx - 1, yl, yh, zl, zh, zb_b, 0);         // x high
+    add_box(vi, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);             // inner block
+  }
+  SplitTiles st;
+  int rc = upload_tiles(vb, &st.boundary);
+  if (rc == IGG_OK) rc = upload_tiles(vi, &st.inner);
+  if (rc != IGG_OK) {
+    cudaFree(st.boundary.dev);
+    cudaFree(st.inner.dev);
+    return rc;
+  }
+  auto res = g->split.emplace(key, st);
+  *out = &res.first->second;
+  return IGG_OK;
+}
+
+// Plane-copy tables of the halo update, one per dimension.
+int build_halo_tables(igg_grid *g) {
+  const long long nx = g->n[0], ny = g->n[1];
+  const long long plane_stride[3] = {1, nx, nx * ny};
+  for (int d = 0; d < 3; ++d) {
+    std::vector<PlaneCopy> v;
+    const int nd = g->n[d], o = g->overlap[d];
+    for (int s = 0; s < g->nsub; ++s) {
+      const int l = g->left[3 * s + d], r = g->right[3 * s + d];
+      if (l >= 0)
+        v.push_back({(long long)s * g->nloc + 0 * plane_stride[d],
+                     (long long)l * g->nloc + (long long)(nd - o) * plane_stride[d]});
+      if (r >= 0)
+        v.push_back({(long long)s * g->nloc + (long long)(nd - 1) * plane_stride[d],
+                     (long long)r * g->nloc + (long long)(o - 1) * plane_stride[d]});
+    }
+    g->ncopies[d] = (int)v.size();
+    if (v.empty()) continue;
+    cudaError_t e = cudaMalloc(&g->copies[d], v.size() * sizeof(PlaneCopy));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(halo table)");
+    e = cudaMemcpy(g->copies[d], v.data(), v.size() * sizeof(PlaneCopy), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(halo table)");
+  }
+  return IGG_OK;
+}
+
+cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const long long sxy = (long long)nx * ny;
+  cudaError_t e = launch_halo(es, g->copies[0], g->ncopies[0], field, ny, nz, nx, sxy, s);
+  if (e == cudaSuccess) e = launch_halo(es, g->copies[1], g->ncopies[1], field, nx, nz, 1, sxy, s);
+  if (e == cudaSuccess) e = launch_halo(es, g->copies[2], g->ncopies[2], field, nx, ny, 1, nx, s);
+  return e;
+}
+
+bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->ncopies[2] > 0; }
+
+// One step of Fig. 1's loop, queued on s: plain (full step, then halo update
+// of T2 on s) or hidden (boundary set + halo on the high-priority stream,
+// inner block on the low-priority stream, s joins both).
+int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const void *Ci,
+                 igg_dtype dt, const Coef &c, bool with_halo, cudaStream_t s) {
+  cudaError_t e;
+  if (!widths) {
+    e = launch_stencil(dt, g->full.dev, g->full.n, T2, T, Ci, c, nullptr, s);
+    if (e != cudaSuccess) return cuda_error(e, "stencil launch");
+    if (with_halo && any_halo(g)) {
+      e = enqueue_halo(g, T2, dtype_size(dt), s);
+      if (e != cudaSuccess) return cuda_error(e, "halo launch");
+    }
+    return IGG_OK;
+  }
+  SplitTiles *st = nullptr;
+  int rc = build_split_tiles(g, widths, &st);
+  if (rc != IGG_OK) return rc;
+  if ((e = cudaEventRecord(g->ev_fork, s)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  if ((e = cudaStreamWaitEvent(g->hi, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
+  if ((e = cudaStreamWaitEvent(g->lo, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
+  e = launch_stencil(dt, st->boundary.dev, st->boundary.n, T2, T, Ci, c, nullptr, g->hi);
+  if (e == cudaSuccess && any_halo(g)) e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
+  if (e != cudaSuccess) return cuda_error(e, "boundary/halo launch");
+  e = launch_stencil(dt, st->inner.dev, st->inner.n, T2, T, Ci, c, nullptr, g->lo);
+  if (e != cudaSuccess) return cuda_error(e, "inner launch");
+  if ((e = cudaEventRecord(g->ev_hi, g->hi)) != cudaSuccess) return cuda_error(e, "record");
+  if ((e = cudaEventRecord(g->ev_lo, g->lo)) != cudaSuccess) return cuda_error(e, "record");
+  if ((e = cudaStreamWaitEvent(s, g->ev_hi, 0)) != cudaSuccess) return cuda_error(e, "wait");
+  if ((e = cudaStreamWaitEvent(s, g->ev_lo, 0)) != cudaSuccess) return cuda_error(e, "wait");
+  return IGG_OK;
+}
+
+int check_widths(const igg_grid *g, const int *w) {
+  if (!w) return IGG_OK;
+  for (int d = 0; d < 3; ++d) {
+    if (w[d] < g->overlap[d])
+      return set_error(IGG_EINVAL, "widths[%d]=%d is smaller than overlap %d", d, w[d],
+                       g->overlap[d]);
+  }
+  return IGG_OK;
+}
+
+void destroy_grid(igg_grid *g) {
+  if (!g) return;
+  for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : g->split) {
+    cudaFree(kv.second.boundary.dev);
+    cudaFree(kv.second.inner.dev);
+  }
+  cudaFree(g->full.dev);
+  for (int d = 0; d < 3; ++d) cudaFree(g->copies[d]);
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_hi) cudaEventDestroy(g->ev_hi);
+  if (g->ev_lo) cudaEventDestroy(g->ev_lo);
+  if (g->hi) cudaStreamDestroy(g->hi);
+  if (g->lo) cudaStreamDestroy(g->lo);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+}
+
+// most partial sums of igg_reduce (blocks of its first kernel)
+constexpr int kMaxRedBlocks = 1024;
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *igg_last_error(void) { return g_err.c_str(); }
+
+int igg_abi_version(void) { return IGG_ABI_VERSION; }
+
+int igg_init_global_grid(int nx, int ny, int nz, const int dims_in[3], int nsub,
+                         const int overlap[3], const int periods[3], igg_grid **out) {
+  clear_error();
+  if (!out) return set_error(IGG_EINVAL, "out is NULL");
+  *out = nullptr;
+  const int n[3] = {nx, ny, nz};
+  int dims[3] = {0, 0, 0}, o[3] = {2, 2, 2}, per[3] = {0, 0, 0};
+  if (dims_in) std::memcpy(dims, dims_in, sizeof dims);
+  if (overlap) std::memcpy(o, overlap, sizeof o);
+  if (periods)
+    for (int d = 0; d < 3; ++d) per[d] = periods[d] ? 1 : 0;
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 3) return set_error(IGG_EINVAL, "local size n[%d]=%d < 3", d, n[d]);
+    if (o[d] < 2 || o[d] > n[d] - 1)
+      return set_error(IGG_EINVAL, "overlap[%d]=%d outside [2, n-1]", d, o[d]);
+  }
+  bool has_free = dims[0] == 0 || dims[1] == 0 || dims[2] == 0;
+  if (has_free) {
+    if (!dims_create(nsub, dims))
+      return set_error(IGG_EINVAL, "cannot factor nsub=%d over dims (%d,%d,%d)", nsub,
+                       dims_in ? dims_in[0] : 0, dims_in ? dims_in[1] : 0,
+                       dims_in ? dims_in[2] : 0);
+  } else {
+    for (int d = 0; d < 3; ++d)
+      if (dims[d] < 0) return set_error(IGG_EINVAL, "negative dims");
+    if (nsub > 0 && nsub != dims[0] * dims[1] * dims[2])
+      return set_error(IGG_EINVAL, "dims product %d differs from nsub %d",
+                       dims[0] * dims[1] * dims[2], nsub);
+  }
+  const long long nloc = (long long)nx * ny * nz;
+  if (nloc > (1LL << 40)) return set_error(IGG_EINVAL, "local array too large");
+
+  igg_grid *g = new (std::nothrow) igg_grid();
+  if (!g) return set_error(IGG_ENOMEM, "host allocation failed");
+  for (int d = 0; d < 3; ++d) {
+    g->n[d] = n[d];
+    g->dims[d] = dims[d];
+    g->overlap[d] = o[d];
+    g->periods[d] = per[d];
+    g->ng[d] = dims[d] * (n[d] - o[d]) + (per[d] ? 0 : o[d]);
+  }
+  g->nsub = dims[0] * dims[1] * dims[2];
+  g->nloc = nloc;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) {
+    destroy_grid(g);
+    return cuda_error(e, "cudaGetDevice");
+  }
+  // topology: coordinates x fastest; neighbours wrap in periodic dimensions
+  g->left.assign(3 * g->nsub, -1);
+  g->right.assign(3 * g->nsub, -1);
+  for (int s = 0; s < g->nsub; ++s) {
+    const int c[3] = {s % dims[0], (s / dims[0]) % dims[1], s / (dims[0] * dims[1])};
+    for (int d = 0; d < 3; ++d) {
+      for (int side = 0; side < 2; ++side) {
+        int cc[3] = {c[0], c[1], c[2]};
+        cc[d] += side == 0 ? -1 : 1;
+        if (cc[d] < 0 || cc[d] >= dims[d]) {
+          if (!per[d]) continue;
+          cc[d] = (cc[d] + dims[d]) % dims[d];
+        }
+        const int nb = cc[0] + dims[0] * (cc[1] + dims[1] * cc[2]);
+        (side == 0 ? g->left : g->right)[3 * s + d] = nb;
+      }
+    }
+  }
+  int lo_prio = 0, hi_prio = 0;
+  e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g->hi, cudaStreamNonBlocking, hi_prio);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&g->lo, cudaStreamNonBlocking, lo_prio);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_hi, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_lo, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    destroy_grid(g);
+    return cuda_error(e, "stream/event creation");
+  }
+  int rc = build_halo_tables(g);
+  if (rc == IGG_OK) rc = build_full_tiles(g);
+  if (rc != IGG_OK) {
+    destroy_grid(g);
+    return rc;
+  }
+  *out = g;
+  return IGG_OK;
+}
+
+int igg_finalize_global_grid(igg_grid *g) {
+  clear_error();
+  if (!g) return IGG_OK;
+  DeviceGuard dg(g->device);
+  cudaError_t e1 = cudaStreamSynchronize(g->hi);
+  cudaError_t e2 = cudaStreamSynchronize(g->lo);
+  destroy_grid(g);
+  if (e1 != cudaSuccess) return cuda_error(e1, "finalize: high-priority stream");
+  if (e2 != cudaSuccess) return cuda_error(e2, "finalize: low-priority stream");
+  return IGG_OK;
+}
+
+int igg_global_size(const igg_grid *g, int n_g[3]) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (!n_g) return set_error(IGG_EINVAL, "n_g is NULL");
+  for (int d = 0; d < 3; ++d) n_g[d] = g->ng[d];
+  return IGG_OK;
+}
+
+int igg_grid_shape(const igg_grid *g, int n[3], int dims[3], int overlap[3], int periods[3],
+                   int *nsub) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  for (int d = 0; d < 3; ++d) {
+    if (n) n[d] = g->n[d];
+    if (dims) dims[d] = g->dims[d];
+    if (overlap) overlap[d] = g->overlap[d];
+    if (periods) periods[d] = g->periods[d];
+  }
+  if (nsub) *nsub = g->nsub;
+  return IGG_OK;
+}
+
+int igg_subdomain_info(const igg_grid *g, int sub, int coords[3], int left[3], int right[3],
+                       int offset[3]) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (sub < 0 || sub >= g->nsub) return set_error(IGG_EINVAL, "sub %d out of range", sub);
+  const int c[3] = {sub % g->dims[0], (sub / g->dims[0]) % g->dims[1],
+                    sub / (g->dims[0] * g->dims[1])};
+  for (int d = 0; d < 3; ++d) {
+    if (coords) coords[d] = c[d];
+    if (left) left[d] = g->left[3 * sub + d];
+    if (right) right[d] = g->right[3 * sub + d];
+    if (offset) offset[d] = c[d] * (g->n[d] - g->overlap[d]);
+  }
+  return IGG_OK;
+}
+
+int igg_update_halo(igg_grid *g, void *const fields[], int nfields, igg_dtype dt,
+                    void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_dtype(dt)) return rc;
+  if (nfields < 0 || (nfields > 0 && !fields)) return set_error(IGG_EINVAL, "bad field list");
+  for (int i = 0; i < nfields; ++i)
+    if (int rc = check_field(g, fields[i], "field")) return rc;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < nfields; ++i) {
+    cudaError_t e = enqueue_halo(g, fields[i], dtype_size(dt), s);
+    if (e != cudaSuccess) return cuda_error(e, "halo launch");
+  }
+  return IGG_OK;
+}
+
+int igg_step(igg_grid *g, void *T2, const void *T, const void *Ci, igg_dtype dt, double lam,
+             double dtime, double dx, double dy, double dz, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_dtype(dt)) return rc;
+  if (int rc = check_field(g, T2, "T2")) return rc;
+  if (int rc = check_field(g, T, "T")) return rc;
+  if (int rc = check_field(g, Ci, "Ci")) return rc;
+  if (T2 == T || T2 == Ci) return set_error(IGG_EINVAL, "T2 aliases T or Ci");
+  if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
+  DeviceGuard dg(g->device);
+  return enqueue_step(g, nullptr, T2, T, Ci, dt, make_coef(lam, dtime, dx, dy, dz), false,
+                      (cudaStream_t)stream);
+}
+
+int igg_step_hidden(igg_grid *g, const int widths[3], void *T2, const void *T, const void *Ci,
+                    igg_dtype dt, double lam, double dtime, double dx, double dy, double dz,
+                    void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (!widths) return set_error(IGG_EINVAL, "widths is NULL");
+  if (int rc = check_widths(g, widths)) return rc;
+  if (int rc = check_dtype(dt)) return rc;
+  if (int rc = check_field(g, T2, "T2")) return rc;
+  if (int rc = check_field(g, T, "T")) return rc;
+  if (int rc = check_field(g, Ci, "Ci")) return rc;
+  if (T2 == T || T2 == Ci) return set_error(IGG_EINVAL, "T2 aliases T or Ci");
+  if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
+  DeviceGuard dg(g->device);
+  return enqueue_step(g, widths, T2, T, Ci, dt, make_coef(lam, dtime, dx, dy, dz), true,
+                      (cudaStream_t)stream);
+}
+
+int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const void *Ci,
+            igg_dtype dt, double lam, double dtime, double dx, double dy, double dz,
+            void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (nt < 0) return set_error(IGG_EINVAL, "nt < 0");
+  if (int rc = check_widths(g, widths)) return rc;
+  if (int rc = check_dtype(dt)) return rc;
+  if (int rc = check_field(g, T2, "T2")) return rc;
+  if (int rc = check_field(g, T, "T")) return rc;
+  if (int rc = check_field(g, Ci, "Ci")) return rc;
+  if (T2 == T || T2 == Ci || T == Ci) return set_error(IGG_EINVAL, "T, T2, Ci alias");
+  if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Coef c = make_coef(lam, dtime, dx, dy, dz);
+  if (nt == 0) return IGG_OK;
+  cudaGraphExec_t exec = nullptr;
+  if (nt >= 2) {
+    SplitTiles *st = nullptr;
+    if (widths) {
+      int rc = build_split_tiles(g, widths, &st);  // before capture: allocates
+      if (rc != IGG_OK) return rc;
+    }
+    const GraphKey key(T, T2, Ci, (int)dt, widths ? 1 : 0, widths ? widths[0] : 0,
+                       widths ? widths[1] : 0, widths ? widths[2] : 0, c.wx, c.wy, c.wz, c.wc);
+    auto it = g->graphs.find(key);
+    if (it != g->graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+      int rc = enqueue_step(g, widths, T2, T, Ci, dt, c, true, g->cap);
+      if (rc == IGG_OK) rc = enqueue_step(g, widths, T, T2, Ci, dt, c, true, g->cap);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(g->cap, &graph);
+      if (rc != IGG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+      if (g->graphs.size() >= 16) {  // bounded cache
+        cudaGraphExecDestroy(g->graphs.begin()->second);
+        g->graphs.erase(g->graphs.begin());
+      }
+      g->graphs.emplace(key, exec);
+    }
+    for (int i = 0; i < nt / 2; ++i) {
+      cudaError_t e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+    }
+  }
+  if (nt % 2) return enqueue_step(g, widths, T2, T, Ci, dt, c, true, s);
+  return IGG_OK;
+}
+
+int igg_reduce(int op, const void *a, const void *b, size_t n, igg_dtype dt, double *out_dev,
+               void *stream) {
+  clear_error();
+  if (op < IGG_RED_MAX || op > IGG_RED_SUM_SQDIFF) return set_error(IGG_EINVAL, "bad op %d", op);
+  if (int rc = check_dtype(dt)) return rc;
+  if (n > 0 && !a) return set_error(IGG_EINVAL, "a is NULL");
+  if (n > 0 && (op == IGG_RED_SUM_DIV || op == IGG_RED_SUM_SQDIFF) && !b)
+    return set_error(IGG_EINVAL, "b is NULL");
+  if (!out_dev) return set_error(IGG_EINVAL, "out_dev is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  long long nb = (long long)((n + 255) / 256);
+  if (nb < 1) nb = 1;
+  if (nb > kMaxRedBlocks) nb = kMaxRedBlocks;
+  // per-call scratch from the stream-ordered allocator: calls on different
+  // streams never share it
+  double *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&scratch, (size_t)nb * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(reduce scratch)");
+  e = launch_reduce(op, a, b, n, dt, scratch, (int)nb, out_dev, s);
+  cudaError_t ef = cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_error(e, "reduce launch");
+  if (ef != cudaSuccess) return cuda_error(ef, "cudaFreeAsync(reduce scratch)");
+  return IGG_OK;
+}
+
+}  // extern "C"

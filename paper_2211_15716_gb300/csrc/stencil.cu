@@ -1,0 +1,149 @@
+// Stencil kernels: Fig. 1's step! on lists of tiles.
+//
+// One kernel serves the full step, the boundary slabs and the inner block of
+// the hidden step, and the batched form: the host turns each of them into a
+// table of tiles, and every CTA sweeps one tile along z with the three z
+// planes of its column kept in registers (z-marching). The x and y
+// neighbours are read through the read-only data cache, where the
+// neighbouring columns of the same CTA have just brought them.
+//
+// Arithmetic (identical in every launch, so every kernel gives the same bits
+// for the same point):
+//   FP64: s_d = T[-d] + T[+d];  l = wc*T;  l += wx*s_x;  l += wy*s_y;
+//         l += wz*s_z;  T2 = T + Ci*l  (FMA where written, round-to-nearest
+//         intrinsics so that no other contraction can happen).
+//   FP32 / BF16 storage: the differences are formed first, which is exact
+//   for neighbouring values within a factor 2:
+//         e_d = (T[+d] - T) + (T[-d] - T);  l = wx*e_x;  l += wy*e_y;
+//         l += wz*e_z;  T2 = T + Ci*l.
+// No CUDA math-library function is used: only + - * and FMA.
+#include <cuda_bf16.h>
+
+#include "igg_internal.h"
+
+namespace igg {
+namespace {
+
+template <class S>
+struct Num;
+
+template <>
+struct Num<double> {
+  using C = double;
+  static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
+};
+template <>
+struct Num<float> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <>
+struct Num<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+  }
+};
+
+template <class C>
+struct W {
+  C wx, wy, wz, wc;
+};
+
+__device__ __forceinline__ W<double> make_w(const Coef &c, double) {
+  return {c.wx, c.wy, c.wz, c.wc};
+}
+__device__ __forceinline__ W<float> make_w(const Coef &c, float) {
+  return {(float)c.wx, (float)c.wy, (float)c.wz, (float)c.wc};
+}
+
+// The update of one inner point (see the file comment for the order).
+__device__ __forceinline__ double cell(double t, double xm, double xp, double ym,
+                                       double yp, double zm, double zp, double ci,
+                                       const W<double> &w) {
+  const double sx = __dadd_rn(xm, xp);
+  const double sy = __dadd_rn(ym, yp);
+  const double sz = __dadd_rn(zm, zp);
+  double l = __dmul_rn(w.wc, t);
+  l = __fma_rn(w.wx, sx, l);
+  l = __fma_rn(w.wy, sy, l);
+  l = __fma_rn(w.wz, sz, l);
+  return __fma_rn(ci, l, t);
+}
+
+__device__ __forceinline__ float cell(float t, float xm, float xp, float ym,
+                                      float yp, float zm, float zp, float ci,
+                                      const W<float> &w) {
+  const float ex = __fadd_rn(__fsub_rn(xp, t), __fsub_rn(xm, t));
+  const float ey = __fadd_rn(__fsub_rn(yp, t), __fsub_rn(ym, t));
+  const float ez = __fadd_rn(__fsub_rn(zp, t), __fsub_rn(zm, t));
+  float l = __fmul_rn(w.wx, ex);
+  l = __fmaf_rn(w.wy, ey, l);
+  l = __fmaf_rn(w.wz, ez, l);
+  return __fmaf_rn(ci, l, t);
+}
+
+template <class S>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    k_stencil_tiles(const Tile *__restrict__ tiles, S *__restrict__ T2,
+                    const S *__restrict__ T, const S *__restrict__ Ci, Coef c0,
+                    const Coef *__restrict__ table) {
+  using N = Num<S>;
+  using C = typename N::C;
+  const Tile t = tiles[blockIdx.x];
+  const int x = t.x0 + (int)threadIdx.x;
+  const int y = t.y0 + (int)threadIdx.y;
+  if (x >= t.xe || y >= t.ye) return;
+  const W<C> w = make_w(table ? table[t.param] : c0, C(0));
+  const long long sy = t.nx;
+  const long long sz = (long long)t.nx * t.ny;
+  long long p = t.base + x + sy * y + sz * (t.z0 - 1);
+  C zm = N::ld(T + p);
+  C zc = N::ld(T + p + sz);
+  for (int z = t.z0; z < t.z1; ++z) {
+    p += sz;
+    const C zp = N::ld(T + p + sz);
+    const C xm = N::ld(T + p - 1);
+    const C xp = N::ld(T + p + 1);
+    const C ym = N::ld(T + p - sy);
+    const C yp = N::ld(T + p + sy);
+    const C ci = N::ld(Ci + p);
+    N::st(T2 + p, cell(zc, xm, xp, ym, yp, zm, zp, ci, w));
+    zm = zc;
+    zc = zp;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stencil(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
+                           const void *T, const void *Ci, const Coef &c,
+                           const Coef *table, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  const dim3 block(kTileX, kTileY);
+  switch (dt) {
+    case IGG_F64:
+      k_stencil_tiles<double><<<ntiles, block, 0, s>>>(
+          tiles, (double *)T2, (const double *)T, (const double *)Ci, c, table);
+      break;
+    case IGG_F32:
+      k_stencil_tiles<float><<<ntiles, block, 0, s>>>(
+          tiles, (float *)T2, (const float *)T, (const float *)Ci, c, table);
+      break;
+    case IGG_BF16:
+      k_stencil_tiles<__nv_bfloat16><<<ntiles, block, 0, s>>>(
+          tiles, (__nv_bfloat16 *)T2, (const __nv_bfloat16 *)T,
+          (const __nv_bfloat16 *)Ci, c, table);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace igg

@@ -1,0 +1,234 @@
+"""Python binding of libigg.so (ctypes): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+turns torch tensors into device pointers and torch streams into
+cudaStream_t handles, checks shapes and dtypes, and raises IggError on a
+negative status. There is no fallback: if the library is missing, the first
+call raises.
+
+Names follow the paper (Fig. 1): init_global_grid -> Grid(...),
+nx_g()/ny_g()/nz_g() -> Grid.global_size(), update_halo! ->
+Grid.update_halo(...), step! -> Grid.step(...), @hide_communication ->
+Grid.step_hidden(...), the time loop -> Grid.run(...),
+finalize_global_grid -> Grid.finalize().
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+F64, F32, BF16 = 0, 1, 2
+RED_MAX, RED_SUM, RED_SUM_DIV, RED_SUM_SQDIFF = 0, 1, 2, 3
+
+_TORCH_DTYPE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+_lib = None
+
+
+class IggError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"igg error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libigg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built: run paper_2211_15716_gb300.build.build() "
+                          "(the library has no CPU fallback)")
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    IP = ctypes.POINTER(ctypes.c_int)
+    L.igg_last_error.restype = ctypes.c_char_p
+    L.igg_abi_version.restype = I
+    L.igg_init_global_grid.argtypes = [I, I, I, IP, I, IP, IP, ctypes.POINTER(P)]
+    L.igg_finalize_global_grid.argtypes = [P]
+    L.igg_global_size.argtypes = [P, IP]
+    L.igg_grid_shape.argtypes = [P, IP, IP, IP, IP, IP]
+    L.igg_subdomain_info.argtypes = [P, I, IP, IP, IP, IP]
+    L.igg_update_halo.argtypes = [P, ctypes.POINTER(P), I, I, P]
+    L.igg_step.argtypes = [P, P, P, P, I, D, D, D, D, D, P]
+    L.igg_step_hidden.argtypes = [P, IP, P, P, P, I, D, D, D, D, D, P]
+    L.igg_run.argtypes = [P, I, IP, P, P, P, I, D, D, D, D, D, P]
+    L.igg_reduce.argtypes = [I, P, P, ctypes.c_size_t, I, P, P]
+    for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
+                 "igg_grid_shape", "igg_subdomain_info", "igg_update_halo", "igg_step",
+                 "igg_step_hidden", "igg_run", "igg_reduce"):
+        getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise IggError(rc, lib().igg_last_error().decode(errors="replace"))
+
+
+def _ints(v):
+    return (ctypes.c_int * 3)(*[int(x) for x in v])
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def dtype_code(dtype: torch.dtype) -> int:
+    try:
+        return _TORCH_DTYPE[dtype]
+    except KeyError:
+        raise TypeError(f"unsupported dtype {dtype}; use float64, float32 or bfloat16") from None
+
+
+def _ptr(t: torch.Tensor, numel: int, dtype: torch.dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Implicit global grid of nsub subdomains of n = (nx, ny, nz) points in
+    one device's memory (Fig. 1 init_global_grid). Fields are tensors of
+    shape (nsub, nz, ny, nx)."""
+
+    def __init__(self, n, dims=(0, 0, 0), nsub: int = 0, overlap=(2, 2, 2), periods=(0, 0, 0)):
+        L = lib()
+        h = ctypes.c_void_p()
+        if nsub:
+            nsub_arg = nsub
+        elif all(dims):
+            nsub_arg = dims[0] * dims[1] * dims[2]
+        else:
+            nsub_arg = 1 if not any(dims) else 0
+        _check(L.igg_init_global_grid(int(n[0]), int(n[1]), int(n[2]), _ints(dims), int(nsub_arg),
+                                      _ints(overlap), _ints(periods), ctypes.byref(h)))
+        self._h = h
+        nn, dd, oo, pp, ns = _ints((0, 0, 0)), _ints((0, 0, 0)), _ints((0, 0, 0)), _ints((0, 0, 0)), ctypes.c_int()
+        _check(L.igg_grid_shape(h, nn, dd, oo, pp, ctypes.byref(ns)))
+        self.n, self.dims, self.overlap = tuple(nn), tuple(dd), tuple(oo)
+        self.periods, self.nsub = tuple(pp), ns.value
+        self.nloc = self.n[0] * self.n[1] * self.n[2]
+
+    # -- lifetime --------------------------------------------------------
+    def finalize(self):
+        """Fig. 1 finalize_global_grid."""
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().igg_finalize_global_grid(h))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.finalize()
+
+    def __del__(self):
+        try:
+            self.finalize()
+        except Exception:
+            pass
+
+    def _handle(self):
+        if not self._h:
+            raise IggError(-4, "grid used after finalize")
+        return self._h
+
+    # -- queries ---------------------------------------------------------
+    @property
+    def shape(self):
+        return (self.nsub, self.n[2], self.n[1], self.n[0])
+
+    def global_size(self):
+        """(nx_g(), ny_g(), nz_g())."""
+        ng = _ints((0, 0, 0))
+        _check(lib().igg_global_size(self._handle(), ng))
+        return tuple(ng)
+
+    def subdomain_info(self, sub: int):
+        """dict(coords, left, right, offset) of subdomain `sub`."""
+        c, l, r, o = (_ints((0, 0, 0)) for _ in range(4))
+        _check(lib().igg_subdomain_info(self._handle(), int(sub), c, l, r, o))
+        return {"coords": tuple(c), "left": tuple(l), "right": tuple(r), "offset": tuple(o)}
+
+    def global_indices(self, sub: int):
+        """Per axis, the global index of each local point of `sub`."""
+        info = self.subdomain_info(sub)
+        ng = self.global_size()
+        out = []
+        for d in range(3):
+            g = torch.arange(self.n[d], dtype=torch.int64) + info["offset"][d]
+            out.append((g % ng[d]) if self.periods[d] else g)
+        return [t.numpy() for t in out]
+
+    def empty(self, dtype=torch.float64, device="cuda"):
+        return torch.empty(self.shape, dtype=dtype, device=device)
+
+    # -- hot path --------------------------------------------------------
+    def update_halo(self, *fields, stream=None):
+        """update_halo!(fields...): all fields must share one dtype."""
+        if not fields:
+            return
+        dt = fields[0].dtype
+        arr = (ctypes.c_void_p * len(fields))(*[_ptr(f, self.nsub * self.nloc, dt, "field").value
+                                                for f in fields])
+        _check(lib().igg_update_halo(self._handle(), arr, len(fields), dtype_code(dt), _stream(stream)))
+
+    def step(self, T2, T, Ci, lam, dt, dx, dy, dz, stream=None):
+        """Fig. 1 step! on every subdomain (inner points of T2)."""
+        n = self.nsub * self.nloc
+        d = T.dtype
+        _check(lib().igg_step(self._handle(), _ptr(T2, n, d, "T2"), _ptr(T, n, d, "T"),
+                              _ptr(Ci, n, d, "Ci"), dtype_code(d), float(lam), float(dt),
+                              float(dx), float(dy), float(dz), _stream(stream)))
+
+    def step_hidden(self, widths, T2, T, Ci, lam, dt, dx, dy, dz, stream=None):
+        """@hide_communication widths { step!(T2, T, ...); update_halo!(T2) }."""
+        n = self.nsub * self.nloc
+        d = T.dtype
+        _check(lib().igg_step_hidden(self._handle(), _ints(widths), _ptr(T2, n, d, "T2"),
+                                     _ptr(T, n, d, "T"), _ptr(Ci, n, d, "Ci"), dtype_code(d),
+                                     float(lam), float(dt), float(dx), float(dy), float(dz),
+                                     _stream(stream)))
+
+    def run(self, nt, T, T2, Ci, lam, dt, dx, dy, dz, widths=None, stream=None):
+        """Fig. 1's time loop (graph-captured). Returns the tensor that holds
+        the newest state: T for even nt, T2 for odd nt."""
+        n = self.nsub * self.nloc
+        d = T.dtype
+        w = _ints(widths) if widths is not None else None
+        _check(lib().igg_run(self._handle(), int(nt), w, _ptr(T, n, d, "T"), _ptr(T2, n, d, "T2"),
+                             _ptr(Ci, n, d, "Ci"), dtype_code(d), float(lam), float(dt), float(dx),
+                             float(dy), float(dz), _stream(stream)))
+        return T if nt % 2 == 0 else T2
+
+
+def reduce(op: int, a: torch.Tensor, b: torch.Tensor | None = None, out: torch.Tensor | None = None,
+           stream=None):
+    """FP64 reduction over all elements (RED_MAX, RED_SUM, RED_SUM_DIV,
+    RED_SUM_SQDIFF). Returns a 1-element float64 device tensor."""
+    n = a.numel()
+    pa = _ptr(a, n, a.dtype, "a")
+    pb = _ptr(b, n, a.dtype, "b") if b is not None else None
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=a.device)
+    _check(lib().igg_reduce(int(op), pa, pb, n, dtype_code(a.dtype), ctypes.c_void_p(out.data_ptr()),
+                            _stream(stream)))
+    return out
