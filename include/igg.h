@@ -186,6 +186,32 @@ int igg_run(igg_grid *grid, int nt, const int widths[3], void *T, void *T2,
 int igg_reduce(int op, const void *a, const void *b, size_t n, igg_dtype dtype,
                double *out_dev, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * The same reductions without any device allocation. The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory at the time they reduce: code running under an allocator
+ * that owns all device memory or forbids growth, host callbacks and
+ * real-time loops with a fixed memory budget, or stream-capture regions
+ * where allocation calls are not allowed.
+ *
+ * Arguments, ops and dtypes as igg_reduce. Each block of the first kernel
+ * reduces one contiguous chunk of 65536 elements, so the summation order
+ * (and possibly the last bits of a sum) differ from igg_reduce's; IGG_RED_MAX
+ * is exact either way. The partial sums live in a file-scope device array
+ * of 32768 doubles (256 KB) that every GPU loading the library holds until
+ * the process exits; n above 32768*65536 = 2^31 elements gives IGG_EINVAL.
+ * The function calls no cudaMalloc, cudaMallocAsync, cudaFree or other
+ * allocating routine. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device, with that device current);
+ * make that first call before any stream capture. All calls share the one
+ * array: calls whose work can overlap on the GPU (different streams, or
+ * several host threads) race and must be ordered by the caller. The array
+ * keeps the last call's contents; every partial sum a call reads is written
+ * by that call first, so nothing has to start at zero.
+ * ------------------------------------------------------------------------- */
+int igg_reduce_noalloc(int op, const void *a, const void *b, size_t n,
+                       igg_dtype dtype, double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

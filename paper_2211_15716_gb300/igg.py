@@ -232,3 +232,24 @@ def reduce(op: int, a: torch.Tensor, b: torch.Tensor | None = None, out: torch.T
     _check(lib().igg_reduce(int(op), pa, pb, n, dtype_code(a.dtype), ctypes.c_void_p(out.data_ptr()),
                             _stream(stream)))
     return out
+
+
+def reduce_noalloc(op: int, a: torch.Tensor, b: torch.Tensor | None = None,
+                   out: torch.Tensor | None = None, stream=None):
+    """igg_reduce_noalloc: the FP64 reduction without any device allocation
+    inside the library (partial sums in a fixed device array of the library).
+    For callers that cannot allocate while they reduce; pass a preallocated
+    `out` (1-element float64 device tensor) to allocate nothing at all.
+    Calls that can overlap on the GPU share that array and must be ordered."""
+    L = lib()
+    fn = L.igg_reduce_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                   ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    n = a.numel()
+    pa = _ptr(a, n, a.dtype, "a")
+    pb = _ptr(b, n, a.dtype, "b") if b is not None else None
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=a.device)
+    _check(fn(int(op), pa, pb, n, dtype_code(a.dtype), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
