@@ -55,6 +55,9 @@ WORKLOADS = {
     "decomposed_2x2x2_512x256x256": Workload(
         "decomposed_2x2x2_512x256x256", (512, 256, 256), dims=(2, 2, 2), periods=(1, 0, 0),
         widths=(16, 2, 2), seed=1),
+    "decomposed_2x2x2_256x128x128": Workload(
+        "decomposed_2x2x2_256x128x128", (256, 128, 128), dims=(2, 2, 2), periods=(1, 0, 0),
+        widths=(16, 2, 2), seed=1),
     "precision_1024": Workload("precision_1024", (1024, 1024, 1024), nt=1000, seed=2, t0="sines",
                                ci="uniform"),
     "precision_128": Workload("precision_128", (128, 128, 128), nt=1000, seed=2, t0="sines",
@@ -80,7 +83,7 @@ def host_fields(w: Workload, grid: Grid, sub: int):
 
 def _to_device(a64: np.ndarray, dtype: torch.dtype, out: torch.Tensor):
     if dtype == torch.float64:
-        out.copy_(torch.from_numpy(np.ascontiguousarray(a64)))
+        out.copy_(torch.from_numpy(np.array(a64, dtype=np.float64, order="C", copy=True)))
     elif dtype == torch.float32:
         out.copy_(torch.from_numpy(synth.to_f32(a64)))
     else:
