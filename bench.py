@@ -266,7 +266,7 @@ def main():
         t = torch.tensor([e2e_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    assert np.isfinite(Rh[0, 5, 5, :8].numpy()).all()
+    assert torch.isfinite(Rh[0, 5, 5, :8].float()).all()
 
     hbm, hbm_kind = peaks()
     value = ws * bytes_step / (ms_step * 1e-3) / 1e9

@@ -165,6 +165,64 @@ int igg_run(igg_grid *grid, int nt, const int widths[3], void *T, void *T2,
             double dy, double dz, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched form: nprob independent diffusion problems of uneven sizes (each
+ * Fig. 1's step! on one array with fixed boundary values, its own lam, dt,
+ * dx, dy, dz), advanced together by ONE persistent kernel launch per step.
+ *
+ * Layout: every field of the batch is one device buffer; problem b is an
+ * array [nz_b][ny_b][nx_b] (x fastest) starting at element offset
+ * offsets[b] (igg_batch_layout), each offset a multiple of 256 bytes; the
+ * buffer holds `total` elements of the dtype. Gaps between problems are never
+ * read or written.
+ * ------------------------------------------------------------------------- */
+
+/* sizes: nprob triples (nx, ny, nz), each >= 3. Creates the tile table with
+ * the default tiling (32x8 tiles, 32-plane z depth, resident CTAs per SM). */
+int igg_batch_create(int nprob, const int *sizes, igg_dtype dtype,
+                     igg_batch **out);
+
+/* Frees the batch (waits for its capture stream). NULL is accepted. */
+int igg_batch_destroy(igg_batch *batch);
+
+/* offsets[nprob] (may be NULL) and the total element count of a field. */
+int igg_batch_layout(const igg_batch *batch, long long *offsets,
+                     long long *total);
+
+/* Per-problem coefficients from host arrays of nprob doubles each; required
+ * before the first step. */
+int igg_batch_set_coefs(igg_batch *batch, const double *lam, const double *dt,
+                        const double *dx, const double *dy, const double *dz);
+
+/* Tiling: variant 0 = 32x8, 1 = 32x4, 2 = 64x4 columns per tile; zb = z
+ * planes per tile (0 = the whole problem depth); ctas_per_sm = CTAs of the
+ * persistent grid per SM (0 = as many as are resident; more than resident
+ * gives IGG_EINVAL). The arithmetic does not depend on the tiling: every
+ * tiling gives the same bits. */
+int igg_batch_configure(igg_batch *batch, int variant, int zb, int ctas_per_sm);
+
+/* Current tiling {variant, zb, ctas_per_sm} and the number of tiles. */
+int igg_batch_get_config(const igg_batch *batch, int cfg[3], int *ntiles);
+
+/* One step of every problem: T2 = step(T) on inner points (layout above). */
+int igg_batch_step(igg_batch *batch, void *T2, const void *T, const void *Ci,
+                   void *stream);
+
+/* nt steps with swaps, captured once into a CUDA graph (two steps per
+ * launch, cached for the same pointers); newest state in T for even nt and
+ * in T2 for odd nt. T2 must hold T's boundary values on entry. */
+int igg_batch_run(igg_batch *batch, int nt, void *T, void *T2, const void *Ci,
+                  void *stream);
+
+/* Autotuner: times every tiling (3 tile shapes x z depths {8,16,32,64,all}
+ * x {resident, half of resident} CTAs per SM) for `reps` steps T -> T2 on the
+ * caller's fields, on `stream`, keeps the fastest and returns it in
+ * best_cfg[3] with its time per step in *best_ms. Writes T2's inner points
+ * and synchronises `stream`. */
+int igg_batch_autotune(igg_batch *batch, void *T2, const void *T,
+                       const void *Ci, int reps, void *stream, int best_cfg[3],
+                       float *best_ms);
+
+/* ---------------------------------------------------------------------------
  * FP64 reductions over n elements of device arrays of `dtype` (used for
  * Fig. 1's maximum(Ci) in the time-step rule and for the checks and the
  * misfit loss):

@@ -1,0 +1,360 @@
+// Batched form of the step: many independent diffusion problems of uneven
+// sizes advanced together, one persistent launch per step, the nt-step loop
+// captured in a CUDA graph, and an autotuner that picks the tile shape, the
+// z depth of a tile and the number of CTAs per SM by timing them on the
+// caller's data.
+//
+// Layout: all problems of a field share one device buffer; problem b is an
+// array [nz_b][ny_b][nx_b] (x fastest) starting at element offset off[b],
+// every offset aligned to 256 bytes. Each problem has its own lam, dt, dx,
+// dy, dz (coefficient table on the device).
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "igg_internal.h"
+
+using namespace igg;
+
+namespace {
+
+// CTAs per SM of each persistent variant for this dtype (occupancy query).
+int max_ctas_per_sm(igg_dtype dt, int variant);
+
+}  // namespace
+
+struct igg_batch {
+  int nprob = 0;
+  igg_dtype dtype = IGG_F32;
+  int device = 0;
+  int sm_count = 0;
+  std::vector<std::array<int, 3>> sizes;
+  std::vector<long long> offsets;
+  long long total = 0;
+  Coef *coef = nullptr;
+  bool have_coef = false;
+  int variant = 0, zb = 32, ctas_per_sm = 0;
+  Tile *tiles = nullptr;
+  int ntiles = 0;
+  cudaStream_t cap = nullptr;
+  std::map<std::tuple<const void *, const void *, const void *>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+void drop_graphs(igg_batch *b) {
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+int build_tiles(igg_batch *b) {
+  int tx = 32, ty = 8;
+  persistent_tile_shape(b->variant, &tx, &ty);
+  std::vector<Tile> v;
+  for (int p = 0; p < b->nprob; ++p) {
+    const int nx = b->sizes[p][0], ny = b->sizes[p][1], nz = b->sizes[p][2];
+    const int zb = b->zb > 0 ? b->zb : nz - 2;
+    for (int z = 1; z < nz - 1; z += zb)
+      for (int y = 1; y < ny - 1; y += ty)
+        for (int x = 1; x < nx - 1; x += tx) {
+          Tile t;
+          t.base = b->offsets[p];
+          t.nx = nx;
+          t.ny = ny;
+          t.x0 = x;
+          t.y0 = y;
+          t.xe = nx - 1;
+          t.ye = ny - 1;
+          t.z0 = z;
+          t.z1 = std::min(z + zb, nz - 1);
+          t.param = p;
+          t.pad = 0;
+          v.push_back(t);
+        }
+  }
+  cudaFree(b->tiles);
+  b->tiles = nullptr;
+  b->ntiles = (int)v.size();
+  cudaError_t e = cudaMalloc(&b->tiles, v.size() * sizeof(Tile));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(batch tiles)");
+  e = cudaMemcpy(b->tiles, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(batch tiles)");
+  drop_graphs(b);
+  return IGG_OK;
+}
+
+int check_fields(const igg_batch *b, const void *T2, const void *T, const void *Ci) {
+  for (const void *p : {T2, T, Ci}) {
+    if (!p) return set_error(IGG_EINVAL, "field pointer is NULL");
+    if ((uintptr_t)p & 15u) return set_error(IGG_EINVAL, "field pointer is not 16-byte aligned");
+  }
+  if (T2 == T || T2 == Ci) return set_error(IGG_EINVAL, "T2 aliases T or Ci");
+  if (!b->have_coef) return set_error(IGG_ESTATE, "igg_batch_set_coefs was not called");
+  return IGG_OK;
+}
+
+int enqueue(igg_batch *b, void *T2, const void *T, const void *Ci, cudaStream_t s) {
+  const int nctas = b->sm_count * b->ctas_per_sm;
+  cudaError_t e = launch_stencil_persistent(b->dtype, b->variant, b->tiles, b->ntiles, nctas, T2,
+                                            T, Ci, b->coef, s);
+  if (e != cudaSuccess) return cuda_error(e, "batched stencil launch");
+  return IGG_OK;
+}
+
+struct DevGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DevGuard(int d) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != d) changed = cudaSetDevice(d) == cudaSuccess;
+  }
+  ~DevGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int igg_batch_create(int nprob, const int *sizes, igg_dtype dt, igg_batch **out) {
+  clear_error();
+  if (!out) return set_error(IGG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nprob <= 0 || !sizes) return set_error(IGG_EINVAL, "need nprob > 0 and sizes");
+  if (dtype_size(dt) == 0) return set_error(IGG_EINVAL, "unknown dtype %d", (int)dt);
+  igg_batch *b = new (std::nothrow) igg_batch();
+  if (!b) return set_error(IGG_ENOMEM, "host allocation failed");
+  b->nprob = nprob;
+  b->dtype = dt;
+  const long long align = 256 / (long long)dtype_size(dt);
+  long long off = 0;
+  for (int p = 0; p < nprob; ++p) {
+    std::array<int, 3> n = {sizes[3 * p], sizes[3 * p + 1], sizes[3 * p + 2]};
+    for (int d = 0; d < 3; ++d)
+      if (n[d] < 3) {
+        delete b;
+        return set_error(IGG_EINVAL, "problem %d: size %d < 3 in dim %d", p, n[d], d);
+      }
+    b->sizes.push_back(n);
+    b->offsets.push_back(off);
+    off += (long long)n[0] * n[1] * n[2];
+    off = (off + align - 1) / align * align;
+  }
+  b->total = off;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->coef, nprob * sizeof(Coef));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(b->coef);
+    delete b;
+    return cuda_error(e, "batch set-up");
+  }
+  b->ctas_per_sm = max_ctas_per_sm(dt, 0);
+  if (int rc = build_tiles(b)) {
+    cudaFree(b->coef);
+    cudaStreamDestroy(b->cap);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return IGG_OK;
+}
+
+int igg_batch_destroy(igg_batch *b) {
+  clear_error();
+  if (!b) return IGG_OK;
+  DevGuard g(b->device);
+  cudaError_t e = cudaStreamSynchronize(b->cap);
+  drop_graphs(b);
+  cudaFree(b->tiles);
+  cudaFree(b->coef);
+  cudaStreamDestroy(b->cap);
+  delete b;
+  if (e != cudaSuccess) return cuda_error(e, "batch destroy");
+  return IGG_OK;
+}
+
+int igg_batch_layout(const igg_batch *b, long long *offsets, long long *total) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (offsets) std::memcpy(offsets, b->offsets.data(), b->nprob * sizeof(long long));
+  if (total) *total = b->total;
+  return IGG_OK;
+}
+
+int igg_batch_set_coefs(igg_batch *b, const double *lam, const double *dt, const double *dx,
+                        const double *dy, const double *dz) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (!lam || !dt || !dx || !dy || !dz) return set_error(IGG_EINVAL, "coefficient array is NULL");
+  std::vector<Coef> c(b->nprob);
+  for (int p = 0; p < b->nprob; ++p) {
+    if (!(dx[p] > 0) || !(dy[p] > 0) || !(dz[p] > 0))
+      return set_error(IGG_EINVAL, "problem %d: spacings must be positive", p);
+    c[p] = make_coef(lam[p], dt[p], dx[p], dy[p], dz[p]);
+  }
+  DevGuard g(b->device);
+  cudaError_t e = cudaMemcpy(b->coef, c.data(), c.size() * sizeof(Coef), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(batch coefficients)");
+  b->have_coef = true;
+  drop_graphs(b);
+  return IGG_OK;
+}
+
+int igg_batch_configure(igg_batch *b, int variant, int zb, int ctas_per_sm) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (variant < 0 || variant >= kPersistentVariants)
+    return set_error(IGG_EINVAL, "variant %d outside [0, %d)", variant, kPersistentVariants);
+  if (zb < 0) return set_error(IGG_EINVAL, "zb < 0");
+  DevGuard g(b->device);
+  const int cmax = max_ctas_per_sm(b->dtype, variant);
+  if (ctas_per_sm <= 0) ctas_per_sm = cmax;
+  if (ctas_per_sm > cmax)
+    return set_error(IGG_EINVAL, "ctas_per_sm %d above the resident maximum %d", ctas_per_sm, cmax);
+  b->variant = variant;
+  b->zb = zb;
+  b->ctas_per_sm = ctas_per_sm;
+  return build_tiles(b);
+}
+
+int igg_batch_get_config(const igg_batch *b, int cfg[3], int *ntiles) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (cfg) {
+    cfg[0] = b->variant;
+    cfg[1] = b->zb;
+    cfg[2] = b->ctas_per_sm;
+  }
+  if (ntiles) *ntiles = b->ntiles;
+  return IGG_OK;
+}
+
+int igg_batch_step(igg_batch *b, void *T2, const void *T, const void *Ci, void *stream) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (int rc = check_fields(b, T2, T, Ci)) return rc;
+  DevGuard g(b->device);
+  return enqueue(b, T2, T, Ci, (cudaStream_t)stream);
+}
+
+int igg_batch_run(igg_batch *b, int nt, void *T, void *T2, const void *Ci, void *stream) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (nt < 0) return set_error(IGG_EINVAL, "nt < 0");
+  if (int rc = check_fields(b, T2, T, Ci)) return rc;
+  if (T == Ci) return set_error(IGG_EINVAL, "T aliases Ci");
+  DevGuard g(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nt >= 2) {
+    auto key = std::make_tuple((const void *)T, (const void *)T2, Ci);
+    cudaGraphExec_t exec = nullptr;
+    auto it = b->graphs.find(key);
+    if (it != b->graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+      int rc = enqueue(b, T2, T, Ci, b->cap);
+      if (rc == IGG_OK) rc = enqueue(b, T, T2, Ci, b->cap);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(b->cap, &graph);
+      if (rc != IGG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiateWithFlags(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+      if (b->graphs.size() >= 8) {
+        cudaGraphExecDestroy(b->graphs.begin()->second);
+        b->graphs.erase(b->graphs.begin());
+      }
+      b->graphs.emplace(key, exec);
+    }
+    for (int i = 0; i < nt / 2; ++i) {
+      cudaError_t e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+    }
+  }
+  if (nt % 2) return enqueue(b, T2, T, Ci, s);
+  return IGG_OK;
+}
+
+int igg_batch_autotune(igg_batch *b, void *T2, const void *T, const void *Ci, int reps,
+                       void *stream, int best_cfg[3], float *best_ms) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (int rc = check_fields(b, T2, T, Ci)) return rc;
+  if (reps <= 0) reps = 3;
+  DevGuard g(b->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_error(e, "cudaEventCreate");
+  const int zbs[] = {8, 16, 32, 64, 0};
+  float best = 1e30f;
+  int bv = b->variant, bz = b->zb, bc = b->ctas_per_sm;
+  int rc = IGG_OK;
+  for (int v = 0; v < kPersistentVariants && rc == IGG_OK; ++v) {
+    const int cmax = max_ctas_per_sm(b->dtype, v);
+    const int cands[2] = {cmax, std::max(1, cmax / 2)};
+    for (int zb : zbs) {
+      for (int ci = 0; ci < (cmax > 1 ? 2 : 1); ++ci) {
+        b->variant = v;
+        b->zb = zb;
+        b->ctas_per_sm = cands[ci];
+        if ((rc = build_tiles(b)) != IGG_OK) break;
+        if ((rc = enqueue(b, T2, T, Ci, s)) != IGG_OK) break;  // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && rc == IGG_OK; ++r) rc = enqueue(b, T2, T, Ci, s);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          rc = cuda_error(e, "autotune timing");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best) {
+          best = ms;
+          bv = v;
+          bz = zb;
+          bc = cands[ci];
+        }
+      }
+      if (rc != IGG_OK) break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->variant = bv;
+  b->zb = bz;
+  b->ctas_per_sm = bc;
+  int rc2 = build_tiles(b);
+  if (rc != IGG_OK) return rc;
+  if (rc2 != IGG_OK) return rc2;
+  if (best_cfg) {
+    best_cfg[0] = bv;
+    best_cfg[1] = bz;
+    best_cfg[2] = bc;
+  }
+  if (best_ms) *best_ms = best;
+  return IGG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+int max_ctas_per_sm(igg_dtype dt, int variant) {
+  int n = persistent_occupancy(dt, variant);
+  return n > 0 ? n : 1;
+}
+}  // namespace

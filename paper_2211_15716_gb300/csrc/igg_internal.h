@@ -57,6 +57,16 @@ cudaError_t launch_stencil(igg_dtype dt, const Tile *tiles, int ntiles, void *T2
                            const void *T, const void *Ci, const Coef &c,
                            const Coef *table, cudaStream_t s);
 
+// Persistent tile-table kernel of the batched form: `variant` selects the
+// tile shape (persistent_tile_shape), nctas the number of CTAs that stride
+// over the tiles. table[tile.param] holds each tile's coefficients.
+constexpr int kPersistentVariants = 3;
+void persistent_tile_shape(int variant, int *tx, int *ty);
+int persistent_occupancy(igg_dtype dt, int variant);  // resident CTAs per SM (0 on error)
+cudaError_t launch_stencil_persistent(igg_dtype dt, int variant, const Tile *tiles, int ntiles,
+                                      int nctas, void *T2, const void *T, const void *Ci,
+                                      const Coef *table, cudaStream_t s);
+
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.
 cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,

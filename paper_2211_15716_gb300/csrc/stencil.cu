@@ -88,18 +88,18 @@ __device__ __forceinline__ float cell(float t, float xm, float xp, float ym,
   return __fmaf_rn(ci, l, t);
 }
 
+// Sweep one tile along z: every thread owns one (x, y) column of the tile,
+// keeps T at z-1, z, z+1 in registers and reads x/y neighbours through the
+// read-only cache.
 template <class S>
-__global__ void __launch_bounds__(kTileX *kTileY)
-    k_stencil_tiles(const Tile *__restrict__ tiles, S *__restrict__ T2,
-                    const S *__restrict__ T, const S *__restrict__ Ci, Coef c0,
-                    const Coef *__restrict__ table) {
+__device__ __forceinline__ void sweep_tile(const Tile &t, int tx, int ty, S *__restrict__ T2,
+                                           const S *__restrict__ T, const S *__restrict__ Ci,
+                                           const W<typename Num<S>::C> &w) {
   using N = Num<S>;
   using C = typename N::C;
-  const Tile t = tiles[blockIdx.x];
-  const int x = t.x0 + (int)threadIdx.x;
-  const int y = t.y0 + (int)threadIdx.y;
+  const int x = t.x0 + tx;
+  const int y = t.y0 + ty;
   if (x >= t.xe || y >= t.ye) return;
-  const W<C> w = make_w(table ? table[t.param] : c0, C(0));
   const long long sy = t.nx;
   const long long sz = (long long)t.nx * t.ny;
   long long p = t.base + x + sy * y + sz * (t.z0 - 1);
@@ -117,6 +117,57 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     zm = zc;
     zc = zp;
   }
+}
+
+// One CTA per tile.
+template <class S>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    k_stencil_tiles(const Tile *__restrict__ tiles, S *__restrict__ T2,
+                    const S *__restrict__ T, const S *__restrict__ Ci, Coef c0,
+                    const Coef *__restrict__ table) {
+  using C = typename Num<S>::C;
+  const Tile t = tiles[blockIdx.x];
+  const W<C> w = make_w(table ? table[t.param] : c0, C(0));
+  sweep_tile<S>(t, (int)threadIdx.x, (int)threadIdx.y, T2, T, Ci, w);
+}
+
+// Persistent form: a fixed grid of CTAs strides over the tile table (the
+// batched form's one launch per step). Tiles of TX x TY columns.
+template <class S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+    k_stencil_persistent(const Tile *__restrict__ tiles, int ntiles, S *__restrict__ T2,
+                         const S *__restrict__ T, const S *__restrict__ Ci,
+                         const Coef *__restrict__ table) {
+  using C = typename Num<S>::C;
+  const int tx = (int)(threadIdx.x % TX), ty = (int)(threadIdx.x / TX);
+  for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
+    const Tile t = tiles[i];
+    const W<C> w = make_w(table[t.param], C(0));
+    sweep_tile<S>(t, tx, ty, T2, T, Ci, w);
+  }
+}
+
+template <class S>
+cudaError_t launch_persistent_t(int variant, const Tile *tiles, int ntiles, int nctas, void *T2,
+                                const void *T, const void *Ci, const Coef *table,
+                                cudaStream_t s) {
+  switch (variant) {
+    case 0:
+      k_stencil_persistent<S, 32, 8><<<nctas, 256, 0, s>>>(tiles, ntiles, (S *)T2, (const S *)T,
+                                                          (const S *)Ci, table);
+      break;
+    case 1:
+      k_stencil_persistent<S, 32, 4><<<nctas, 128, 0, s>>>(tiles, ntiles, (S *)T2, (const S *)T,
+                                                          (const S *)Ci, table);
+      break;
+    case 2:
+      k_stencil_persistent<S, 64, 4><<<nctas, 256, 0, s>>>(tiles, ntiles, (S *)T2, (const S *)T,
+                                                          (const S *)Ci, table);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -144,6 +195,53 @@ cudaError_t launch_stencil(igg_dtype dt, const Tile *tiles, int ntiles, void *T2
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <class S>
+int occupancy_t(int variant) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (variant) {
+    case 0:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stencil_persistent<S, 32, 8>, 256, 0);
+      break;
+    case 1:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stencil_persistent<S, 32, 4>, 128, 0);
+      break;
+    case 2:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stencil_persistent<S, 64, 4>, 256, 0);
+      break;
+  }
+  return e == cudaSuccess ? n : 0;
+}
+
+int persistent_occupancy(igg_dtype dt, int variant) {
+  switch (dt) {
+    case IGG_F64: return occupancy_t<double>(variant);
+    case IGG_F32: return occupancy_t<float>(variant);
+    case IGG_BF16: return occupancy_t<__nv_bfloat16>(variant);
+  }
+  return 0;
+}
+
+void persistent_tile_shape(int variant, int *tx, int *ty) {
+  static const int shapes[kPersistentVariants][2] = {{32, 8}, {32, 4}, {64, 4}};
+  *tx = shapes[variant][0];
+  *ty = shapes[variant][1];
+}
+
+cudaError_t launch_stencil_persistent(igg_dtype dt, int variant, const Tile *tiles, int ntiles,
+                                      int nctas, void *T2, const void *T, const void *Ci,
+                                      const Coef *table, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (variant < 0 || variant >= kPersistentVariants || nctas <= 0) return cudaErrorInvalidValue;
+  switch (dt) {
+    case IGG_F64: return launch_persistent_t<double>(variant, tiles, ntiles, nctas, T2, T, Ci, table, s);
+    case IGG_F32: return launch_persistent_t<float>(variant, tiles, ntiles, nctas, T2, T, Ci, table, s);
+    case IGG_BF16:
+      return launch_persistent_t<__nv_bfloat16>(variant, tiles, ntiles, nctas, T2, T, Ci, table, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace igg

@@ -253,3 +253,113 @@ def reduce_noalloc(op: int, a: torch.Tensor, b: torch.Tensor | None = None,
         out = torch.empty(1, dtype=torch.float64, device=a.device)
     _check(fn(int(op), pa, pb, n, dtype_code(a.dtype), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+_batch_sigs_done = False
+
+
+def _batch_sigs():
+    global _batch_sigs_done
+    if _batch_sigs_done:
+        return lib()
+    L = lib()
+    P, I = ctypes.c_void_p, ctypes.c_int
+    IP = ctypes.POINTER(ctypes.c_int)
+    DP = ctypes.POINTER(ctypes.c_double)
+    LLP = ctypes.POINTER(ctypes.c_longlong)
+    L.igg_batch_create.argtypes = [I, IP, I, ctypes.POINTER(P)]
+    L.igg_batch_destroy.argtypes = [P]
+    L.igg_batch_layout.argtypes = [P, LLP, LLP]
+    L.igg_batch_set_coefs.argtypes = [P, DP, DP, DP, DP, DP]
+    L.igg_batch_configure.argtypes = [P, I, I, I]
+    L.igg_batch_get_config.argtypes = [P, IP, IP]
+    L.igg_batch_step.argtypes = [P, P, P, P, P]
+    L.igg_batch_run.argtypes = [P, I, P, P, P, P]
+    L.igg_batch_autotune.argtypes = [P, P, P, P, I, P, IP, ctypes.POINTER(ctypes.c_float)]
+    for n in ("igg_batch_create", "igg_batch_destroy", "igg_batch_layout", "igg_batch_set_coefs",
+              "igg_batch_configure", "igg_batch_get_config", "igg_batch_step", "igg_batch_run",
+              "igg_batch_autotune"):
+        getattr(L, n).restype = I
+    _batch_sigs_done = True
+    return L
+
+
+class Batch:
+    """Many independent problems of uneven sizes, packed in one buffer per
+    field (problem b at element offset offsets[b], shape (nz, ny, nx)),
+    advanced by one persistent launch per step."""
+
+    def __init__(self, sizes, dtype=torch.float32):
+        L = _batch_sigs()
+        self.sizes = [tuple(int(v) for v in s) for s in sizes]
+        self.dtype = dtype
+        flat = (ctypes.c_int * (3 * len(self.sizes)))(*[v for s in self.sizes for v in s])
+        h = ctypes.c_void_p()
+        _check(L.igg_batch_create(len(self.sizes), flat, dtype_code(dtype), ctypes.byref(h)))
+        self._h = h
+        offs = (ctypes.c_longlong * len(self.sizes))()
+        tot = ctypes.c_longlong()
+        _check(L.igg_batch_layout(h, offs, ctypes.byref(tot)))
+        self.offsets = list(offs)
+        self.total = tot.value
+
+    def destroy(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(_batch_sigs().igg_batch_destroy(h))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def empty(self, device="cuda"):
+        return torch.empty(self.total, dtype=self.dtype, device=device)
+
+    def view(self, field: torch.Tensor, b: int) -> torch.Tensor:
+        nx, ny, nz = self.sizes[b]
+        o = self.offsets[b]
+        return field[o:o + nx * ny * nz].view(nz, ny, nx)
+
+    def set_coefs(self, lam, dt, dx, dy, dz):
+        n = len(self.sizes)
+        arrs = [(ctypes.c_double * n)(*[float(v) for v in a]) for a in (lam, dt, dx, dy, dz)]
+        _check(_batch_sigs().igg_batch_set_coefs(self._h, *arrs))
+
+    def configure(self, variant=0, zb=32, ctas_per_sm=0):
+        _check(_batch_sigs().igg_batch_configure(self._h, int(variant), int(zb), int(ctas_per_sm)))
+
+    def config(self):
+        cfg = _ints((0, 0, 0))
+        nt = ctypes.c_int()
+        _check(_batch_sigs().igg_batch_get_config(self._h, cfg, ctypes.byref(nt)))
+        return {"variant": cfg[0], "zb": cfg[1], "ctas_per_sm": cfg[2], "ntiles": nt.value}
+
+    def _p(self, t, name):
+        return _ptr(t, self.total, self.dtype, name)
+
+    def step(self, T2, T, Ci, stream=None):
+        _check(_batch_sigs().igg_batch_step(self._h, self._p(T2, "T2"), self._p(T, "T"), self._p(Ci, "Ci"),
+                                            _stream(stream)))
+
+    def run(self, nt, T, T2, Ci, stream=None):
+        """nt steps (CUDA graph); returns T for even nt, T2 for odd nt."""
+        _check(_batch_sigs().igg_batch_run(self._h, int(nt), self._p(T, "T"), self._p(T2, "T2"),
+                                           self._p(Ci, "Ci"), _stream(stream)))
+        return T if nt % 2 == 0 else T2
+
+    def autotune(self, T2, T, Ci, reps=3, stream=None):
+        """Time every (tile shape, z depth, CTAs/SM) candidate on these fields
+        and keep the fastest. Writes T2's inner points; synchronises."""
+        cfg = _ints((0, 0, 0))
+        ms = ctypes.c_float()
+        _check(_batch_sigs().igg_batch_autotune(self._h, self._p(T2, "T2"), self._p(T, "T"), self._p(Ci, "Ci"),
+                                                int(reps), _stream(stream), cfg, ctypes.byref(ms)))
+        return {"variant": cfg[0], "zb": cfg[1], "ctas_per_sm": cfg[2], "ms": ms.value}

@@ -109,3 +109,28 @@ def setup(w: Workload, grid: Grid, Ci: torch.Tensor):
     dx, dy, dz = (spacing(w.l[d], ng[d]) for d in range(3))
     ci_max = float(reduce(RED_MAX, Ci).item())
     return dx, dy, dz, cfl_dt(dx, dy, dz, w.lam, ci_max)
+
+
+def batch_problems(seed=3, count=256, nmin=32, nmax=192):
+    """The batched workload: `count` problems with each dimension uniform on
+    {nmin..nmax}, lam ~ U[0.5, 2], constant Ci = 1/U[1.5, 2.5] per problem,
+    Gaussian-bump T0, per-problem dx = 1/(n-1) and dt by Fig. 1's rule."""
+    sizes, lam, ci = synth.batch_problems(seed, count, nmin, nmax)
+    dd = [[spacing(1.0, int(n)) for n in s] for s in sizes]
+    dt = [cfl_dt(*dd[b], float(lam[b]), float(ci[b])) for b in range(count)]
+    return [tuple(int(v) for v in s) for s in sizes], lam, ci, dd, dt
+
+
+def make_batch_fields(batch, ci, dtype=torch.float32):
+    """T (Gaussian bump per problem), T2 = copy(T) and Ci (constant per
+    problem) packed in the batch layout."""
+    T = batch.empty()
+    Ci = batch.empty()
+    T.zero_()
+    Ci.zero_()
+    for b, (nx, ny, nz) in enumerate(batch.sizes):
+        g = [np.arange(nx), np.arange(ny), np.arange(nz)]
+        t0 = np.broadcast_to(synth.gaussian_bump(*g, (nx, ny, nz)), (nz, ny, nx))
+        _to_device(t0, dtype, batch.view(T, b))
+        _to_device(np.full((nz, ny, nx), float(ci[b])), dtype, batch.view(Ci, b))
+    return T, T.clone(), Ci
