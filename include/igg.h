@@ -223,6 +223,62 @@ int igg_batch_autotune(igg_batch *batch, void *T2, const void *T,
                        float *best_ms);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint form: gradients of a function J(T_nt) of the state after nt steps
+ * of Fig. 1's loop with respect to Ci and to the initial state T_0 (the
+ * differentiated solver; dt is held fixed). Grids with ONE non-periodic
+ * subdomain; F64 or F32 fields; the Ci gradient is accumulated in FP64.
+ *
+ * Forward step on inner points p: T_{n+1}[p] = T_n[p] + Ci[p]*l(T_n)[p],
+ * l(T)[p] = sum_d w_d (T[p-e_d] + T[p+e_d] - 2 T[p]), w_d = dt*lam/dd^2;
+ * boundary points are unchanged.
+ * ------------------------------------------------------------------------- */
+
+/* One backward step. lam_in = dJ/dT_{n+1}; writes lam_out = dJ/dT_n on
+ * every point:
+ *   v = Ci*lam_in on inner points, 0 elsewhere,
+ *   lam_out[q] = lam_in[q] + sum_d w_d (v[q-e_d] + v[q+e_d] - 2 v[q])
+ * (neighbours outside the array count as 0), and accumulates
+ *   gCi[p] += lam_in[p] * l(T_n)[p] on inner points p (gCi: FP64 array).
+ * lam_out must not alias lam_in. */
+int igg_adjoint_step(igg_grid *grid, void *lam_out, const void *lam_in,
+                     const void *T_n, const void *Ci, double *gCi,
+                     igg_dtype dtype, double lam, double dt, double dx,
+                     double dy, double dz, void *stream);
+
+/* Number of checkpoints of an nt-step run with one checkpoint every `every`
+ * steps: the states T_0, T_every, T_2every, ... before step nt, i.e.
+ * ceil(nt/every). Returns the count (> 0) or IGG_EINVAL. */
+int igg_checkpoint_slots(int nt, int every);
+
+/* Forward run that keeps checkpoints: nt steps from T0 (boundary values of
+ * T0 stay fixed), storing state T_{k*every} in slot k of `ckpt`
+ * (igg_checkpoint_slots fields, contiguous) and T_nt in T_out. `work` holds
+ * two fields (scratch of the caller). */
+int igg_forward_checkpointed(igg_grid *grid, int nt, int every, const void *T0,
+                             const void *Ci, igg_dtype dtype, double lam,
+                             double dt, double dx, double dy, double dz,
+                             void *ckpt, void *work, void *T_out, void *stream);
+
+/* Backward run: from lam_nt = dJ/dT_nt and the checkpoints of
+ * igg_forward_checkpointed, recomputes each segment of `every` states from
+ * its checkpoint (into `seg`, every-1 fields; unused when every == 1) and
+ * runs the adjoint steps backward in time. Writes gT0 = dJ/dT_0 (dtype
+ * field) and gCi = dJ/dCi (FP64 field, overwritten). `work` holds two fields.
+ * Memory: (ceil(nt/every) + every + 3) fields instead of nt + 1. */
+int igg_adjoint_checkpointed(igg_grid *grid, int nt, int every,
+                             const void *ckpt, const void *Ci,
+                             const void *lam_nt, igg_dtype dtype, double lam,
+                             double dt, double dx, double dy, double dz,
+                             void *seg, void *work, void *gT0, double *gCi,
+                             void *stream);
+
+/* out = a - b over n elements (F64 or F32): the gradient T_nt - T_obs of the
+ * misfit 0.5*sum((T_nt - T_obs)^2), whose value is 0.5*igg_reduce(
+ * IGG_RED_SUM_SQDIFF, T_nt, T_obs). out may alias a. */
+int igg_residual(void *out, const void *a, const void *b, size_t n,
+                 igg_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------------------
  * FP64 reductions over n elements of device arrays of `dtype` (used for
  * Fig. 1's maximum(Ci) in the time-step rule and for the checks and the
  * misfit loss):

@@ -73,6 +73,13 @@ cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
                         void *field, int na, int nb, long long sa, long long sb,
                         cudaStream_t s);
 
+// Adjoint step over every point of one array, and out = a - b elementwise.
+cudaError_t launch_adjoint(igg_dtype dt, int nx, int ny, int nz, void *lam_out,
+                           const void *lam_in, const void *Tn, const void *Ci, double *gCi,
+                           const Coef &c, cudaStream_t s);
+cudaError_t launch_sub(igg_dtype dt, long long n, void *out, const void *a, const void *b,
+                       cudaStream_t s);
+
 cudaError_t launch_reduce(int op, const void *a, const void *b, size_t n,
                           igg_dtype dt, double *scratch, int nblocks,
                           double *out, cudaStream_t s);

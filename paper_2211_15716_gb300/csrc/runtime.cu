@@ -665,4 +665,132 @@ int igg_reduce(int op, const void *a, const void *b, size_t n, igg_dtype dt, dou
   return IGG_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint (differentiated Fig. 1 loop) on a single-subdomain, non-periodic
+// grid; drivers with checkpoints every `every` steps.
+// ---------------------------------------------------------------------------
+static int check_adjoint_grid(const igg_grid *g, igg_dtype dt) {
+  if (g->nsub != 1 || g->periods[0] || g->periods[1] || g->periods[2])
+    return set_error(IGG_EINVAL, "the adjoint needs a single non-periodic subdomain");
+  if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "adjoint dtype must be F64 or F32");
+  return IGG_OK;
+}
+
+int igg_checkpoint_slots(int nt, int every) {
+  clear_error();
+  if (nt < 1 || every < 1) return set_error(IGG_EINVAL, "need nt >= 1 and every >= 1");
+  return (nt + every - 1) / every;
+}
+
+int igg_adjoint_step(igg_grid *g, void *lam_out, const void *lam_in, const void *Tn,
+                     const void *Ci, double *gCi, igg_dtype dt, double lam, double dtime,
+                     double dx, double dy, double dz, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_adjoint_grid(g, dt)) return rc;
+  for (const void *p : {(const void *)lam_out, lam_in, Tn, Ci, (const void *)gCi})
+    if (int rc = check_field(g, p, "field")) return rc;
+  if (lam_out == lam_in) return set_error(IGG_EINVAL, "lam_out aliases lam_in");
+  if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
+  DeviceGuard dg(g->device);
+  cudaError_t e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], lam_out, lam_in, Tn, Ci, gCi,
+                                 make_coef(lam, dtime, dx, dy, dz), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
+  return IGG_OK;
+}
+
+int igg_residual(void *out, const void *a, const void *b, size_t n, igg_dtype dt, void *stream) {
+  clear_error();
+  if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "dtype must be F64 or F32");
+  if (n > 0 && (!out || !a || !b)) return set_error(IGG_EINVAL, "NULL pointer");
+  if (n == 0) return IGG_OK;
+  cudaError_t e = launch_sub(dt, (long long)n, out, a, b, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "residual launch");
+  return IGG_OK;
+}
+
+int igg_forward_checkpointed(igg_grid *g, int nt, int every, const void *T0, const void *Ci,
+                             igg_dtype dt, double lam, double dtime, double dx, double dy,
+                             double dz, void *ckpt, void *work, void *T_out, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_adjoint_grid(g, dt)) return rc;
+  const int nslots = igg_checkpoint_slots(nt, every);
+  if (nslots < 0) return nslots;
+  for (const void *p : {T0, Ci, (const void *)ckpt, (const void *)work, (const void *)T_out})
+    if (int rc = check_field(g, p, "field")) return rc;
+  if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t es = dtype_size(dt), bytes = (size_t)g->nloc * es;
+  char *A = (char *)work, *B = (char *)work + bytes, *K = (char *)ckpt;
+  const Coef c = make_coef(lam, dtime, dx, dy, dz);
+  cudaError_t e = cudaMemcpyAsync(A, T0, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B, T0, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(K, T0, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "checkpoint copy");
+  char *cur = A;
+  for (int n = 0; n < nt; ++n) {
+    char *nxt = cur == A ? B : A;
+    if (int rc = enqueue_step(g, nullptr, nxt, cur, Ci, dt, c, false, s)) return rc;
+    cur = nxt;
+    if ((n + 1) % every == 0 && n + 1 < nt) {
+      e = cudaMemcpyAsync(K + (size_t)((n + 1) / every) * bytes, cur, bytes,
+                          cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return cuda_error(e, "checkpoint copy");
+    }
+  }
+  e = cudaMemcpyAsync(T_out, cur, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "result copy");
+  return IGG_OK;
+}
+
+int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, const void *Ci,
+                             const void *lam_nt, igg_dtype dt, double lam, double dtime,
+                             double dx, double dy, double dz, void *seg, void *work, void *gT0,
+                             double *gCi, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_adjoint_grid(g, dt)) return rc;
+  const int nslots = igg_checkpoint_slots(nt, every);
+  if (nslots < 0) return nslots;
+  for (const void *p : {ckpt, Ci, lam_nt, (const void *)work, (const void *)gT0, (const void *)gCi})
+    if (int rc = check_field(g, p, "field")) return rc;
+  if (every > 1)
+    if (int rc = check_field(g, seg, "seg")) return rc;
+  if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t es = dtype_size(dt), bytes = (size_t)g->nloc * es;
+  const char *K = (const char *)ckpt;
+  char *S = (char *)seg, *LA = (char *)work, *LB = (char *)work + bytes;
+  const Coef c = make_coef(lam, dtime, dx, dy, dz);
+  cudaError_t e = cudaMemcpyAsync(LA, lam_nt, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(gCi, 0, (size_t)g->nloc * sizeof(double), s);
+  // segment buffers carry the fixed boundary values of T0 (steps write inner points only)
+  for (int j = 1; j < every && e == cudaSuccess; ++j)
+    e = cudaMemcpyAsync(S + (size_t)(j - 1) * bytes, K, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "adjoint set-up copies");
+  char *cur = LA;
+  for (int k = nslots - 1; k >= 0; --k) {
+    const int s0 = k * every, s1 = std::min(s0 + every, nt), len = s1 - s0;
+    auto state = [&](int j) -> const char * {
+      return j == 0 ? K + (size_t)k * bytes : S + (size_t)(j - 1) * bytes;
+    };
+    for (int j = 1; j < len; ++j)
+      if (int rc = enqueue_step(g, nullptr, (void *)state(j), state(j - 1), Ci, dt, c, false, s))
+        return rc;
+    for (int j = len - 1; j >= 0; --j) {
+      char *nxt = cur == LA ? LB : LA;
+      e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], nxt, cur, state(j), Ci, gCi, c, s);
+      if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
+      cur = nxt;
+    }
+  }
+  e = cudaMemcpyAsync(gT0, cur, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "gradient copy");
+  return IGG_OK;
+}
+
 }  // extern "C"

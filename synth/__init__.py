@@ -130,6 +130,21 @@ def sine_modes(seed, gx, gy, gz, n_g, l=(1.0, 1.0, 1.0), base=1.7, amp=0.1,
     return out
 
 
+def ci_smooth(seed, gx, gy, gz, n_g, l=(1.0, 1.0, 1.0), mean=0.53, amp=0.2, modes=4,
+              lo=0.4, hi=0.667, stream=13):
+    """A smooth random heat-capacity field (the hidden Ci* of the inverse
+    problem): mean * (1 + amp * sum_j a_j prod_d sin(pi m_jd x_d)), a_j ~
+    U[-1, 1], m_jd in {1, 2, 3}, clipped to [lo, hi]; float64 [z][y][x]."""
+    x, y, z = _coords(gx, gy, gz, n_g, l)
+    u = uniform(seed, stream, np.arange(4 * modes, dtype=np.uint64)).reshape(modes, 4)
+    acc = np.zeros(np.broadcast_shapes(x.shape, y.shape, z.shape))
+    for a, mx, my, mz in u:
+        m = [1 + int(v * 3) for v in (mx, my, mz)]
+        acc = acc + (2 * a - 1) * (np.sin(np.pi * m[0] * x / l[0]) * np.sin(np.pi * m[1] * y / l[1])
+                                   * np.sin(np.pi * m[2] * z / l[2]))
+    return np.clip(mean * (1 + amp * acc), lo, hi)
+
+
 def batch_problems(seed, count=256, nmin=32, nmax=192, stream=11):
     """Independent problems of uneven sizes: per problem (nx, ny, nz) with each
     dimension iid uniform on {nmin..nmax}, lam ~ U[0.5, 2] and a constant
