@@ -71,7 +71,7 @@ int build_tiles(igg_batch *b) {
           t.z0 = z;
           t.z1 = std::min(z + zb, nz - 1);
           t.param = p;
-          t.pad = 0;
+          t.xb = x;
           v.push_back(t);
         }
   }

@@ -15,13 +15,16 @@ namespace igg {
 // over z0 <= z < z1. All indices are local to the array; `base` is the
 // element offset of the array inside the field buffer. Every point of a tile
 // is an inner point of its array.
+// In the vector kernels x0 is the (16-byte aligned) first point of lane 0's
+// vector and the tile computes the points xb <= x < xe; in the scalar kernels
+// xb = x0.
 struct Tile {
   long long base;
   int nx, ny;
   int x0, y0, xe, ye;
   int z0, z1;
   int param;  // row of the coefficient table (batched form), else 0
-  int pad;
+  int xb;
 };
 static_assert(sizeof(Tile) == 48, "Tile layout");
 
@@ -56,6 +59,16 @@ size_t dtype_size(igg_dtype t);
 cudaError_t launch_stencil(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
                            const void *T, const void *Ci, const Coef &c,
                            const Coef *table, cudaStream_t s);
+
+// Vector form: 16-byte loads of V = 16/sizeof(element) points along x per
+// thread, one warp per row of a tile of 32*V x kVecRows points; needs rows
+// whose length is a multiple of V (16-byte aligned rows). Tiles from
+// vec_tiles-style tables (x0 aligned to V).
+constexpr int kVecRows = 8;
+int vec_width(igg_dtype dt);  // V
+cudaError_t launch_stencil_vec(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
+                               const void *T, const void *Ci, const Coef &c,
+                               const Coef *table, cudaStream_t s);
 
 // Persistent tile-table kernel of the batched form: `variant` selects the
 // tile shape (persistent_tile_shape), nctas the number of CTAs that stride

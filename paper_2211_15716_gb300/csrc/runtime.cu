@@ -154,9 +154,41 @@ void add_box(std::vector<Tile> &v, long long base, int nx, int ny, int x0, int x
         t.z0 = zc;
         t.z1 = std::min(zc + zb, z1);
         t.param = param;
-        t.pad = 0;
+        t.xb = x;
         v.push_back(t);
       }
+}
+
+// Tiles of the vector kernel: lane 0 of a tile starts at an x multiple of V,
+// the tile computes xb <= x < xe, one warp per row (kVecRows rows).
+void add_box_vec(std::vector<Tile> &v, long long base, int nx, int ny, int x0, int x1, int y0,
+                 int y1, int z0, int z1, int zb, int param, int V) {
+  if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;
+  const int span = 32 * V;
+  for (int zc = z0; zc < z1; zc += zb)
+    for (int y = y0; y < y1; y += kVecRows)
+      for (int xa = (x0 / V) * V; xa < x1; xa += span) {
+        Tile t;
+        t.base = base;
+        t.nx = nx;
+        t.ny = ny;
+        t.x0 = xa;
+        t.y0 = y;
+        t.xb = std::max(x0, xa);
+        t.xe = std::min(x1, xa + span);
+        t.ye = y1;
+        t.z0 = zc;
+        t.z1 = std::min(zc + zb, z1);
+        t.param = param;
+        v.push_back(t);
+      }
+}
+
+// one entry point for both tile kinds (V = 1: scalar kernel tiles)
+void add_tiles(std::vector<Tile> &v, int V, long long base, int nx, int ny, int x0, int x1,
+               int y0, int y1, int z0, int z1, int zb, int param) {
+  if (V > 1) add_box_vec(v, base, nx, ny, x0, x1, y0, y1, z0, z1, zb, param, V);
+  else add_box(v, base, nx, ny, x0, x1, y0, y1, z0, z1, zb, param);
 }
 
 long long xy_tiles_of(int x0, int x1, int y0, int y1) {
@@ -188,8 +220,8 @@ struct igg_grid {
   std::vector<int> left, right;  // [nsub*3]
   cudaStream_t hi = nullptr, lo = nullptr, cap = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
-  TileSet full;
-  std::map<std::array<int, 3>, SplitTiles> split;
+  std::map<int, TileSet> full;                     // keyed by V (1 = scalar tiles)
+  std::map<std::array<int, 4>, SplitTiles> split;  // keyed by widths and V
   PlaneCopy *copies[3] = {nullptr, nullptr, nullptr};
   int ncopies[3] = {0, 0, 0};
   std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -221,20 +253,34 @@ int check_coef(double lam, double dt, double dx, double dy, double dz) {
   return IGG_OK;
 }
 
-// Tiles of one box per subdomain, for the full step or a split part.
-int build_full_tiles(igg_grid *g) {
-  if (g->full.dev || g->full.n) return IGG_OK;
+// Vector width used for dtype dt on this grid (1 = scalar kernel): the
+// 16-byte vector kernel needs rows of a multiple of V points.
+int grid_vec(const igg_grid *g, igg_dtype dt) {
+  const int V = vec_width(dt);
+  return (V > 1 && g->n[0] % V == 0) ? V : 1;
+}
+
+// Tiles of one box per subdomain, for the full step.
+int build_full_tiles(igg_grid *g, int V, TileSet **out) {
+  auto it = g->full.find(V);
+  if (it != g->full.end()) {
+    *out = &it->second;
+    return IGG_OK;
+  }
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   const long long xy = xy_tiles_of(1, nx - 1, 1, ny - 1) * g->nsub;
   const int zb = choose_zb(xy, nz - 2);
   std::vector<Tile> v;
   for (int s = 0; s < g->nsub; ++s)
-    add_box(v, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
-  return upload_tiles(v, &g->full);
+    add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
+  TileSet ts;
+  if (int rc = upload_tiles(v, &ts)) return rc;
+  *out = &g->full.emplace(V, ts).first->second;
+  return IGG_OK;
 }
 
-int build_split_tiles(igg_grid *g, const int w[3], SplitTiles **out) {
-  std::array<int, 3> key = {w[0], w[1], w[2]};
+int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
+  std::array<int, 4> key = {w[0], w[1], w[2], V};
   auto it = g->split.find(key);
   if (it != g->split.end()) {
     *out = &it->second;
@@ -260,13 +306,13 @@ int build_split_tiles(igg_grid *g, const int w[3], SplitTiles **out) {
   const int zb_i = choose_zb(xy_i * g->nsub, zh - zl > 0 ? zh - zl : 1);
   for (int s = 0; s < g->nsub; ++s) {
     const long long base = (long long)s * g->nloc;
-    add_box(vb, base, nx, ny, 1, nx - 1, 1, ny - 1, 1, zl, 64, 0);          // z low
-    add_box(vb, base, nx, ny, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, 0);     // z high
-    add_box(vb, base, nx, ny, 1, nx - 1, 1, yl, zl, zh, zb_b, 0);           // y low
-    add_box(vb, base, nx, ny, 1, nx - 1, yh, ny - 1, zl, zh, zb_b, 0);      // y high
-    add_box(vb, base, nx, ny, 1, xl, yl, yh, zl, zh, zb_b, 0);              // x low
-    add_box(vb, base, nx, ny, xh, nx - 1, yl, yh, zl, zh, zb_b, 0);         // x high
-    add_box(vi, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);             // inner block
+    add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, ny - 1, 1, zl, 64, 0);          // z low
+    add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, 0);     // z high
+    add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, yl, zl, zh, zb_b, 0);           // y low
+    add_tiles(vb, V, base, nx, ny, 1, nx - 1, yh, ny - 1, zl, zh, zb_b, 0);      // y high
+    add_tiles(vb, V, base, nx, ny, 1, xl, yl, yh, zl, zh, zb_b, 0);              // x low
+    add_tiles(vb, V, base, nx, ny, xh, nx - 1, yl, yh, zl, zh, zb_b, 0);         // x high
+    add_tiles(vi, V, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);             // inner block
   }
   SplitTiles st;
   int rc = upload_tiles(vb, &st.boundary);
@@ -279,6 +325,12 @@ int build_split_tiles(igg_grid *g, const int w[3], SplitTiles **out) {
   auto res = g->split.emplace(key, st);
   *out = &res.first->second;
   return IGG_OK;
+}
+
+cudaError_t launch_tiles(int V, igg_dtype dt, const TileSet &ts, void *T2, const void *T,
+                         const void *Ci, const Coef &c, cudaStream_t s) {
+  if (V > 1) return launch_stencil_vec(dt, ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
+  return launch_stencil(dt, ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
 
 // Plane-copy tables of the halo update, one per dimension.
@@ -324,8 +376,11 @@ bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->nco
 int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const void *Ci,
                  igg_dtype dt, const Coef &c, bool with_halo, cudaStream_t s) {
   cudaError_t e;
+  const int V = grid_vec(g, dt);
   if (!widths) {
-    e = launch_stencil(dt, g->full.dev, g->full.n, T2, T, Ci, c, nullptr, s);
+    TileSet *full = nullptr;
+    if (int rc = build_full_tiles(g, V, &full)) return rc;
+    e = launch_tiles(V, dt, *full, T2, T, Ci, c, s);
     if (e != cudaSuccess) return cuda_error(e, "stencil launch");
     if (with_halo && any_halo(g)) {
       e = enqueue_halo(g, T2, dtype_size(dt), s);
@@ -334,15 +389,15 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
     return IGG_OK;
   }
   SplitTiles *st = nullptr;
-  int rc = build_split_tiles(g, widths, &st);
+  int rc = build_split_tiles(g, widths, V, &st);
   if (rc != IGG_OK) return rc;
   if ((e = cudaEventRecord(g->ev_fork, s)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(g->hi, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
   if ((e = cudaStreamWaitEvent(g->lo, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
-  e = launch_stencil(dt, st->boundary.dev, st->boundary.n, T2, T, Ci, c, nullptr, g->hi);
+  e = launch_tiles(V, dt, st->boundary, T2, T, Ci, c, g->hi);
   if (e == cudaSuccess && any_halo(g)) e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
   if (e != cudaSuccess) return cuda_error(e, "boundary/halo launch");
-  e = launch_stencil(dt, st->inner.dev, st->inner.n, T2, T, Ci, c, nullptr, g->lo);
+  e = launch_tiles(V, dt, st->inner, T2, T, Ci, c, g->lo);
   if (e != cudaSuccess) return cuda_error(e, "inner launch");
   if ((e = cudaEventRecord(g->ev_hi, g->hi)) != cudaSuccess) return cuda_error(e, "record");
   if ((e = cudaEventRecord(g->ev_lo, g->lo)) != cudaSuccess) return cuda_error(e, "record");
@@ -368,7 +423,7 @@ void destroy_grid(igg_grid *g) {
     cudaFree(kv.second.boundary.dev);
     cudaFree(kv.second.inner.dev);
   }
-  cudaFree(g->full.dev);
+  for (auto &kv : g->full) cudaFree(kv.second.dev);
   for (int d = 0; d < 3; ++d) cudaFree(g->copies[d]);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_hi) cudaEventDestroy(g->ev_hi);
@@ -472,7 +527,6 @@ int igg_init_global_grid(int nx, int ny, int nz, const int dims_in[3], int nsub,
     return cuda_error(e, "stream/event creation");
   }
   int rc = build_halo_tables(g);
-  if (rc == IGG_OK) rc = build_full_tiles(g);
   if (rc != IGG_OK) {
     destroy_grid(g);
     return rc;
@@ -600,10 +654,14 @@ int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const v
   if (nt == 0) return IGG_OK;
   cudaGraphExec_t exec = nullptr;
   if (nt >= 2) {
-    SplitTiles *st = nullptr;
+    // tile tables are allocated before the capture starts
+    const int V = grid_vec(g, dt);
     if (widths) {
-      int rc = build_split_tiles(g, widths, &st);  // before capture: allocates
-      if (rc != IGG_OK) return rc;
+      SplitTiles *st = nullptr;
+      if (int rc = build_split_tiles(g, widths, V, &st)) return rc;
+    } else {
+      TileSet *full = nullptr;
+      if (int rc = build_full_tiles(g, V, &full)) return rc;
     }
     const GraphKey key(T, T2, Ci, (int)dt, widths ? 1 : 0, widths ? widths[0] : 0,
                        widths ? widths[1] : 0, widths ? widths[2] : 0, c.wx, c.wy, c.wz, c.wc);

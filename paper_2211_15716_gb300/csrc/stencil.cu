@@ -170,6 +170,139 @@ cudaError_t launch_persistent_t(int variant, const Tile *tiles, int ntiles, int 
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Vector form. One warp per tile row; lane l holds the V = 16/sizeof(S)
+// points x0 + l*V .. x0 + l*V + V-1 of that row as one 16-byte vector and
+// keeps the planes z-1, z, z+1 of its vector in registers. x neighbours come
+// from the neighbouring lane by shuffle (lanes 0 and 31 load the one point
+// beyond the warp), y neighbours are 16-byte loads of the rows above and
+// below (cache hits: the neighbouring warps load those rows as their own).
+// Only points with xb <= x < xe are written; a vector with every point
+// inside is stored whole, otherwise point by point.
+// ---------------------------------------------------------------------------
+template <class S>
+struct Vec {
+  static constexpr int V = 16 / (int)sizeof(S);
+  using C = typename Num<S>::C;
+  C v[V];
+};
+
+__device__ __forceinline__ void unpack(const uint4 &r, Vec<double> &o) {
+  o.v[0] = __hiloint2double((int)r.y, (int)r.x);
+  o.v[1] = __hiloint2double((int)r.w, (int)r.z);
+}
+__device__ __forceinline__ uint4 pack(const Vec<double> &o) {
+  uint4 r;
+  r.x = (unsigned)__double2loint(o.v[0]);
+  r.y = (unsigned)__double2hiint(o.v[0]);
+  r.z = (unsigned)__double2loint(o.v[1]);
+  r.w = (unsigned)__double2hiint(o.v[1]);
+  return r;
+}
+__device__ __forceinline__ void unpack(const uint4 &r, Vec<float> &o) {
+  o.v[0] = __uint_as_float(r.x);
+  o.v[1] = __uint_as_float(r.y);
+  o.v[2] = __uint_as_float(r.z);
+  o.v[3] = __uint_as_float(r.w);
+}
+__device__ __forceinline__ uint4 pack(const Vec<float> &o) {
+  return make_uint4(__float_as_uint(o.v[0]), __float_as_uint(o.v[1]), __float_as_uint(o.v[2]),
+                    __float_as_uint(o.v[3]));
+}
+// BF16 -> FP32 is exact: the 16 bits become the upper half of the float.
+__device__ __forceinline__ void unpack(const uint4 &r, Vec<__nv_bfloat16> &o) {
+  const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    o.v[2 * i] = __uint_as_float(w[i] << 16);
+    o.v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+__device__ __forceinline__ unsigned short bf16_bits(float f) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+__device__ __forceinline__ uint4 pack(const Vec<__nv_bfloat16> &o) {
+  unsigned w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    w[i] = (unsigned)bf16_bits(o.v[2 * i]) | ((unsigned)bf16_bits(o.v[2 * i + 1]) << 16);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <class S>
+__device__ __forceinline__ void ldvec(const S *p, Vec<S> &o) {
+  unpack(__ldg(reinterpret_cast<const uint4 *>(p)), o);
+}
+
+template <class S>
+__device__ __forceinline__ typename Num<S>::C ld1(const S *p) {
+  return Num<S>::ld(p);
+}
+
+template <class S>
+__global__ void __launch_bounds__(32 * kVecRows)
+    k_stencil_vec(const Tile *__restrict__ tiles, S *__restrict__ T2, const S *__restrict__ T,
+                  const S *__restrict__ Ci, Coef c0, const Coef *__restrict__ table) {
+  using C = typename Num<S>::C;
+  constexpr int V = Vec<S>::V;
+  const Tile t = tiles[blockIdx.x];
+  const W<C> w = make_w(table ? table[t.param] : c0, C(0));
+  const int lane = threadIdx.x & 31;
+  const int y = t.y0 + (int)(threadIdx.x >> 5);
+  if (y >= t.ye) return;  // whole warp leaves together
+  const int xs = t.x0 + lane * V;
+  // this lane's vector is needed if it overlaps [xb - 1, xe + 1) inside the row
+  const bool need = xs < t.nx && xs + V > t.xb - 1 && xs < t.xe + 1;
+  const bool comp = xs + V > t.xb && xs < t.xe;  // has points to compute
+  const long long sy = t.nx;
+  const long long sz = (long long)t.nx * t.ny;
+  long long p = t.base + xs + sy * y + sz * (t.z0 - 1);
+  Vec<S> zm, zc, zp, ym, yp, ci;
+#pragma unroll
+  for (int i = 0; i < V; ++i) zm.v[i] = zc.v[i] = zp.v[i] = C(0);
+  if (need) {
+    ldvec(T + p, zm);
+    ldvec(T + p + sz, zc);
+  }
+  const bool left_ld = lane == 0 && comp && xs > 0;
+  const bool right_ld = lane == 31 && comp && xs + V < t.nx;
+  for (int z = t.z0; z < t.z1; ++z) {
+    p += sz;
+    if (need) ldvec(T + p + sz, zp);
+    if (comp) {
+      ldvec(T + p - sy, ym);
+      ldvec(T + p + sy, yp);
+      ldvec(Ci + p, ci);
+    }
+    C left = __shfl_up_sync(0xffffffffu, zc.v[V - 1], 1);
+    C right = __shfl_down_sync(0xffffffffu, zc.v[0], 1);
+    if (left_ld) left = ld1(T + p - 1);
+    if (right_ld) right = ld1(T + p + V);
+    if (comp) {
+      Vec<S> out;
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const C xm = i == 0 ? left : zc.v[i - 1];
+        const C xp = i == V - 1 ? right : zc.v[i + 1];
+        out.v[i] = cell(zc.v[i], xm, xp, ym.v[i], yp.v[i], zm.v[i], zp.v[i], ci.v[i], w);
+      }
+      if (xs >= t.xb && xs + V <= t.xe) {
+        *reinterpret_cast<uint4 *>(T2 + p) = pack(out);
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          if (xs + i >= t.xb && xs + i < t.xe) Num<S>::st(T2 + p + i, out.v[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+      zm.v[i] = zc.v[i];
+      zc.v[i] = zp.v[i];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_stencil(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
@@ -222,6 +355,35 @@ int persistent_occupancy(igg_dtype dt, int variant) {
     case IGG_BF16: return occupancy_t<__nv_bfloat16>(variant);
   }
   return 0;
+}
+
+int vec_width(igg_dtype dt) {
+  const size_t s = dtype_size(dt);
+  return s ? (int)(16 / s) : 0;
+}
+
+cudaError_t launch_stencil_vec(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
+                               const void *T, const void *Ci, const Coef &c,
+                               const Coef *table, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (dt) {
+    case IGG_F64:
+      k_stencil_vec<double><<<ntiles, 32 * kVecRows, 0, s>>>(
+          tiles, (double *)T2, (const double *)T, (const double *)Ci, c, table);
+      break;
+    case IGG_F32:
+      k_stencil_vec<float><<<ntiles, 32 * kVecRows, 0, s>>>(
+          tiles, (float *)T2, (const float *)T, (const float *)Ci, c, table);
+      break;
+    case IGG_BF16:
+      k_stencil_vec<__nv_bfloat16><<<ntiles, 32 * kVecRows, 0, s>>>(
+          tiles, (__nv_bfloat16 *)T2, (const __nv_bfloat16 *)T, (const __nv_bfloat16 *)Ci, c,
+          table);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 void persistent_tile_shape(int variant, int *tx, int *ty) {
