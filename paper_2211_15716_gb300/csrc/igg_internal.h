@@ -60,13 +60,28 @@ cudaError_t launch_stencil(igg_dtype dt, const Tile *tiles, int ntiles, void *T2
                            const void *T, const void *Ci, const Coef &c,
                            const Coef *table, cudaStream_t s);
 
-// Vector form: 16-byte loads of V = 16/sizeof(element) points along x per
-// thread, one warp per row of a tile of 32*V x kVecRows points; needs rows
-// whose length is a multiple of V (16-byte aligned rows). Tiles from
-// vec_tiles-style tables (x0 aligned to V).
-constexpr int kVecRows = 8;
+// Tile of the vector kernel. Each thread holds V = 16/sizeof(element)
+// consecutive points of a row as one 16-byte vector; a row of the tile is a
+// segment of lpr = 2^lpr_log2 lanes (lpr*V points), a warp holds 32/lpr rows
+// and a CTA kVecWarps warps. Rows are the index r of stride `sr` elements and
+// the tile marches over the index m of stride `sm`: rows along y and march
+// along z normally, or (swap = 1) rows along z and march along y for boxes
+// thin in y. The tile computes the points xb <= x < xe, rows r0 <= r < re,
+// marching m0 <= m < m1; lane 0 of a row starts at x0 (a multiple of V).
+struct VTile {
+  long long base;
+  long long sr, sm;
+  int nx;
+  int x0, xb, xe;
+  int r0, re;
+  int m0, m1;
+  int param;
+  unsigned short lpr_log2, swap;
+};
+static_assert(sizeof(VTile) == 64, "VTile layout");
+constexpr int kVecWarps = 8;
 int vec_width(igg_dtype dt);  // V
-cudaError_t launch_stencil_vec(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
+cudaError_t launch_stencil_vec(igg_dtype dt, const VTile *tiles, int ntiles, void *T2,
                                const void *T, const void *Ci, const Coef &c,
                                const Coef *table, cudaStream_t s);
 

@@ -72,9 +72,11 @@ struct DeviceGuard {
   }
 };
 
+// Device tile table of one launch: Tile (scalar kernel, V = 1) or VTile.
 struct TileSet {
-  Tile *dev = nullptr;
+  void *dev = nullptr;
   int n = 0;
+  int V = 1;
 };
 
 struct SplitTiles {
@@ -159,36 +161,58 @@ void add_box(std::vector<Tile> &v, long long base, int nx, int ny, int x0, int x
       }
 }
 
-// Tiles of the vector kernel: lane 0 of a tile starts at an x multiple of V,
-// the tile computes xb <= x < xe, one warp per row (kVecRows rows).
-void add_box_vec(std::vector<Tile> &v, long long base, int nx, int ny, int x0, int x1, int y0,
+// Tiles of the vector kernel for the box [x0,x1) x [y0,y1) x [z0,z1) of one
+// array. Rows run along y and the tiles march along z, unless the box is thin
+// in y (fewer than kVecWarps rows) and longer in z: then rows run along z and
+// the tiles march along y. A row of a tile is a segment of lpr lanes, the
+// smallest power of two (<= 32) that covers the box's width in vectors.
+void add_box_vec(std::vector<VTile> &v, long long base, int nx, int ny, int x0, int x1, int y0,
                  int y1, int z0, int z1, int zb, int param, int V) {
   if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;
-  const int span = 32 * V;
-  for (int zc = z0; zc < z1; zc += zb)
-    for (int y = y0; y < y1; y += kVecRows)
-      for (int xa = (x0 / V) * V; xa < x1; xa += span) {
-        Tile t;
+  const long long sxy = (long long)nx * ny;
+  const bool swap = (y1 - y0) < kVecWarps && (z1 - z0) > (y1 - y0);
+  const int r0 = swap ? z0 : y0, r1 = swap ? z1 : y1;
+  const int m0 = swap ? y0 : z0, m1 = swap ? y1 : z1;
+  const long long sr = swap ? sxy : nx, sm = swap ? nx : sxy;
+  const int mb = swap ? (m1 - m0) : zb;
+  const int a0 = (x0 / V) * V;
+  const int nvec = (x1 - a0 + V - 1) / V;
+  int lg = 0;
+  while ((1 << lg) < nvec && lg < 5) ++lg;
+  const int lpr = 1 << lg;
+  const int rows_per_cta = kVecWarps * (32 / lpr);
+  const int span = lpr * V;
+  for (int mc = m0; mc < m1; mc += mb)
+    for (int r = r0; r < r1; r += rows_per_cta)
+      for (int xa = a0; xa < x1; xa += span) {
+        VTile t;
         t.base = base;
+        t.sr = sr;
+        t.sm = sm;
         t.nx = nx;
-        t.ny = ny;
         t.x0 = xa;
-        t.y0 = y;
         t.xb = std::max(x0, xa);
         t.xe = std::min(x1, xa + span);
-        t.ye = y1;
-        t.z0 = zc;
-        t.z1 = std::min(zc + zb, z1);
+        t.r0 = r;
+        t.re = std::min(r + rows_per_cta, r1);
+        t.m0 = mc;
+        t.m1 = std::min(mc + mb, m1);
         t.param = param;
+        t.lpr_log2 = (unsigned short)lg;
+        t.swap = swap ? 1 : 0;
         v.push_back(t);
       }
 }
 
-// one entry point for both tile kinds (V = 1: scalar kernel tiles)
-void add_tiles(std::vector<Tile> &v, int V, long long base, int nx, int ny, int x0, int x1,
-               int y0, int y1, int z0, int z1, int zb, int param) {
-  if (V > 1) add_box_vec(v, base, nx, ny, x0, x1, y0, y1, z0, z1, zb, param, V);
-  else add_box(v, base, nx, ny, x0, x1, y0, y1, z0, z1, zb, param);
+// Tiles of one box for either kernel: V > 1 vector tiles, V = 1 scalar tiles.
+struct TileLists {
+  std::vector<Tile> scalar;
+  std::vector<VTile> vec;
+};
+void add_tiles(TileLists &v, int V, long long base, int nx, int ny, int x0, int x1, int y0,
+               int y1, int z0, int z1, int zb, int param) {
+  if (V > 1) add_box_vec(v.vec, base, nx, ny, x0, x1, y0, y1, z0, z1, zb, param, V);
+  else add_box(v.scalar, base, nx, ny, x0, x1, y0, y1, z0, z1, zb, param);
 }
 
 long long xy_tiles_of(int x0, int x1, int y0, int y1) {
@@ -196,15 +220,21 @@ long long xy_tiles_of(int x0, int x1, int y0, int y1) {
   return (long long)((x1 - x0 + kTileX - 1) / kTileX) * ((y1 - y0 + kTileY - 1) / kTileY);
 }
 
-int upload_tiles(const std::vector<Tile> &v, TileSet *out) {
+template <class TT>
+int upload_vec(const std::vector<TT> &v, TileSet *out) {
   out->n = (int)v.size();
   out->dev = nullptr;
   if (v.empty()) return IGG_OK;
-  cudaError_t e = cudaMalloc(&out->dev, v.size() * sizeof(Tile));
+  cudaError_t e = cudaMalloc(&out->dev, v.size() * sizeof(TT));
   if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(tiles)");
-  e = cudaMemcpy(out->dev, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(out->dev, v.data(), v.size() * sizeof(TT), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(tiles)");
   return IGG_OK;
+}
+
+int upload_tiles(const TileLists &v, int V, TileSet *out) {
+  out->V = V;
+  return V > 1 ? upload_vec(v.vec, out) : upload_vec(v.scalar, out);
 }
 
 }  // namespace
@@ -270,11 +300,11 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   const long long xy = xy_tiles_of(1, nx - 1, 1, ny - 1) * g->nsub;
   const int zb = choose_zb(xy, nz - 2);
-  std::vector<Tile> v;
+  TileLists v;
   for (int s = 0; s < g->nsub; ++s)
     add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
   TileSet ts;
-  if (int rc = upload_tiles(v, &ts)) return rc;
+  if (int rc = upload_tiles(v, V, &ts)) return rc;
   *out = &g->full.emplace(V, ts).first->second;
   return IGG_OK;
 }
@@ -294,7 +324,7 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
   const int xl = lo_end(w[0], nx), xh = std::max(hi_beg(w[0], nx), xl);
   const int yl = lo_end(w[1], ny), yh = std::max(hi_beg(w[1], ny), yl);
   const int zl = lo_end(w[2], nz), zh = std::max(hi_beg(w[2], nz), zl);
-  std::vector<Tile> vb, vi;
+  TileLists vb, vi;
   // z slabs: all inner x, y; y slabs: z in the inner block range; x slabs:
   // y and z in the inner block ranges. The six boxes are disjoint and their
   // union with the inner block is the set of inner points.
@@ -315,8 +345,8 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
     add_tiles(vi, V, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);             // inner block
   }
   SplitTiles st;
-  int rc = upload_tiles(vb, &st.boundary);
-  if (rc == IGG_OK) rc = upload_tiles(vi, &st.inner);
+  int rc = upload_tiles(vb, V, &st.boundary);
+  if (rc == IGG_OK) rc = upload_tiles(vi, V, &st.inner);
   if (rc != IGG_OK) {
     cudaFree(st.boundary.dev);
     cudaFree(st.inner.dev);
@@ -329,8 +359,8 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
 
 cudaError_t launch_tiles(int V, igg_dtype dt, const TileSet &ts, void *T2, const void *T,
                          const void *Ci, const Coef &c, cudaStream_t s) {
-  if (V > 1) return launch_stencil_vec(dt, ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
-  return launch_stencil(dt, ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
+  if (V > 1) return launch_stencil_vec(dt, (const VTile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
+  return launch_stencil(dt, (const Tile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
 
 // Plane-copy tables of the halo update, one per dimension.

@@ -219,15 +219,15 @@ __device__ __forceinline__ void unpack(const uint4 &r, Vec<__nv_bfloat16> &o) {
     o.v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
 }
-__device__ __forceinline__ unsigned short bf16_bits(float f) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+// two FP32 values -> one BF16x2 word (round to nearest even, one packed
+// conversion instruction)
+__device__ __forceinline__ unsigned bf16x2_bits(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned *>(&h);
 }
 __device__ __forceinline__ uint4 pack(const Vec<__nv_bfloat16> &o) {
-  unsigned w[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    w[i] = (unsigned)bf16_bits(o.v[2 * i]) | ((unsigned)bf16_bits(o.v[2 * i + 1]) << 16);
-  return make_uint4(w[0], w[1], w[2], w[3]);
+  return make_uint4(bf16x2_bits(o.v[0], o.v[1]), bf16x2_bits(o.v[2], o.v[3]),
+                    bf16x2_bits(o.v[4], o.v[5]), bf16x2_bits(o.v[6], o.v[7]));
 }
 
 template <class S>
@@ -241,51 +241,59 @@ __device__ __forceinline__ typename Num<S>::C ld1(const S *p) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(32 * kVecRows)
-    k_stencil_vec(const Tile *__restrict__ tiles, S *__restrict__ T2, const S *__restrict__ T,
+__global__ void __launch_bounds__(32 * kVecWarps)
+    k_stencil_vec(const VTile *__restrict__ tiles, S *__restrict__ T2, const S *__restrict__ T,
                   const S *__restrict__ Ci, Coef c0, const Coef *__restrict__ table) {
   using C = typename Num<S>::C;
   constexpr int V = Vec<S>::V;
-  const Tile t = tiles[blockIdx.x];
+  const VTile t = tiles[blockIdx.x];
   const W<C> w = make_w(table ? table[t.param] : c0, C(0));
   const int lane = threadIdx.x & 31;
-  const int y = t.y0 + (int)(threadIdx.x >> 5);
-  if (y >= t.ye) return;  // whole warp leaves together
-  const int xs = t.x0 + lane * V;
+  const int lpr = 1 << t.lpr_log2;
+  const int rows_per_warp = 32 >> t.lpr_log2;
+  const int row0 = t.r0 + (int)(threadIdx.x >> 5) * rows_per_warp;
+  if (row0 >= t.re) return;  // the whole warp has no row of the tile
+  const int sl = lane & (lpr - 1);
+  const int r = row0 + (lane >> t.lpr_log2);
+  const bool row_ok = r < t.re;
+  const int xs = t.x0 + sl * V;
   // this lane's vector is needed if it overlaps [xb - 1, xe + 1) inside the row
-  const bool need = xs < t.nx && xs + V > t.xb - 1 && xs < t.xe + 1;
-  const bool comp = xs + V > t.xb && xs < t.xe;  // has points to compute
-  const long long sy = t.nx;
-  const long long sz = (long long)t.nx * t.ny;
-  long long p = t.base + xs + sy * y + sz * (t.z0 - 1);
-  Vec<S> zm, zc, zp, ym, yp, ci;
+  const bool need = row_ok && xs < t.nx && xs + V > t.xb - 1 && xs < t.xe + 1;
+  const bool comp = row_ok && xs + V > t.xb && xs < t.xe;  // has points to compute
+  const long long sr = t.sr, sm = t.sm;
+  long long p = t.base + xs + sr * r + sm * (t.m0 - 1);
+  Vec<S> mm, mc, mp, rm, rp, ci;
 #pragma unroll
-  for (int i = 0; i < V; ++i) zm.v[i] = zc.v[i] = zp.v[i] = C(0);
+  for (int i = 0; i < V; ++i) mm.v[i] = mc.v[i] = mp.v[i] = C(0);
   if (need) {
-    ldvec(T + p, zm);
-    ldvec(T + p + sz, zc);
+    ldvec(T + p, mm);
+    ldvec(T + p + sm, mc);
   }
-  const bool left_ld = lane == 0 && comp && xs > 0;
-  const bool right_ld = lane == 31 && comp && xs + V < t.nx;
-  for (int z = t.z0; z < t.z1; ++z) {
-    p += sz;
-    if (need) ldvec(T + p + sz, zp);
+  const bool left_ld = sl == 0 && comp && xs > 0;
+  const bool right_ld = sl == lpr - 1 && comp && xs + V < t.nx;
+  const bool swap = t.swap != 0;
+  for (int m = t.m0; m < t.m1; ++m) {
+    p += sm;
+    if (need) ldvec(T + p + sm, mp);
     if (comp) {
-      ldvec(T + p - sy, ym);
-      ldvec(T + p + sy, yp);
+      ldvec(T + p - sr, rm);
+      ldvec(T + p + sr, rp);
       ldvec(Ci + p, ci);
     }
-    C left = __shfl_up_sync(0xffffffffu, zc.v[V - 1], 1);
-    C right = __shfl_down_sync(0xffffffffu, zc.v[0], 1);
+    C left = __shfl_up_sync(0xffffffffu, mc.v[V - 1], 1, lpr);
+    C right = __shfl_down_sync(0xffffffffu, mc.v[0], 1, lpr);
     if (left_ld) left = ld1(T + p - 1);
     if (right_ld) right = ld1(T + p + V);
     if (comp) {
       Vec<S> out;
 #pragma unroll
       for (int i = 0; i < V; ++i) {
-        const C xm = i == 0 ? left : zc.v[i - 1];
-        const C xp = i == V - 1 ? right : zc.v[i + 1];
-        out.v[i] = cell(zc.v[i], xm, xp, ym.v[i], yp.v[i], zm.v[i], zp.v[i], ci.v[i], w);
+        const C xm = i == 0 ? left : mc.v[i - 1];
+        const C xp = i == V - 1 ? right : mc.v[i + 1];
+        // rows along y: (row pair, march pair) = (y, z); swapped: (z, y)
+        const C ym = swap ? mm.v[i] : rm.v[i], yp = swap ? mp.v[i] : rp.v[i];
+        const C zm = swap ? rm.v[i] : mm.v[i], zp = swap ? rp.v[i] : mp.v[i];
+        out.v[i] = cell(mc.v[i], xm, xp, ym, yp, zm, zp, ci.v[i], w);
       }
       if (xs >= t.xb && xs + V <= t.xe) {
         *reinterpret_cast<uint4 *>(T2 + p) = pack(out);
@@ -297,8 +305,8 @@ __global__ void __launch_bounds__(32 * kVecRows)
     }
 #pragma unroll
     for (int i = 0; i < V; ++i) {
-      zm.v[i] = zc.v[i];
-      zc.v[i] = zp.v[i];
+      mm.v[i] = mc.v[i];
+      mc.v[i] = mp.v[i];
     }
   }
 }
@@ -362,21 +370,21 @@ int vec_width(igg_dtype dt) {
   return s ? (int)(16 / s) : 0;
 }
 
-cudaError_t launch_stencil_vec(igg_dtype dt, const Tile *tiles, int ntiles, void *T2,
+cudaError_t launch_stencil_vec(igg_dtype dt, const VTile *tiles, int ntiles, void *T2,
                                const void *T, const void *Ci, const Coef &c,
                                const Coef *table, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   switch (dt) {
     case IGG_F64:
-      k_stencil_vec<double><<<ntiles, 32 * kVecRows, 0, s>>>(
+      k_stencil_vec<double><<<ntiles, 32 * kVecWarps, 0, s>>>(
           tiles, (double *)T2, (const double *)T, (const double *)Ci, c, table);
       break;
     case IGG_F32:
-      k_stencil_vec<float><<<ntiles, 32 * kVecRows, 0, s>>>(
+      k_stencil_vec<float><<<ntiles, 32 * kVecWarps, 0, s>>>(
           tiles, (float *)T2, (const float *)T, (const float *)Ci, c, table);
       break;
     case IGG_BF16:
-      k_stencil_vec<__nv_bfloat16><<<ntiles, 32 * kVecRows, 0, s>>>(
+      k_stencil_vec<__nv_bfloat16><<<ntiles, 32 * kVecWarps, 0, s>>>(
           tiles, (__nv_bfloat16 *)T2, (const __nv_bfloat16 *)T, (const __nv_bfloat16 *)Ci, c,
           table);
       break;
