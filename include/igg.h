@@ -126,6 +126,21 @@ int igg_subdomain_info(const igg_grid *grid, int sub, int coords[3],
 int igg_update_halo(igg_grid *grid, void *const fields[], int nfields,
                     igg_dtype dtype, void *stream);
 
+/* Device error word of the grid's pipelined kernels: bit 1 = a bounded
+ * wait inside a kernel gave up (the kernel stopped early and its output is
+ * incomplete), bit 2 = waiting for its own copies in flight gave up.
+ * Synchronises the device; clear != 0 resets the word to 0. */
+#define IGG_DEV_ERR_TIMEOUT 1u
+#define IGG_DEV_ERR_DRAIN 2u
+int igg_device_status(igg_grid *grid, unsigned *status, int clear);
+
+/* Grid options. IGG_OPT_TMA (default 1): run the full step and the inner
+ * block with the TMA-pipelined kernel when the row length is a multiple of
+ * 16 bytes; 0 selects the register-pipelined vector kernel. Results are
+ * bit-identical either way. Waits for the grid's streams. */
+#define IGG_OPT_TMA 1
+int igg_grid_set_option(igg_grid *grid, int option, int value);
+
 /* ---------------------------------------------------------------------------
  * Diffusion step (Fig. 1 step!) on every subdomain:
  *   T2 = T + dt*(lam*Ci*(d2x/dx^2 + d2y/dy^2 + d2z/dz^2))

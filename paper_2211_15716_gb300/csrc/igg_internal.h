@@ -95,6 +95,31 @@ cudaError_t launch_stencil_persistent(igg_dtype dt, int variant, const Tile *til
                                       int nctas, void *T2, const void *T, const void *Ci,
                                       const Coef *table, cudaStream_t s);
 
+// TMA-pipelined kernel for regular boxes (rows along y, march along z). A
+// tile computes xb <= x < xe (lane 0 of a row at x0, a multiple of V, the
+// tile spans tma_tile_width points), rows y0 <= y < ye (at most
+// tma_tile_rows), planes z0 <= z < z1 of the array at element offset `base`,
+// which is plane zoff of the field seen as one stack of nsub*nz planes.
+struct TmaTile {
+  long long base;
+  int x0, xb, xe;
+  int y0, ye;
+  int z0, z1;
+  int zoff;
+  int pad[2];
+};
+static_assert(sizeof(TmaTile) == 48, "TmaTile layout");
+// bits of the device error word: IGG_DEV_ERR_TIMEOUT, IGG_DEV_ERR_DRAIN (igg.h)
+int tma_tile_width(igg_dtype dt);
+int tma_tile_rows();
+bool tma_available();
+// Sets the kernel's shared-memory attribute and returns its resident CTAs per
+// SM; call before launching (and before any stream capture).
+cudaError_t tma_prepare(igg_dtype dt, int *ctas_per_sm);
+cudaError_t launch_stencil_tma(igg_dtype dt, const TmaTile *tiles, int ntiles, void *T2,
+                               const void *T, const void *Ci, int nx, int ny, long long nzt,
+                               const Coef &c, unsigned *dev_err, cudaStream_t s);
+
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.
 cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,

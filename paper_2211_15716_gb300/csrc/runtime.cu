@@ -72,11 +72,13 @@ struct DeviceGuard {
   }
 };
 
-// Device tile table of one launch: Tile (scalar kernel, V = 1) or VTile.
+// Device tile table of one launch: Tile (scalar kernel, V = 1), VTile
+// (vector kernel) or TmaTile (TMA kernel, tma = true).
 struct TileSet {
   void *dev = nullptr;
   int n = 0;
   int V = 1;
+  bool tma = false;
 };
 
 struct SplitTiles {
@@ -204,10 +206,71 @@ void add_box_vec(std::vector<VTile> &v, long long base, int nx, int ny, int x0, 
       }
 }
 
-// Tiles of one box for either kernel: V > 1 vector tiles, V = 1 scalar tiles.
+// dtype whose vector width is V (V = 16 / element size)
+igg_dtype dtype_of_vec(int V) { return V == 2 ? IGG_F64 : V == 4 ? IGG_F32 : IGG_BF16; }
+
+// z depth of TMA tiles: each tile loads two extra planes of T and of Ci, so
+// deeper is cheaper, but the tile count should fill whole waves of resident
+// CTAs; minimise (extra-plane cost) / (wave efficiency).
+int choose_zb_tma(long long xy_tiles, int zext, long long slots) {
+  int best = std::min(64, zext);
+  double best_cost = 1e30;
+  for (int zb : {16, 24, 32, 40, 48, 64, 96, 128}) {
+    const int z = std::min(zb, zext);
+    const long long nt = xy_tiles * ((zext + z - 1) / z);
+    const long long waves = (nt + slots - 1) / slots;
+    const double eff = (double)nt / (double)(waves * slots);
+    const double cost = (1.0 + (2.0 / z) * (2.0 / 3.0)) / eff;
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = z;
+    }
+    if (zb >= zext) break;
+  }
+  return best;
+}
+
+long long tma_xy_tiles(int x0, int x1, int y0, int y1, int V, int Wt, int Ht) {
+  if (x0 >= x1 || y0 >= y1) return 0;
+  const int a0 = (x0 / V) * V;
+  return (long long)((x1 - a0 + Wt - 1) / Wt) * ((y1 - y0 + Ht - 1) / Ht);
+}
+
+// resident-CTA slots of the TMA kernel for the dtype of vector width V
+long long tma_slots(int V) {
+  int per_sm = 1, sms = 152, dev = 0;
+  if (tma_prepare(dtype_of_vec(V), &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (long long)per_sm * sms;
+}
+
+// Tiles of the TMA kernel for one regular box of subdomain plane offset zoff.
+void add_box_tma(std::vector<TmaTile> &v, long long base, long long zoff, int x0, int x1, int y0,
+                 int y1, int z0, int z1, int zb, int V, int Wt, int Ht) {
+  if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;
+  for (int zc = z0; zc < z1; zc += zb)
+    for (int y = y0; y < y1; y += Ht)
+      for (int xa = (x0 / V) * V; xa < x1; xa += Wt) {
+        TmaTile t;
+        t.base = base;
+        t.x0 = xa;
+        t.xb = std::max(x0, xa);
+        t.xe = std::min(x1, xa + Wt);
+        t.y0 = y;
+        t.ye = std::min(y + Ht, y1);
+        t.z0 = zc;
+        t.z1 = std::min(zc + zb, z1);
+        t.zoff = (int)zoff;
+        t.pad[0] = t.pad[1] = 0;
+        v.push_back(t);
+      }
+}
+
+// Tiles of one box for the kernel of the set: scalar (V = 1), vector or TMA.
 struct TileLists {
   std::vector<Tile> scalar;
   std::vector<VTile> vec;
+  std::vector<TmaTile> tma;
 };
 void add_tiles(TileLists &v, int V, long long base, int nx, int ny, int x0, int x1, int y0,
                int y1, int z0, int z1, int zb, int param) {
@@ -232,8 +295,10 @@ int upload_vec(const std::vector<TT> &v, TileSet *out) {
   return IGG_OK;
 }
 
-int upload_tiles(const TileLists &v, int V, TileSet *out) {
+int upload_tiles(const TileLists &v, int V, TileSet *out, bool tma = false) {
   out->V = V;
+  out->tma = tma;
+  if (tma) return upload_vec(v.tma, out);
   return V > 1 ? upload_vec(v.vec, out) : upload_vec(v.scalar, out);
 }
 
@@ -255,6 +320,8 @@ struct igg_grid {
   PlaneCopy *copies[3] = {nullptr, nullptr, nullptr};
   int ncopies[3] = {0, 0, 0};
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  unsigned *dev_err = nullptr;  // device error word of the pipelined kernels
+  bool tma_enabled = true;      // TMA kernel for the regular boxes when available
 };
 
 namespace {
@@ -283,6 +350,10 @@ int check_coef(double lam, double dt, double dx, double dy, double dz) {
   return IGG_OK;
 }
 
+// The TMA kernel takes the regular boxes (full step, inner block) of grids
+// whose rows are 16-byte multiples, unless disabled on the grid.
+bool use_tma(const igg_grid *g, int V) { return V > 1 && g->tma_enabled && tma_available(); }
+
 // Vector width used for dtype dt on this grid (1 = scalar kernel): the
 // 16-byte vector kernel needs rows of a multiple of V points.
 int grid_vec(const igg_grid *g, igg_dtype dt) {
@@ -301,10 +372,20 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
   const long long xy = xy_tiles_of(1, nx - 1, 1, ny - 1) * g->nsub;
   const int zb = choose_zb(xy, nz - 2);
   TileLists v;
-  for (int s = 0; s < g->nsub; ++s)
-    add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
+  const bool tma = use_tma(g, V);
+  const int Wt = tma ? tma_tile_width(dtype_of_vec(V)) : 0, Ht = tma_tile_rows();
+  const int zbt = tma ? choose_zb_tma(tma_xy_tiles(1, nx - 1, 1, ny - 1, V, Wt, Ht) * g->nsub,
+                                      nz - 2, tma_slots(V))
+                      : 0;
+  for (int s = 0; s < g->nsub; ++s) {
+    if (tma)
+      add_box_tma(v.tma, (long long)s * g->nloc, (long long)s * nz, 1, nx - 1, 1, ny - 1, 1, nz - 1,
+                  zbt, V, Wt, Ht);
+    else
+      add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
+  }
   TileSet ts;
-  if (int rc = upload_tiles(v, V, &ts)) return rc;
+  if (int rc = upload_tiles(v, V, &ts, tma)) return rc;
   *out = &g->full.emplace(V, ts).first->second;
   return IGG_OK;
 }
@@ -332,8 +413,15 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
   xy_b += 2 * xy_tiles_of(1, nx - 1, 1, ny - 1);
   xy_b += 2 * xy_tiles_of(1, nx - 1, 1, yl) + 2 * xy_tiles_of(1, xl, yl, yh);
   xy_i += xy_tiles_of(xl, xh, yl, yh);
-  const int zb_b = choose_zb(xy_b * g->nsub, zh - zl > 0 ? zh - zl : 1);
+  // boundary slabs are thin: short z sweeps give many tiles that run side by
+  // side instead of a few long latency-bound sweeps on the critical path
+  const int zb_b = std::min(8, choose_zb(xy_b * g->nsub, zh - zl > 0 ? zh - zl : 1));
   const int zb_i = choose_zb(xy_i * g->nsub, zh - zl > 0 ? zh - zl : 1);
+  const int Wt_i = use_tma(g, V) ? tma_tile_width(dtype_of_vec(V)) : 0;
+  const int zbt_i = use_tma(g, V)
+                        ? choose_zb_tma(tma_xy_tiles(xl, xh, yl, yh, V, Wt_i, tma_tile_rows()) * g->nsub,
+                                        zh - zl > 0 ? zh - zl : 1, tma_slots(V))
+                        : 0;
   for (int s = 0; s < g->nsub; ++s) {
     const long long base = (long long)s * g->nloc;
     add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, ny - 1, 1, zl, 64, 0);          // z low
@@ -342,11 +430,15 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
     add_tiles(vb, V, base, nx, ny, 1, nx - 1, yh, ny - 1, zl, zh, zb_b, 0);      // y high
     add_tiles(vb, V, base, nx, ny, 1, xl, yl, yh, zl, zh, zb_b, 0);              // x low
     add_tiles(vb, V, base, nx, ny, xh, nx - 1, yl, yh, zl, zh, zb_b, 0);         // x high
-    add_tiles(vi, V, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);             // inner block
+    if (use_tma(g, V))                                                              // inner block
+      add_box_tma(vi.tma, base, (long long)s * nz, xl, xh, yl, yh, zl, zh, zbt_i, V, Wt_i,
+                  tma_tile_rows());
+    else
+      add_tiles(vi, V, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);
   }
   SplitTiles st;
   int rc = upload_tiles(vb, V, &st.boundary);
-  if (rc == IGG_OK) rc = upload_tiles(vi, V, &st.inner);
+  if (rc == IGG_OK) rc = upload_tiles(vi, V, &st.inner, use_tma(g, V));
   if (rc != IGG_OK) {
     cudaFree(st.boundary.dev);
     cudaFree(st.inner.dev);
@@ -357,8 +449,11 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
   return IGG_OK;
 }
 
-cudaError_t launch_tiles(int V, igg_dtype dt, const TileSet &ts, void *T2, const void *T,
-                         const void *Ci, const Coef &c, cudaStream_t s) {
+cudaError_t launch_tiles(const igg_grid *g, int V, igg_dtype dt, const TileSet &ts, void *T2,
+                         const void *T, const void *Ci, const Coef &c, cudaStream_t s) {
+  if (ts.tma)
+    return launch_stencil_tma(dt, (const TmaTile *)ts.dev, ts.n, T2, T, Ci, g->n[0], g->n[1],
+                              (long long)g->nsub * g->n[2], c, g->dev_err, s);
   if (V > 1) return launch_stencil_vec(dt, (const VTile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
   return launch_stencil(dt, (const Tile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
@@ -410,7 +505,7 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   if (!widths) {
     TileSet *full = nullptr;
     if (int rc = build_full_tiles(g, V, &full)) return rc;
-    e = launch_tiles(V, dt, *full, T2, T, Ci, c, s);
+    e = launch_tiles(g, V, dt, *full, T2, T, Ci, c, s);
     if (e != cudaSuccess) return cuda_error(e, "stencil launch");
     if (with_halo && any_halo(g)) {
       e = enqueue_halo(g, T2, dtype_size(dt), s);
@@ -424,10 +519,10 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   if ((e = cudaEventRecord(g->ev_fork, s)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(g->hi, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
   if ((e = cudaStreamWaitEvent(g->lo, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
-  e = launch_tiles(V, dt, st->boundary, T2, T, Ci, c, g->hi);
+  e = launch_tiles(g, V, dt, st->boundary, T2, T, Ci, c, g->hi);
   if (e == cudaSuccess && any_halo(g)) e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
   if (e != cudaSuccess) return cuda_error(e, "boundary/halo launch");
-  e = launch_tiles(V, dt, st->inner, T2, T, Ci, c, g->lo);
+  e = launch_tiles(g, V, dt, st->inner, T2, T, Ci, c, g->lo);
   if (e != cudaSuccess) return cuda_error(e, "inner launch");
   if ((e = cudaEventRecord(g->ev_hi, g->hi)) != cudaSuccess) return cuda_error(e, "record");
   if ((e = cudaEventRecord(g->ev_lo, g->lo)) != cudaSuccess) return cuda_error(e, "record");
@@ -455,6 +550,7 @@ void destroy_grid(igg_grid *g) {
   }
   for (auto &kv : g->full) cudaFree(kv.second.dev);
   for (int d = 0; d < 3; ++d) cudaFree(g->copies[d]);
+  cudaFree(g->dev_err);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_hi) cudaEventDestroy(g->ev_hi);
   if (g->ev_lo) cudaEventDestroy(g->ev_lo);
@@ -555,6 +651,12 @@ int igg_init_global_grid(int nx, int ny, int nz, const int dims_in[3], int nsub,
   if (e != cudaSuccess) {
     destroy_grid(g);
     return cuda_error(e, "stream/event creation");
+  }
+  e = cudaMalloc(&g->dev_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(g->dev_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    destroy_grid(g);
+    return cuda_error(e, "device error word");
   }
   int rc = build_halo_tables(g);
   if (rc != IGG_OK) {
@@ -878,6 +980,40 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
   }
   e = cudaMemcpyAsync(gT0, cur, bytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_error(e, "gradient copy");
+  return IGG_OK;
+}
+
+
+int igg_device_status(igg_grid *g, unsigned *status, int clear) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (!status) return set_error(IGG_EINVAL, "status is NULL");
+  DeviceGuard dg(g->device);
+  cudaError_t e = cudaMemcpy(status, g->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(g->dev_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_error(e, "device status");
+  return IGG_OK;
+}
+
+int igg_grid_set_option(igg_grid *g, int option, int value) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (option != IGG_OPT_TMA) return set_error(IGG_EINVAL, "unknown option %d", option);
+  DeviceGuard dg(g->device);
+  cudaError_t e1 = cudaStreamSynchronize(g->hi), e2 = cudaStreamSynchronize(g->lo);
+  if (e1 != cudaSuccess) return cuda_error(e1, "set_option");
+  if (e2 != cudaSuccess) return cuda_error(e2, "set_option");
+  g->tma_enabled = value != 0;
+  // tile tables and graphs depend on the kernel choice
+  for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+  g->graphs.clear();
+  for (auto &kv : g->split) {
+    cudaFree(kv.second.boundary.dev);
+    cudaFree(kv.second.inner.dev);
+  }
+  g->split.clear();
+  for (auto &kv : g->full) cudaFree(kv.second.dev);
+  g->full.clear();
   return IGG_OK;
 }
 

@@ -1,0 +1,351 @@
+// TMA-pipelined stencil kernel for the regular boxes of the step (the full
+// step and the inner block of the split): a producer warp streams, plane by
+// plane along z, a tile of T with a one-vector / one-row halo and the
+// matching tile of Ci from HBM into a ring of shared-memory stages with
+// cp.async.bulk.tensor (TMA); eight consumer warps compute from shared
+// memory and write T2 with 16-byte stores. The bytes in flight per SM are
+// set by the ring (several stages of ~18 KB per CTA), not by registers, which
+// keeps HBM busy.
+//
+// Ring protocol (per stage s: mbarrier full[s], count 1 + transaction bytes;
+// mbarrier empty[s], count = consumer warps): load k goes to stage k % NS;
+// the producer waits empty[s] before reusing a stage, arms full[s] with the
+// byte count and issues the copies; consumers wait full[s], read, and each
+// warp arrives on empty[s]. Load k holds T plane z0-1+k and Ci plane
+// z0-2+k; step z uses T planes z (neighbours) and z+1, Ci plane z, and keeps
+// T plane z-1 of its own points in registers.
+//
+// Every wait is bounded (about 2 s of globaltimer); on a timeout the kernel
+// records IGG_DEV_ERR_TIMEOUT in the device error word, stops, waits (again
+// bounded) for the copies it issued, and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "cell.cuh"
+#include "igg_internal.h"
+
+namespace igg {
+namespace {
+
+template <class S>
+struct TmaShape {
+  static constexpr int V = 16 / (int)sizeof(S);
+  static constexpr int LPR = sizeof(S) == 2 ? 16 : 32;  // lanes per row
+  static constexpr int W = LPR * V;                     // computed points per row
+  static constexpr int BW = W + 2 * V;                  // T box width (vector halo each side)
+  static constexpr int H = 16;                          // rows per tile
+  static constexpr int BH = H + 2;                      // T box height (row halo)
+  static constexpr int NS = 4;                          // stages
+  static constexpr int CONSUMERS = 8;                   // consumer warps
+  static constexpr int ROWS_PER_PASS = CONSUMERS * (32 / LPR);
+  static constexpr int RPT = H / ROWS_PER_PASS;         // rows per consumer thread
+  static constexpr int TB = BW * BH * (int)sizeof(S);   // T box bytes
+  static constexpr int TBA = (TB + 127) / 128 * 128;
+  static constexpr int CB = W * H * (int)sizeof(S);     // Ci box bytes
+  static constexpr int STAGE = (TBA + CB + 127) / 128 * 128;
+  static constexpr int SMEM = NS * STAGE + 2 * NS * 8 + 64;
+  static_assert(H % ROWS_PER_PASS == 0, "rows per tile");
+  static_assert(BW <= 256 && BH <= 256, "TMA box dims");
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+// Bounded wait for the phase of the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_test(bar, parity)) return true;
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int x, int y,
+                                            int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+template <class S>
+__device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
+  unpack(*reinterpret_cast<const uint4 *>(p), o);
+}
+
+template <class S>
+__global__ void __launch_bounds__(32 * (TmaShape<S>::CONSUMERS + 1))
+    k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
+                  const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
+                  unsigned *__restrict__ dev_err) {
+  using Sh = TmaShape<S>;
+  using C = typename Num<S>::C;
+  constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const unsigned sbase = smem_u32(smem);
+  const unsigned full0 = sbase + NS * Sh::STAGE;
+  const unsigned empty0 = full0 + NS * 8;
+  volatile int *flags = reinterpret_cast<volatile int *>(smem + NS * Sh::STAGE + 2 * NS * 8);
+  // flags[0]: abort; flags[1]: loads issued; flags[2]: loads consumed
+
+  const TmaTile t = tiles[blockIdx.x];
+  const int K = (t.z1 - t.z0) + 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, Sh::CONSUMERS);
+    }
+    flags[0] = 0;
+    flags[1] = 0;
+    flags[2] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == Sh::CONSUMERS) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int k = 0;
+      for (; k < K; ++k) {
+        const int s = k % NS;
+        if (k >= NS && !mbar_wait(empty0 + 8 * s, ((k / NS) - 1) & 1)) {
+          atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
+          flags[0] = 1;
+          break;
+        }
+        if (flags[0]) break;
+        const unsigned bar = full0 + 8 * s;
+        const unsigned dst = sbase + s * Sh::STAGE;
+        mbar_expect_tx(bar, Sh::TB + Sh::CB);
+        tma_load_3d(dst, &mapT, t.x0 - V, t.y0 - 1, t.zoff + t.z0 - 1 + k, bar);
+        tma_load_3d(dst + Sh::TBA, &mapC, t.x0, t.y0, t.zoff + t.z0 - 2 + k, bar);
+      }
+      flags[1] = k;
+    }
+  } else {
+    // ---------------- consumers ----------------
+    const int sl = lane % LPR;
+    const int xs = t.x0 + sl * V;
+    const W<C> w = make_w(c0, C(0));
+    int rowi[Sh::RPT];
+    bool comp[Sh::RPT];
+#pragma unroll
+    for (int j = 0; j < Sh::RPT; ++j) {
+      rowi[j] = warp * (32 / LPR) + lane / LPR + j * Sh::ROWS_PER_PASS;  // row in the tile
+      comp[j] = (t.y0 + rowi[j] < t.ye) && xs + V > t.xb && xs < t.xe;
+    }
+    const bool full_vec = xs >= t.xb && xs + V <= t.xe;
+    const long long sy = nx, sz = (long long)nx * ny;
+    Vec<S> zm[Sh::RPT];
+    bool ok = mbar_wait(full0, 0);
+    if (!ok) {
+      atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
+      flags[0] = 1;
+    } else {
+      const S *Tb = reinterpret_cast<const S *>(smem);
+#pragma unroll
+      for (int j = 0; j < Sh::RPT; ++j) lds_vec(Tb + (rowi[j] + 1) * Sh::BW + V + sl * V, zm[j]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0);
+    }
+    int consumed = 1;
+    for (int z = t.z0; ok && z < t.z1; ++z) {
+      const int k = z - t.z0 + 1;
+      const int s = k % NS, s1 = (k + 1) % NS;
+      if (!mbar_wait(full0 + 8 * s, (k / NS) & 1) ||
+          !mbar_wait(full0 + 8 * s1, ((k + 1) / NS) & 1)) {
+        atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
+        flags[0] = 1;
+        ok = false;
+        break;
+      }
+      consumed = k + 2;
+      const S *Tc = reinterpret_cast<const S *>(smem + s * Sh::STAGE);
+      const S *Tn = reinterpret_cast<const S *>(smem + s1 * Sh::STAGE);
+      const S *Cn = reinterpret_cast<const S *>(smem + s1 * Sh::STAGE + Sh::TBA);
+#pragma unroll
+      for (int j = 0; j < Sh::RPT; ++j) {
+        const int r = rowi[j];
+        const S *row = Tc + (r + 1) * Sh::BW + V + sl * V;
+        Vec<S> c, up, dn, zp, ci;
+        lds_vec(row, c);
+        lds_vec(row - Sh::BW, up);
+        lds_vec(row + Sh::BW, dn);
+        lds_vec(Tn + (r + 1) * Sh::BW + V + sl * V, zp);
+        lds_vec(Cn + r * Sh::W + sl * V, ci);
+        C left = __shfl_up_sync(0xffffffffu, c.v[V - 1], 1, LPR);
+        C right = __shfl_down_sync(0xffffffffu, c.v[0], 1, LPR);
+        if (sl == 0) left = Num<S>::cv(row[-1]);
+        if (sl == LPR - 1) right = Num<S>::cv(row[V]);
+        if (comp[j]) {
+          Vec<S> out;
+#pragma unroll
+          for (int i = 0; i < V; ++i) {
+            const C xm = i == 0 ? left : c.v[i - 1];
+            const C xp = i == V - 1 ? right : c.v[i + 1];
+            out.v[i] = cell(c.v[i], xm, xp, up.v[i], dn.v[i], zm[j].v[i], zp.v[i], ci.v[i], w);
+          }
+          S *dst = T2 + t.base + xs + sy * (t.y0 + r) + sz * z;
+          if (full_vec) {
+            *reinterpret_cast<uint4 *>(dst) = pack(out);
+          } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+              if (xs + i >= t.xb && xs + i < t.xe) Num<S>::st(dst + i, out.v[i]);
+          }
+        }
+        zm[j] = c;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * s);
+    }
+    if (warp == 0 && lane == 0) flags[2] = consumed;
+  }
+  __syncthreads();
+  // After an abort, wait (bounded) for copies issued but never consumed, so
+  // that no bulk copy writes into this CTA's shared memory after it exits.
+  if (threadIdx.x == 0 && flags[0]) {
+    for (int k = flags[2]; k < flags[1]; ++k) {
+      if (!mbar_wait(full0 + 8 * (k % NS), (k / NS) & 1)) {
+        atomicOr(dev_err, IGG_DEV_ERR_DRAIN);
+        break;
+      }
+    }
+  }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+template <class S>
+bool encode(CUtensorMap *m, const void *base, int nx, int ny, long long nzt, int bx, int by) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  CUtensorMapDataType t = sizeof(S) == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                          : sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nzt};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(S), (cuuint64_t)nx * ny * sizeof(S)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, t, 3, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class S>
+cudaError_t prepare_t(int *ctas_per_sm) {
+  using Sh = TmaShape<S>;
+  cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Sh::SMEM);
+  if (e == cudaSuccess && ctas_per_sm)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_stencil_tma<S>,
+                                                      32 * (Sh::CONSUMERS + 1), Sh::SMEM);
+  return e;
+}
+
+template <class S>
+cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
+                     int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
+                     cudaStream_t s) {
+  using Sh = TmaShape<S>;
+  CUtensorMap mT, mC;
+  if (!encode<S>(&mT, T, nx, ny, nzt, Sh::BW, Sh::BH) || !encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, Sh::H))
+    return cudaErrorInvalidValue;
+  k_stencil_tma<S><<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny,
+                                                                      c, dev_err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tma_tile_width(igg_dtype dt) {
+  switch (dt) {
+    case IGG_F64: return TmaShape<double>::W;
+    case IGG_F32: return TmaShape<float>::W;
+    case IGG_BF16: return TmaShape<__nv_bfloat16>::W;
+  }
+  return 0;
+}
+int tma_tile_rows() { return TmaShape<float>::H; }
+
+bool tma_available() { return encode_fn() != nullptr; }
+
+cudaError_t tma_prepare(igg_dtype dt, int *ctas_per_sm) {
+  switch (dt) {
+    case IGG_F64: return prepare_t<double>(ctas_per_sm);
+    case IGG_F32: return prepare_t<float>(ctas_per_sm);
+    case IGG_BF16: return prepare_t<__nv_bfloat16>(ctas_per_sm);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stencil_tma(igg_dtype dt, const TmaTile *tiles, int ntiles, void *T2,
+                               const void *T, const void *Ci, int nx, int ny, long long nzt,
+                               const Coef &c, unsigned *dev_err, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (dt) {
+    case IGG_F64: return launch_t<double>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+    case IGG_F32: return launch_t<float>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+    case IGG_BF16:
+      return launch_t<__nv_bfloat16>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace igg

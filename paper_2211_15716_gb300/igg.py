@@ -62,9 +62,12 @@ def lib():
     L.igg_step_hidden.argtypes = [P, IP, P, P, P, I, D, D, D, D, D, P]
     L.igg_run.argtypes = [P, I, IP, P, P, P, I, D, D, D, D, D, P]
     L.igg_reduce.argtypes = [I, P, P, ctypes.c_size_t, I, P, P]
+    L.igg_device_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint), I]
+    L.igg_grid_set_option.argtypes = [P, I, I]
     for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
                  "igg_grid_shape", "igg_subdomain_info", "igg_update_halo", "igg_step",
-                 "igg_step_hidden", "igg_run", "igg_reduce"):
+                 "igg_step_hidden", "igg_run", "igg_reduce", "igg_device_status",
+                 "igg_grid_set_option"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -177,6 +180,18 @@ class Grid:
             g = torch.arange(self.n[d], dtype=torch.int64) + info["offset"][d]
             out.append((g % ng[d]) if self.periods[d] else g)
         return [t.numpy() for t in out]
+
+    OPT_TMA = 1
+
+    def set_option(self, option: int, value: int):
+        """igg_grid_set_option (OPT_TMA: 1 = TMA kernel for regular boxes)."""
+        _check(lib().igg_grid_set_option(self._handle(), int(option), int(value)))
+
+    def device_status(self, clear: bool = False) -> int:
+        """Device error word of the pipelined kernels (0 = no error)."""
+        st = ctypes.c_uint()
+        _check(lib().igg_device_status(self._handle(), ctypes.byref(st), int(clear)))
+        return st.value
 
     def empty(self, dtype=torch.float64, device="cuda"):
         return torch.empty(self.shape, dtype=dtype, device=device)

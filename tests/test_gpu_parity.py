@@ -258,3 +258,51 @@ def test_widths_below_overlap_rejected():
         T = g.empty()
         with pytest.raises(igg.IggError):
             g.step_hidden((2, 2, 2), T.clone(), T, T.clone(), 1.0, 1e-3, 1.0, 1.0, 1.0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("n,dims,periods,overlap,widths", [
+    ((64, 37, 29), (2, 1, 2), (1, 0, 0), (2, 2, 2), (16, 2, 2)),
+    ((144, 40, 70), (1, 2, 1), (0, 1, 0), (2, 2, 2), (3, 4, 5)),
+    ((256, 33, 18), (2, 2, 2), (1, 0, 1), (2, 3, 2), (16, 3, 2)),
+])
+def test_tma_and_vector_kernels_same_bits(dtype, n, dims, periods, overlap, widths):
+    """The TMA-pipelined kernel and the register-pipelined vector kernel give
+    identical bits for the full step and the hidden step, and the device
+    error word stays clear."""
+    with igg.Grid(n, dims=dims, overlap=overlap, periods=periods) as g:
+        T0, Ci = grid_fields(g, 8)
+        T, Cd = dev(T0, dtype), dev(Ci, dtype)
+        dx, dy, dz, dt = wl.setup(wl.Workload("t", n), g, dev(Ci))
+        outs = []
+        for tma in (1, 0):
+            g.set_option(g.OPT_TMA, tma)
+            A, B = T.clone(), T.clone()
+            g.step(A, T, Cd, 1.0, dt, dx, dy, dz)
+            g.step_hidden(widths, B, T, Cd, 1.0, dt, dx, dy, dz)
+            R = g.run(5, T.clone(), T.clone(), Cd, 1.0, dt, dx, dy, dz, widths=widths)
+            torch.cuda.synchronize()
+            outs.append((A, B, R))
+        assert g.device_status() == 0
+        iv = {torch.float64: torch.int64, torch.float32: torch.int32, torch.bfloat16: torch.int16}[dtype]
+        for a, b in zip(outs[0], outs[1]):
+            assert torch.equal(a.view(iv), b.view(iv))
+
+
+def test_tma_full_size_decomposed_matches_oracle():
+    """The benchmark's launch configuration (2x2x2 x 512x256x256 FP64,
+    widths (16,2,2), graph loop) at full size: 2 hidden steps through the
+    TMA path, every point compared with the oracle."""
+    w = wl.WORKLOADS["decomposed_2x2x2_512x256x256"]
+    with igg.Grid(w.n, dims=w.dims, overlap=w.overlap, periods=w.periods) as g:
+        T, T2, Ci = wl.make_fields(w, g)
+        dx, dy, dz, dt = wl.setup(w, g, Ci)
+        T0 = T.cpu().numpy()
+        Cih = Ci.cpu().numpy()
+        res = g.run(2, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)
+        gpu = res.cpu().numpy()
+        assert g.device_status() == 0
+    oracle.set_threads(0)
+    ref = oracle.run_decomposed(T0, Cih, 2, w.lam, dt, dx, dy, dz, w.dims, w.periods, w.overlap,
+                                widths=w.widths)
+    assert rel_err(gpu, ref) <= FP64_TOL
