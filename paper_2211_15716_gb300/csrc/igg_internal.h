@@ -95,30 +95,33 @@ cudaError_t launch_stencil_persistent(igg_dtype dt, int variant, const Tile *til
                                       int nctas, void *T2, const void *T, const void *Ci,
                                       const Coef *table, cudaStream_t s);
 
-// TMA-pipelined kernel for regular boxes (rows along y, march along z). A
-// tile computes xb <= x < xe (lane 0 of a row at x0, a multiple of V, the
-// tile spans tma_tile_width points), rows y0 <= y < ye (at most
-// tma_tile_rows), planes z0 <= z < z1 of the array at element offset `base`,
-// which is plane zoff of the field seen as one stack of nsub*nz planes.
+// TMA-pipelined kernel. A tile computes xb <= x < xe (lane 0 of a row at x0,
+// a multiple of V; the tile spans tma_tile_width points), rows r0 <= r < re
+// (at most tma_tile_rows) and march steps m0 <= m < m1 of the array at
+// element offset `base`, which starts at plane zoff of the field seen as one
+// stack of nsub*nz planes. Variants: TMA_WIDE (rows along y, march along z),
+// TMA_NARROW (the same with 16-point rows, for x slabs) and TMA_WIDE_SWAP
+// (rows along z, march along y, for y slabs).
 struct TmaTile {
   long long base;
   int x0, xb, xe;
-  int y0, ye;
-  int z0, z1;
+  int r0, re;
+  int m0, m1;
   int zoff;
   int pad[2];
 };
+enum { TMA_WIDE = 0, TMA_NARROW = 1, TMA_WIDE_SWAP = 2 };
 static_assert(sizeof(TmaTile) == 48, "TmaTile layout");
 // bits of the device error word: IGG_DEV_ERR_TIMEOUT, IGG_DEV_ERR_DRAIN (igg.h)
-int tma_tile_width(igg_dtype dt);
-int tma_tile_rows();
+int tma_tile_width(igg_dtype dt, int variant);
+int tma_tile_rows(igg_dtype dt, int variant);
 bool tma_available();
 // Sets the kernel's shared-memory attribute and returns its resident CTAs per
 // SM; call before launching (and before any stream capture).
-cudaError_t tma_prepare(igg_dtype dt, int *ctas_per_sm);
-cudaError_t launch_stencil_tma(igg_dtype dt, const TmaTile *tiles, int ntiles, void *T2,
-                               const void *T, const void *Ci, int nx, int ny, long long nzt,
-                               const Coef &c, unsigned *dev_err, cudaStream_t s);
+cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
+cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
+                               void *T2, const void *T, const void *Ci, int nx, int ny,
+                               long long nzt, const Coef &c, unsigned *dev_err, cudaStream_t s);
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.

@@ -73,16 +73,18 @@ struct DeviceGuard {
 };
 
 // Device tile table of one launch: Tile (scalar kernel, V = 1), VTile
-// (vector kernel) or TmaTile (TMA kernel, tma = true).
+// (vector kernel) or TmaTile (TMA kernel variant tma >= 0).
 struct TileSet {
   void *dev = nullptr;
   int n = 0;
   int V = 1;
-  bool tma = false;
+  int tma = -1;
 };
 
+// The split: boundary set (one launch per tile kind) and inner block.
 struct SplitTiles {
-  TileSet boundary, inner;
+  std::vector<TileSet> boundary;
+  TileSet inner;
 };
 
 using GraphKey = std::tuple<const void *, const void *, const void *, int, int, int, int, int,
@@ -236,30 +238,33 @@ long long tma_xy_tiles(int x0, int x1, int y0, int y1, int V, int Wt, int Ht) {
   return (long long)((x1 - a0 + Wt - 1) / Wt) * ((y1 - y0 + Ht - 1) / Ht);
 }
 
-// resident-CTA slots of the TMA kernel for the dtype of vector width V
-long long tma_slots(int V) {
+// resident-CTA slots of a TMA kernel variant for the dtype of vector width V
+long long tma_slots(int V, int variant = TMA_WIDE) {
   int per_sm = 1, sms = 152, dev = 0;
-  if (tma_prepare(dtype_of_vec(V), &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (tma_prepare(dtype_of_vec(V), variant, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return (long long)per_sm * sms;
 }
 
-// Tiles of the TMA kernel for one regular box of subdomain plane offset zoff.
-void add_box_tma(std::vector<TmaTile> &v, long long base, long long zoff, int x0, int x1, int y0,
-                 int y1, int z0, int z1, int zb, int V, int Wt, int Ht) {
-  if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;
-  for (int zc = z0; zc < z1; zc += zb)
-    for (int y = y0; y < y1; y += Ht)
+// Tiles of a TMA kernel variant for one box of the subdomain whose planes
+// start at zoff. Rows run over [r0, r1) in blocks of Ht, the march over
+// [m0, m1) in chunks of mb: rows y / march z, or (swapped variant) rows z /
+// march y.
+void add_box_tma(std::vector<TmaTile> &v, long long base, long long zoff, int x0, int x1, int r0,
+                 int r1, int m0, int m1, int mb, int V, int Wt, int Ht) {
+  if (x0 >= x1 || r0 >= r1 || m0 >= m1) return;
+  for (int mc = m0; mc < m1; mc += mb)
+    for (int r = r0; r < r1; r += Ht)
       for (int xa = (x0 / V) * V; xa < x1; xa += Wt) {
         TmaTile t;
         t.base = base;
         t.x0 = xa;
         t.xb = std::max(x0, xa);
         t.xe = std::min(x1, xa + Wt);
-        t.y0 = y;
-        t.ye = std::min(y + Ht, y1);
-        t.z0 = zc;
-        t.z1 = std::min(zc + zb, z1);
+        t.r0 = r;
+        t.re = std::min(r + Ht, r1);
+        t.m0 = mc;
+        t.m1 = std::min(mc + mb, m1);
         t.zoff = (int)zoff;
         t.pad[0] = t.pad[1] = 0;
         v.push_back(t);
@@ -295,10 +300,10 @@ int upload_vec(const std::vector<TT> &v, TileSet *out) {
   return IGG_OK;
 }
 
-int upload_tiles(const TileLists &v, int V, TileSet *out, bool tma = false) {
+int upload_tiles(const TileLists &v, int V, TileSet *out, int tma = -1) {
   out->V = V;
   out->tma = tma;
-  if (tma) return upload_vec(v.tma, out);
+  if (tma >= 0) return upload_vec(v.tma, out);
   return V > 1 ? upload_vec(v.vec, out) : upload_vec(v.scalar, out);
 }
 
@@ -373,7 +378,8 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
   const int zb = choose_zb(xy, nz - 2);
   TileLists v;
   const bool tma = use_tma(g, V);
-  const int Wt = tma ? tma_tile_width(dtype_of_vec(V)) : 0, Ht = tma_tile_rows();
+  const int Wt = tma ? tma_tile_width(dtype_of_vec(V), TMA_WIDE) : 0;
+  const int Ht = tma ? tma_tile_rows(dtype_of_vec(V), TMA_WIDE) : 0;
   const int zbt = tma ? choose_zb_tma(tma_xy_tiles(1, nx - 1, 1, ny - 1, V, Wt, Ht) * g->nsub,
                                       nz - 2, tma_slots(V))
                       : 0;
@@ -385,7 +391,7 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
       add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
   }
   TileSet ts;
-  if (int rc = upload_tiles(v, V, &ts, tma)) return rc;
+  if (int rc = upload_tiles(v, V, &ts, tma ? TMA_WIDE : -1)) return rc;
   *out = &g->full.emplace(V, ts).first->second;
   return IGG_OK;
 }
@@ -417,30 +423,56 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
   // side instead of a few long latency-bound sweeps on the critical path
   const int zb_b = std::min(8, choose_zb(xy_b * g->nsub, zh - zl > 0 ? zh - zl : 1));
   const int zb_i = choose_zb(xy_i * g->nsub, zh - zl > 0 ? zh - zl : 1);
-  const int Wt_i = use_tma(g, V) ? tma_tile_width(dtype_of_vec(V)) : 0;
-  const int zbt_i = use_tma(g, V)
-                        ? choose_zb_tma(tma_xy_tiles(xl, xh, yl, yh, V, Wt_i, tma_tile_rows()) * g->nsub,
-                                        zh - zl > 0 ? zh - zl : 1, tma_slots(V))
-                        : 0;
-  for (int s = 0; s < g->nsub; ++s) {
-    const long long base = (long long)s * g->nloc;
-    add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, ny - 1, 1, zl, 64, 0);          // z low
-    add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, 0);     // z high
-    add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, yl, zl, zh, zb_b, 0);           // y low
-    add_tiles(vb, V, base, nx, ny, 1, nx - 1, yh, ny - 1, zl, zh, zb_b, 0);      // y high
-    add_tiles(vb, V, base, nx, ny, 1, xl, yl, yh, zl, zh, zb_b, 0);              // x low
-    add_tiles(vb, V, base, nx, ny, xh, nx - 1, yl, yh, zl, zh, zb_b, 0);         // x high
-    if (use_tma(g, V))                                                              // inner block
-      add_box_tma(vi.tma, base, (long long)s * nz, xl, xh, yl, yh, zl, zh, zbt_i, V, Wt_i,
-                  tma_tile_rows());
-    else
-      add_tiles(vi, V, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);
-  }
   SplitTiles st;
-  int rc = upload_tiles(vb, V, &st.boundary);
-  if (rc == IGG_OK) rc = upload_tiles(vi, V, &st.inner, use_tma(g, V));
+  int rc = IGG_OK;
+  if (use_tma(g, V)) {
+    // TMA: z slabs with wide tiles, y slabs with wide tiles marching along y
+    // (rows along z), x slabs with narrow tiles, inner block with wide tiles
+    const igg_dtype d = dtype_of_vec(V);
+    const int Ww = tma_tile_width(d, TMA_WIDE), Hw = tma_tile_rows(d, TMA_WIDE);
+    const int Wn = tma_tile_width(d, TMA_NARROW), Hn = tma_tile_rows(d, TMA_NARROW);
+    TileLists wz, sy, nxs;
+    const int zbt_i = choose_zb_tma(tma_xy_tiles(xl, xh, yl, yh, V, Ww, Hw) * g->nsub,
+                                    zh - zl > 0 ? zh - zl : 1, tma_slots(V));
+    for (int s = 0; s < g->nsub; ++s) {
+      const long long base = (long long)s * g->nloc, zoff = (long long)s * nz;
+      add_box_tma(wz.tma, base, zoff, 1, nx - 1, 1, ny - 1, 1, zl, 64, V, Ww, Hw);          // z low
+      add_box_tma(wz.tma, base, zoff, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, V, Ww, Hw);     // z high
+      add_box_tma(sy.tma, base, zoff, 1, nx - 1, zl, zh, 1, yl, 64, V, Ww, Hw);            // y low
+      add_box_tma(sy.tma, base, zoff, 1, nx - 1, zl, zh, yh, ny - 1, 64, V, Ww, Hw);       // y high
+      add_box_tma(nxs.tma, base, zoff, 1, xl, yl, yh, zl, zh, 32, V, Wn, Hn);              // x low
+      add_box_tma(nxs.tma, base, zoff, xh, nx - 1, yl, yh, zl, zh, 32, V, Wn, Hn);         // x high
+      add_box_tma(vi.tma, base, zoff, xl, xh, yl, yh, zl, zh, zbt_i, V, Ww, Hw);           // inner
+    }
+    const std::pair<TileLists *, int> parts[3] = {
+        {&nxs, TMA_NARROW}, {&wz, TMA_WIDE}, {&sy, TMA_WIDE_SWAP}};
+    for (auto &pt : parts) {
+      if (pt.first->tma.empty()) continue;
+      TileSet ts;
+      if ((rc = upload_tiles(*pt.first, V, &ts, pt.second)) != IGG_OK) break;
+      st.boundary.push_back(ts);
+    }
+    if (rc == IGG_OK) rc = upload_tiles(vi, V, &st.inner, TMA_WIDE);
+  } else {
+    for (int s = 0; s < g->nsub; ++s) {
+      const long long base = (long long)s * g->nloc;
+      add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, ny - 1, 1, zl, 64, 0);          // z low
+      add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, 0);     // z high
+      add_tiles(vb, V, base, nx, ny, 1, nx - 1, 1, yl, zl, zh, zb_b, 0);           // y low
+      add_tiles(vb, V, base, nx, ny, 1, nx - 1, yh, ny - 1, zl, zh, zb_b, 0);      // y high
+      add_tiles(vb, V, base, nx, ny, 1, xl, yl, yh, zl, zh, zb_b, 0);              // x low
+      add_tiles(vb, V, base, nx, ny, xh, nx - 1, yl, yh, zl, zh, zb_b, 0);         // x high
+      add_tiles(vi, V, base, nx, ny, xl, xh, yl, yh, zl, zh, zb_i, 0);             // inner block
+    }
+    TileSet tb;
+    rc = upload_tiles(vb, V, &tb);
+    if (rc == IGG_OK) {
+      st.boundary.push_back(tb);
+      rc = upload_tiles(vi, V, &st.inner);
+    }
+  }
   if (rc != IGG_OK) {
-    cudaFree(st.boundary.dev);
+    for (auto &b : st.boundary) cudaFree(b.dev);
     cudaFree(st.inner.dev);
     return rc;
   }
@@ -451,9 +483,9 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
 
 cudaError_t launch_tiles(const igg_grid *g, int V, igg_dtype dt, const TileSet &ts, void *T2,
                          const void *T, const void *Ci, const Coef &c, cudaStream_t s) {
-  if (ts.tma)
-    return launch_stencil_tma(dt, (const TmaTile *)ts.dev, ts.n, T2, T, Ci, g->n[0], g->n[1],
-                              (long long)g->nsub * g->n[2], c, g->dev_err, s);
+  if (ts.tma >= 0)
+    return launch_stencil_tma(dt, ts.tma, (const TmaTile *)ts.dev, ts.n, T2, T, Ci, g->n[0],
+                              g->n[1], (long long)g->nsub * g->n[2], c, g->dev_err, s);
   if (V > 1) return launch_stencil_vec(dt, (const VTile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
   return launch_stencil(dt, (const Tile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
@@ -519,7 +551,9 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   if ((e = cudaEventRecord(g->ev_fork, s)) != cudaSuccess) return cuda_error(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(g->hi, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
   if ((e = cudaStreamWaitEvent(g->lo, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
-  e = launch_tiles(g, V, dt, st->boundary, T2, T, Ci, c, g->hi);
+  e = cudaSuccess;
+  for (const TileSet &b : st->boundary)
+    if (e == cudaSuccess) e = launch_tiles(g, V, dt, b, T2, T, Ci, c, g->hi);
   if (e == cudaSuccess && any_halo(g)) e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
   if (e != cudaSuccess) return cuda_error(e, "boundary/halo launch");
   e = launch_tiles(g, V, dt, st->inner, T2, T, Ci, c, g->lo);
@@ -545,7 +579,7 @@ void destroy_grid(igg_grid *g) {
   if (!g) return;
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &kv : g->split) {
-    cudaFree(kv.second.boundary.dev);
+    for (auto &b : kv.second.boundary) cudaFree(b.dev);
     cudaFree(kv.second.inner.dev);
   }
   for (auto &kv : g->full) cudaFree(kv.second.dev);
@@ -1008,7 +1042,7 @@ int igg_grid_set_option(igg_grid *g, int option, int value) {
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   for (auto &kv : g->split) {
-    cudaFree(kv.second.boundary.dev);
+    for (auto &b : kv.second.boundary) cudaFree(b.dev);
     cudaFree(kv.second.inner.dev);
   }
   g->split.clear();

@@ -30,13 +30,25 @@
 namespace igg {
 namespace {
 
+// Tile shapes: lanes per row LPR (W = LPR*V points), H rows.
 template <class S>
+struct WideShape {
+  static constexpr int LPR = sizeof(S) == 2 ? 16 : 32;
+  static constexpr int H = 16;
+};
+template <class S>
+struct NarrowShape {  // 16-point rows (x slabs), one row per 16/V... lanes
+  static constexpr int LPR = 16 / (16 / (int)sizeof(S));
+  static constexpr int H = 8 * (32 / LPR);
+};
+
+template <class S, int LPR_, int H_>
 struct TmaShape {
   static constexpr int V = 16 / (int)sizeof(S);
-  static constexpr int LPR = sizeof(S) == 2 ? 16 : 32;  // lanes per row
+  static constexpr int LPR = LPR_;                      // lanes per row
   static constexpr int W = LPR * V;                     // computed points per row
   static constexpr int BW = W + 2 * V;                  // T box width (vector halo each side)
-  static constexpr int H = 16;                          // rows per tile
+  static constexpr int H = H_;                          // rows per tile
   static constexpr int BH = H + 2;                      // T box height (row halo)
   static constexpr int NS = 4;                          // stages
   static constexpr int CONSUMERS = 8;                   // consumer warps
@@ -112,12 +124,16 @@ __device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);
 }
 
-template <class S>
-__global__ void __launch_bounds__(32 * (TmaShape<S>::CONSUMERS + 1))
+// SWAP = false: rows along y, march along z (box {BW, BH, 1}); SWAP = true:
+// rows along z, march along y (box {BW, 1, BH}), for boxes thin in y. The
+// cell arithmetic gets the y and z neighbour pairs in their own slots either
+// way, so both orientations give the same bits.
+template <class S, int LPR_, int H_, bool SWAP>
+__global__ void __launch_bounds__(32 * 9)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
                   unsigned *__restrict__ dev_err) {
-  using Sh = TmaShape<S>;
+  using Sh = TmaShape<S, LPR_, H_>;
   using C = typename Num<S>::C;
   constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -128,7 +144,7 @@ __global__ void __launch_bounds__(32 * (TmaShape<S>::CONSUMERS + 1))
   // flags[0]: abort; flags[1]: loads issued; flags[2]: loads consumed
 
   const TmaTile t = tiles[blockIdx.x];
-  const int K = (t.z1 - t.z0) + 2;
+  const int K = (t.m1 - t.m0) + 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -159,8 +175,14 @@ __global__ void __launch_bounds__(32 * (TmaShape<S>::CONSUMERS + 1))
         const unsigned bar = full0 + 8 * s;
         const unsigned dst = sbase + s * Sh::STAGE;
         mbar_expect_tx(bar, Sh::TB + Sh::CB);
-        tma_load_3d(dst, &mapT, t.x0 - V, t.y0 - 1, t.zoff + t.z0 - 1 + k, bar);
-        tma_load_3d(dst + Sh::TBA, &mapC, t.x0, t.y0, t.zoff + t.z0 - 2 + k, bar);
+        const int mT = t.m0 - 1 + k, mC = t.m0 - 2 + k;  // march index of the T / Ci plane
+        if (!SWAP) {
+          tma_load_3d(dst, &mapT, t.x0 - V, t.r0 - 1, t.zoff + mT, bar);
+          tma_load_3d(dst + Sh::TBA, &mapC, t.x0, t.r0, t.zoff + mC, bar);
+        } else {
+          tma_load_3d(dst, &mapT, t.x0 - V, mT, t.zoff + t.r0 - 1, bar);
+          tma_load_3d(dst + Sh::TBA, &mapC, t.x0, mC, t.zoff + t.r0, bar);
+        }
       }
       flags[1] = k;
     }
@@ -174,10 +196,11 @@ __global__ void __launch_bounds__(32 * (TmaShape<S>::CONSUMERS + 1))
 #pragma unroll
     for (int j = 0; j < Sh::RPT; ++j) {
       rowi[j] = warp * (32 / LPR) + lane / LPR + j * Sh::ROWS_PER_PASS;  // row in the tile
-      comp[j] = (t.y0 + rowi[j] < t.ye) && xs + V > t.xb && xs < t.xe;
+      comp[j] = (t.r0 + rowi[j] < t.re) && xs + V > t.xb && xs < t.xe;
     }
     const bool full_vec = xs >= t.xb && xs + V <= t.xe;
     const long long sy = nx, sz = (long long)nx * ny;
+    const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
     Vec<S> zm[Sh::RPT];
     bool ok = mbar_wait(full0, 0);
     if (!ok) {
@@ -191,8 +214,8 @@ __global__ void __launch_bounds__(32 * (TmaShape<S>::CONSUMERS + 1))
       if (lane == 0) mbar_arrive(empty0);
     }
     int consumed = 1;
-    for (int z = t.z0; ok && z < t.z1; ++z) {
-      const int k = z - t.z0 + 1;
+    for (int m = t.m0; ok && m < t.m1; ++m) {
+      const int k = m - t.m0 + 1;
       const int s = k % NS, s1 = (k + 1) % NS;
       if (!mbar_wait(full0 + 8 * s, (k / NS) & 1) ||
           !mbar_wait(full0 + 8 * s1, ((k + 1) / NS) & 1)) {
@@ -225,9 +248,13 @@ __global__ void __launch_bounds__(32 * (TmaShape<S>::CONSUMERS + 1))
           for (int i = 0; i < V; ++i) {
             const C xm = i == 0 ? left : c.v[i - 1];
             const C xp = i == V - 1 ? right : c.v[i + 1];
-            out.v[i] = cell(c.v[i], xm, xp, up.v[i], dn.v[i], zm[j].v[i], zp.v[i], ci.v[i], w);
+            // (up, dn) are the row pair, (zm, zp) the march pair
+            if (!SWAP)
+              out.v[i] = cell(c.v[i], xm, xp, up.v[i], dn.v[i], zm[j].v[i], zp.v[i], ci.v[i], w);
+            else
+              out.v[i] = cell(c.v[i], xm, xp, zm[j].v[i], zp.v[i], up.v[i], dn.v[i], ci.v[i], w);
           }
-          S *dst = T2 + t.base + xs + sy * (t.y0 + r) + sz * z;
+          S *dst = T2 + t.base + xs + srow * (t.r0 + r) + smarch * m;
           if (full_vec) {
             *reinterpret_cast<uint4 *>(dst) = pack(out);
           } else {
@@ -273,7 +300,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 template <class S>
-bool encode(CUtensorMap *m, const void *base, int nx, int ny, long long nzt, int bx, int by) {
+bool encode(CUtensorMap *m, const void *base, int nx, int ny, long long nzt, int bx, int by,
+            int bz) {
   auto fn = encode_fn();
   if (!fn) return false;
   CUtensorMapDataType t = sizeof(S) == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -281,69 +309,110 @@ bool encode(CUtensorMap *m, const void *base, int nx, int ny, long long nzt, int
                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nzt};
   const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(S), (cuuint64_t)nx * ny * sizeof(S)};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, t, 3, const_cast<void *>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <class S>
+template <class S, class Shp, bool SWAP>
 cudaError_t prepare_t(int *ctas_per_sm) {
-  using Sh = TmaShape<S>;
-  cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Sh::SMEM);
+  using Sh = TmaShape<S, Shp::LPR, Shp::H>;
+  cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<S, Shp::LPR, Shp::H, SWAP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   if (e == cudaSuccess && ctas_per_sm)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_stencil_tma<S>,
-                                                      32 * (Sh::CONSUMERS + 1), Sh::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        ctas_per_sm, k_stencil_tma<S, Shp::LPR, Shp::H, SWAP>, 32 * (Sh::CONSUMERS + 1), Sh::SMEM);
   return e;
 }
 
-template <class S>
+template <class S, class Shp, bool SWAP>
 cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
                      cudaStream_t s) {
-  using Sh = TmaShape<S>;
+  using Sh = TmaShape<S, Shp::LPR, Shp::H>;
   CUtensorMap mT, mC;
-  if (!encode<S>(&mT, T, nx, ny, nzt, Sh::BW, Sh::BH) || !encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, Sh::H))
-    return cudaErrorInvalidValue;
-  k_stencil_tma<S><<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny,
-                                                                      c, dev_err);
+  const bool ok = SWAP ? encode<S>(&mT, T, nx, ny, nzt, Sh::BW, 1, Sh::BH) &&
+                             encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, 1, Sh::H)
+                       : encode<S>(&mT, T, nx, ny, nzt, Sh::BW, Sh::BH, 1) &&
+                             encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, Sh::H, 1);
+  if (!ok) return cudaErrorInvalidValue;
+  k_stencil_tma<S, Shp::LPR, Shp::H, SWAP><<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(
+      mT, mC, tiles, (S *)T2, nx, ny, c, dev_err);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-int tma_tile_width(igg_dtype dt) {
-  switch (dt) {
-    case IGG_F64: return TmaShape<double>::W;
-    case IGG_F32: return TmaShape<float>::W;
-    case IGG_BF16: return TmaShape<__nv_bfloat16>::W;
-  }
-  return 0;
-}
-int tma_tile_rows() { return TmaShape<float>::H; }
-
-bool tma_available() { return encode_fn() != nullptr; }
-
-cudaError_t tma_prepare(igg_dtype dt, int *ctas_per_sm) {
-  switch (dt) {
-    case IGG_F64: return prepare_t<double>(ctas_per_sm);
-    case IGG_F32: return prepare_t<float>(ctas_per_sm);
-    case IGG_BF16: return prepare_t<__nv_bfloat16>(ctas_per_sm);
+template <class S>
+cudaError_t prepare_v(int variant, int *ctas) {
+  switch (variant) {
+    case TMA_WIDE: return prepare_t<S, WideShape<S>, false>(ctas);
+    case TMA_NARROW: return prepare_t<S, NarrowShape<S>, false>(ctas);
+    case TMA_WIDE_SWAP: return prepare_t<S, WideShape<S>, true>(ctas);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_stencil_tma(igg_dtype dt, const TmaTile *tiles, int ntiles, void *T2,
-                               const void *T, const void *Ci, int nx, int ny, long long nzt,
-                               const Coef &c, unsigned *dev_err, cudaStream_t s) {
+template <class S>
+cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, const void *T,
+                     const void *Ci, int nx, int ny, long long nzt, const Coef &c,
+                     unsigned *dev_err, cudaStream_t s) {
+  switch (variant) {
+    case TMA_WIDE:
+      return launch_t<S, WideShape<S>, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+    case TMA_NARROW:
+      return launch_t<S, NarrowShape<S>, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+    case TMA_WIDE_SWAP:
+      return launch_t<S, WideShape<S>, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int tma_tile_width(igg_dtype dt, int variant) {
+  const bool narrow = variant == TMA_NARROW;
+  switch (dt) {
+    case IGG_F64: return narrow ? NarrowShape<double>::LPR * 2 : WideShape<double>::LPR * 2;
+    case IGG_F32: return narrow ? NarrowShape<float>::LPR * 4 : WideShape<float>::LPR * 4;
+    case IGG_BF16:
+      return narrow ? NarrowShape<__nv_bfloat16>::LPR * 8 : WideShape<__nv_bfloat16>::LPR * 8;
+  }
+  return 0;
+}
+
+int tma_tile_rows(igg_dtype dt, int variant) {
+  const bool narrow = variant == TMA_NARROW;
+  switch (dt) {
+    case IGG_F64: return narrow ? NarrowShape<double>::H : WideShape<double>::H;
+    case IGG_F32: return narrow ? NarrowShape<float>::H : WideShape<float>::H;
+    case IGG_BF16: return narrow ? NarrowShape<__nv_bfloat16>::H : WideShape<__nv_bfloat16>::H;
+  }
+  return 0;
+}
+
+bool tma_available() { return encode_fn() != nullptr; }
+
+cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
+  switch (dt) {
+    case IGG_F64: return prepare_v<double>(variant, ctas_per_sm);
+    case IGG_F32: return prepare_v<float>(variant, ctas_per_sm);
+    case IGG_BF16: return prepare_v<__nv_bfloat16>(variant, ctas_per_sm);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
+                               void *T2, const void *T, const void *Ci, int nx, int ny,
+                               long long nzt, const Coef &c, unsigned *dev_err, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   switch (dt) {
-    case IGG_F64: return launch_t<double>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
-    case IGG_F32: return launch_t<float>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+    case IGG_F64:
+      return launch_v<double>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+    case IGG_F32:
+      return launch_v<float>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
     case IGG_BF16:
-      return launch_t<__nv_bfloat16>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+      return launch_v<__nv_bfloat16>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -265,6 +265,7 @@ def test_widths_below_overlap_rejected():
     ((64, 37, 29), (2, 1, 2), (1, 0, 0), (2, 2, 2), (16, 2, 2)),
     ((144, 40, 70), (1, 2, 1), (0, 1, 0), (2, 2, 2), (3, 4, 5)),
     ((256, 33, 18), (2, 2, 2), (1, 0, 1), (2, 3, 2), (16, 3, 2)),
+    ((64, 37, 29), (1, 1, 2), (0, 0, 0), (2, 2, 2), (40, 20, 20)),  # empty inner block
 ])
 def test_tma_and_vector_kernels_same_bits(dtype, n, dims, periods, overlap, widths):
     """The TMA-pipelined kernel and the register-pipelined vector kernel give
