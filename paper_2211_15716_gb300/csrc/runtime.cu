@@ -448,6 +448,12 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
         {&nxs, TMA_NARROW}, {&wz, TMA_WIDE}, {&sy, TMA_WIDE_SWAP}};
     for (auto &pt : parts) {
       if (pt.first->tma.empty()) continue;
+      // each kernel variant needs its shared-memory attribute before launch
+      cudaError_t e = tma_prepare(d, pt.second, nullptr);
+      if (e != cudaSuccess) {
+        rc = cuda_error(e, "TMA kernel set-up");
+        break;
+      }
       TileSet ts;
       if ((rc = upload_tiles(*pt.first, V, &ts, pt.second)) != IGG_OK) break;
       st.boundary.push_back(ts);
