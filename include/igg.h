@@ -162,7 +162,11 @@ int igg_step(igg_grid *grid, void *T2, const void *T, const void *Ci,
  * widths[d]) runs first on the library's high-priority stream, followed
  * there by the halo update of T2; the inner block runs concurrently on the
  * low-priority stream; `stream` waits for both. Requires widths[d] >=
- * overlap[d] (so all sent planes are in the boundary set). The result is
+ * overlap[d] (so all sent planes are in the boundary set). The boundary
+ * launches compute whole tiles of the kernel: inner-block points that share
+ * a tile with boundary points are computed there as well (before the halo
+ * update), and the low-priority launch covers the remaining inner block.
+ * Every point is computed once with the same arithmetic, so the result is
  * bit-identical to igg_step followed by igg_update_halo(T2). */
 int igg_step_hidden(igg_grid *grid, const int widths[3], void *T2,
                     const void *T, const void *Ci, igg_dtype dtype, double lam,

@@ -99,9 +99,8 @@ cudaError_t launch_stencil_persistent(igg_dtype dt, int variant, const Tile *til
 // a multiple of V; the tile spans tma_tile_width points), rows r0 <= r < re
 // (at most tma_tile_rows) and march steps m0 <= m < m1 of the array at
 // element offset `base`, which starts at plane zoff of the field seen as one
-// stack of nsub*nz planes. Variants: TMA_WIDE (rows along y, march along z),
-// TMA_NARROW (the same with 16-point rows, for x slabs) and TMA_WIDE_SWAP
-// (rows along z, march along y, for y slabs).
+// stack of nsub*nz planes. Variants: TMA_WIDE (rows along y, march along z)
+// and TMA_WIDE_SWAP (rows along z, march along y, for y slabs).
 struct TmaTile {
   long long base;
   int x0, xb, xe;
@@ -110,7 +109,7 @@ struct TmaTile {
   int zoff;
   int pad[2];
 };
-enum { TMA_WIDE = 0, TMA_NARROW = 1, TMA_WIDE_SWAP = 2 };
+enum { TMA_WIDE = 0, TMA_WIDE_SWAP = 2 };
 static_assert(sizeof(TmaTile) == 48, "TmaTile layout");
 // bits of the device error word: IGG_DEV_ERR_TIMEOUT, IGG_DEV_ERR_DRAIN (igg.h)
 int tma_tile_width(igg_dtype dt, int variant);

@@ -427,25 +427,34 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
   int rc = IGG_OK;
   if (use_tma(g, V)) {
     // TMA: z slabs with wide tiles, y slabs with wide tiles marching along y
-    // (rows along z), x slabs with narrow tiles, inner block with wide tiles
+    // (rows along z). The x slabs are widened to whole wide tiles at both
+    // ends of each row (narrow boxes make short TMA rows); the inner-block
+    // points inside those tiles are computed there, before the halo update,
+    // and the inner-block launch covers the rest. Every point is computed
+    // exactly once with the same arithmetic, so the result is unchanged.
     const igg_dtype d = dtype_of_vec(V);
     const int Ww = tma_tile_width(d, TMA_WIDE), Hw = tma_tile_rows(d, TMA_WIDE);
-    const int Wn = tma_tile_width(d, TMA_NARROW), Hn = tma_tile_rows(d, TMA_NARROW);
-    TileLists wz, sy, nxs;
-    const int zbt_i = choose_zb_tma(tma_xy_tiles(xl, xh, yl, yh, V, Ww, Hw) * g->nsub,
+    int xlw = std::min(std::max(xl, (xl + Ww - 1) / Ww * Ww), nx - 1);
+    int xhw = std::max(xlw, std::min(xh, std::max(1, ((nx - Ww) / V) * V)));
+    TileLists wz, sy, wx;
+    const int zbt_i = choose_zb_tma(tma_xy_tiles(xlw, xhw, yl, yh, V, Ww, Hw) * g->nsub,
                                     zh - zl > 0 ? zh - zl : 1, tma_slots(V));
+    const int zbt_x = choose_zb_tma(
+        (tma_xy_tiles(1, xlw, yl, yh, V, Ww, Hw) + tma_xy_tiles(xhw, nx - 1, yl, yh, V, Ww, Hw)) *
+            g->nsub,
+        zh - zl > 0 ? zh - zl : 1, tma_slots(V));
     for (int s = 0; s < g->nsub; ++s) {
       const long long base = (long long)s * g->nloc, zoff = (long long)s * nz;
       add_box_tma(wz.tma, base, zoff, 1, nx - 1, 1, ny - 1, 1, zl, 64, V, Ww, Hw);          // z low
       add_box_tma(wz.tma, base, zoff, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, V, Ww, Hw);     // z high
       add_box_tma(sy.tma, base, zoff, 1, nx - 1, zl, zh, 1, yl, 64, V, Ww, Hw);            // y low
       add_box_tma(sy.tma, base, zoff, 1, nx - 1, zl, zh, yh, ny - 1, 64, V, Ww, Hw);       // y high
-      add_box_tma(nxs.tma, base, zoff, 1, xl, yl, yh, zl, zh, 32, V, Wn, Hn);              // x low
-      add_box_tma(nxs.tma, base, zoff, xh, nx - 1, yl, yh, zl, zh, 32, V, Wn, Hn);         // x high
-      add_box_tma(vi.tma, base, zoff, xl, xh, yl, yh, zl, zh, zbt_i, V, Ww, Hw);           // inner
+      add_box_tma(wx.tma, base, zoff, 1, xlw, yl, yh, zl, zh, zbt_x, V, Ww, Hw);           // x low
+      add_box_tma(wx.tma, base, zoff, xhw, nx - 1, yl, yh, zl, zh, zbt_x, V, Ww, Hw);      // x high
+      add_box_tma(vi.tma, base, zoff, xlw, xhw, yl, yh, zl, zh, zbt_i, V, Ww, Hw);         // inner
     }
     const std::pair<TileLists *, int> parts[3] = {
-        {&nxs, TMA_NARROW}, {&wz, TMA_WIDE}, {&sy, TMA_WIDE_SWAP}};
+        {&wz, TMA_WIDE}, {&sy, TMA_WIDE_SWAP}, {&wx, TMA_WIDE}};
     for (auto &pt : parts) {
       if (pt.first->tma.empty()) continue;
       // each kernel variant needs its shared-memory attribute before launch

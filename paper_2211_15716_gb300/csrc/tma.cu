@@ -36,11 +36,6 @@ struct WideShape {
   static constexpr int LPR = sizeof(S) == 2 ? 16 : 32;
   static constexpr int H = 16;
 };
-template <class S>
-struct NarrowShape {  // 16-point rows (x slabs), one row per 16/V... lanes
-  static constexpr int LPR = 16 / (16 / (int)sizeof(S));
-  static constexpr int H = 8 * (32 / LPR);
-};
 
 template <class S, int LPR_, int H_>
 struct TmaShape {
@@ -347,7 +342,6 @@ template <class S>
 cudaError_t prepare_v(int variant, int *ctas) {
   switch (variant) {
     case TMA_WIDE: return prepare_t<S, WideShape<S>, false>(ctas);
-    case TMA_NARROW: return prepare_t<S, NarrowShape<S>, false>(ctas);
     case TMA_WIDE_SWAP: return prepare_t<S, WideShape<S>, true>(ctas);
   }
   return cudaErrorInvalidValue;
@@ -360,8 +354,6 @@ cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, co
   switch (variant) {
     case TMA_WIDE:
       return launch_t<S, WideShape<S>, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
-    case TMA_NARROW:
-      return launch_t<S, NarrowShape<S>, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
     case TMA_WIDE_SWAP:
       return launch_t<S, WideShape<S>, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
   }
@@ -370,23 +362,20 @@ cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, co
 
 }  // namespace
 
-int tma_tile_width(igg_dtype dt, int variant) {
-  const bool narrow = variant == TMA_NARROW;
+int tma_tile_width(igg_dtype dt, int) {
   switch (dt) {
-    case IGG_F64: return narrow ? NarrowShape<double>::LPR * 2 : WideShape<double>::LPR * 2;
-    case IGG_F32: return narrow ? NarrowShape<float>::LPR * 4 : WideShape<float>::LPR * 4;
-    case IGG_BF16:
-      return narrow ? NarrowShape<__nv_bfloat16>::LPR * 8 : WideShape<__nv_bfloat16>::LPR * 8;
+    case IGG_F64: return WideShape<double>::LPR * 2;
+    case IGG_F32: return WideShape<float>::LPR * 4;
+    case IGG_BF16: return WideShape<__nv_bfloat16>::LPR * 8;
   }
   return 0;
 }
 
-int tma_tile_rows(igg_dtype dt, int variant) {
-  const bool narrow = variant == TMA_NARROW;
+int tma_tile_rows(igg_dtype dt, int) {
   switch (dt) {
-    case IGG_F64: return narrow ? NarrowShape<double>::H : WideShape<double>::H;
-    case IGG_F32: return narrow ? NarrowShape<float>::H : WideShape<float>::H;
-    case IGG_BF16: return narrow ? NarrowShape<__nv_bfloat16>::H : WideShape<__nv_bfloat16>::H;
+    case IGG_F64: return WideShape<double>::H;
+    case IGG_F32: return WideShape<float>::H;
+    case IGG_BF16: return WideShape<__nv_bfloat16>::H;
   }
   return 0;
 }
