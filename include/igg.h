@@ -134,11 +134,19 @@ int igg_update_halo(igg_grid *grid, void *const fields[], int nfields,
 #define IGG_DEV_ERR_DRAIN 2u
 int igg_device_status(igg_grid *grid, unsigned *status, int clear);
 
-/* Grid options. IGG_OPT_TMA (default 1): run the full step and the inner
- * block with the TMA-pipelined kernel when the row length is a multiple of
- * 16 bytes; 0 selects the register-pipelined vector kernel. Results are
- * bit-identical either way. Waits for the grid's streams. */
+/* Grid options (wait for the grid's streams; cached CUDA graphs are
+ * rebuilt):
+ *   IGG_OPT_TMA (default 1): run the regular boxes of the step with the
+ *     TMA-pipelined kernel when the row length is a multiple of 16 bytes; 0
+ *     selects the register-pipelined vector kernel. Bit-identical results.
+ *   IGG_OPT_F64_EMU (default 1): F64 fields use the emulated FP64 cell: for
+ *     points whose 7 stencil values share sign and exponent, the second
+ *     differences are formed exactly in integers, weighted in float-float
+ *     and applied with two FP64 FMAs (per-step error about 2^-44 of
+ *     sum_d |w_d D_d| plus two FP64 roundings of T2); other points, and all
+ *     points with 0, use the FP64 cell (8 FP64 instructions per point). */
 #define IGG_OPT_TMA 1
+#define IGG_OPT_F64_EMU 2
 int igg_grid_set_option(igg_grid *grid, int option, int value);
 
 /* ---------------------------------------------------------------------------

@@ -55,17 +55,38 @@ struct W {
   C wx, wy, wz, wc;
 };
 
+// FP64 weights: the doubles, the same weights as float pairs wh + wl for the
+// emulated FP64 cell, and which cell to use.
+template <>
+struct W<double> {
+  double wx, wy, wz, wc;
+  float wh[3], wl[3];
+  bool emu;
+};
+
 __device__ __forceinline__ W<double> make_w(const Coef &c, double) {
-  return {c.wx, c.wy, c.wz, c.wc};
+  W<double> w;
+  w.wx = c.wx;
+  w.wy = c.wy;
+  w.wz = c.wz;
+  w.wc = c.wc;
+  const double d[3] = {c.wx, c.wy, c.wz};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    w.wh[i] = __double2float_rn(d[i]);
+    w.wl[i] = __double2float_rn(__dsub_rn(d[i], (double)w.wh[i]));
+  }
+  w.emu = c.f64_emu != 0;
+  return w;
 }
 __device__ __forceinline__ W<float> make_w(const Coef &c, float) {
   return {(float)c.wx, (float)c.wy, (float)c.wz, (float)c.wc};
 }
 
-// The update of one inner point (see the file comment for the order).
-__device__ __forceinline__ double cell(double t, double xm, double xp, double ym,
-                                       double yp, double zm, double zp, double ci,
-                                       const W<double> &w) {
+// The FP64 update of one inner point (see the file comment for the order).
+__device__ __forceinline__ double cell_f64(double t, double xm, double xp, double ym,
+                                           double yp, double zm, double zp, double ci,
+                                           const W<double> &w) {
   const double sx = __dadd_rn(xm, xp);
   const double sy = __dadd_rn(ym, yp);
   const double sz = __dadd_rn(zm, zp);
@@ -74,6 +95,111 @@ __device__ __forceinline__ double cell(double t, double xm, double xp, double ym
   l = __fma_rn(w.wy, sy, l);
   l = __fma_rn(w.wz, sz, l);
   return __fma_rn(ci, l, t);
+}
+
+
+// ---------------------------------------------------------------------------
+// FP64 update with FP32/integer arithmetic for the differences ("emulated
+// FP64"). GB300 issues about two FP64 instructions per SM and clock, so the
+// 8-instruction FP64 cell caps the step near a quarter of HBM speed; this cell
+// spends two FP64 FMAs per point and does the rest on the FP32, integer and
+// conversion pipes.
+//
+// When the seven values of a stencil share sign and exponent e, each is
+// M * 2^(e-52) with an integer mantissa M < 2^53 whose top 24 bits Mh lie in
+// [2^23, 2^24). The second difference in units u = 2^(e-52) is the integer
+//   D_d = (Mh[+d] + Mh[-d] - 2 Mh)*2^29 + (Ml[+d] + Ml[-d] - 2 Ml),
+// Ml the low 29 bits; the Mh part lies in (-2^24, 2^24) and the Ml part in
+// (-2^30, 2^30), so A = dMh*2^29, B1 = dMl rounded down to a multiple of 128
+// and B2 = dMl mod 128 are exact FP32 numbers with D_d = A + B1 + B2. An
+// error-free two-sum gives D_d = s_d + t_d to about 2^-48 relative; the
+// weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is formed with exact FMA
+// product splits and two-sums of the three leading products (S) plus the
+// small terms (C), to about 2^-44 of sum_d |w_d D_d|. Finally
+//   T2 = fma(Ci, S*u, fma(Ci, C*u, T))
+// in FP64 (S*u and C*u widened to FP64 exactly by bit manipulation).
+//
+// Points whose values differ in sign or exponent, or whose exponent leaves
+// the range of the FP32 scalings, take cell_f64. The choice depends only on
+// the point's inputs, so every kernel makes the same choice and produces the
+// same bits.
+// ---------------------------------------------------------------------------
+struct Split {
+  int mh;       // top 24 bits of the 53-bit mantissa (with the hidden 1)
+  int ml;       // low 29 bits
+  unsigned eh;  // sign and exponent field (upper 12 bits of the high word)
+};
+
+__device__ __forceinline__ Split split64(double v) {
+  const unsigned H = (unsigned)__double2hiint(v), L = (unsigned)__double2loint(v);
+  Split s;
+  s.eh = H & 0xFFF00000u;
+  s.mh = (int)__funnelshift_l(L, (H & 0x000FFFFFu) | 0x00100000u, 3);
+  s.ml = (int)(L & 0x1FFFFFFFu);
+  return s;
+}
+
+// float -> double by bit manipulation (exact for normal floats; zero and
+// subnormal floats give a signed zero)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, mag = b & 0x7FFFFFFFu;
+  if ((mag & 0x7F800000u) == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned hi = sign | ((mag >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// error-free sum of two floats: a + b = s + e exactly
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// One point from pre-split values: sc the centre, sn[6] the neighbours in the
+// order x-, x+, y-, y+, z-, z+ with their doubles in tn[6] (read only by the
+// fallback).
+__device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Split *sn,
+                                           const double *tn, double ci, const W<double> &w) {
+  const unsigned e = sc.eh;
+  const unsigned diff = (sn[0].eh ^ e) | (sn[1].eh ^ e) | (sn[2].eh ^ e) | (sn[3].eh ^ e) |
+                        (sn[4].eh ^ e) | (sn[5].eh ^ e);
+  const int E = (int)((e >> 20) & 0x7FFu);
+  if (diff != 0u || E < 949 || E > 1147)
+    return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+  float P[3], X[3], R[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int dmh = sn[2 * d].mh + sn[2 * d + 1].mh - 2 * sc.mh;
+    const int dml = sn[2 * d].ml + sn[2 * d + 1].ml - 2 * sc.ml;
+    const float A = __fmul_rn(__int2float_rn(dmh), 536870912.0f);  // dMh * 2^29, exact
+    const float B1 = __int2float_rn(dml & ~127);                    // exact
+    const float B2 = __int2float_rn(dml & 127);                     // exact
+    float err;
+    const float sd = two_sum(A, B1, err);
+    const float td = __fadd_rn(err, B2);
+    P[d] = __fmul_rn(w.wh[d], sd);
+    X[d] = __fmaf_rn(w.wh[d], sd, -P[d]);
+    R[d] = __fmaf_rn(w.wl[d], sd, __fmul_rn(w.wh[d], td));
+  }
+  float e1, e2;
+  const float S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
+  const float C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
+                            __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
+  const float u = __int_as_float((E - 948) << 23);  // 2^(e-52)
+  return __fma_rn(ci, f2d_bits(__fmul_rn(S, u)), __fma_rn(ci, f2d_bits(__fmul_rn(C, u)), tc));
+}
+
+// The FP64 update used by every kernel: the emulated cell or the FP64 cell.
+__device__ __forceinline__ double cell(double t, double xm, double xp, double ym, double yp,
+                                       double zm, double zp, double ci, const W<double> &w) {
+  if (!w.emu) return cell_f64(t, xm, xp, ym, yp, zm, zp, ci, w);
+  const double tn[6] = {xm, xp, ym, yp, zm, zp};
+  Split sn[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) sn[i] = split64(tn[i]);
+  return cell_emu(t, split64(t), sn, tn, ci, w);
 }
 
 __device__ __forceinline__ float cell(float t, float xm, float xp, float ym,

@@ -37,6 +37,8 @@ constexpr int kTileY = 8;
 // all formed on the host in FP64.
 struct Coef {
   double wx, wy, wz, wc;
+  int f64_emu;  // FP64 fields: 1 = emulated FP64 cell, 0 = FP64 cell
+  int pad;
 };
 
 Coef make_coef(double lam, double dt, double dx, double dy, double dz);

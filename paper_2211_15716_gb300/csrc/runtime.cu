@@ -51,6 +51,8 @@ Coef make_coef(double lam, double dt, double dx, double dy, double dz) {
   c.wy = k / (dy * dy);
   c.wz = k / (dz * dz);
   c.wc = -2.0 * (c.wx + c.wy + c.wz);
+  c.f64_emu = 0;
+  c.pad = 0;
   return c;
 }
 
@@ -327,6 +329,7 @@ struct igg_grid {
   std::map<GraphKey, cudaGraphExec_t> graphs;
   unsigned *dev_err = nullptr;  // device error word of the pipelined kernels
   bool tma_enabled = true;      // TMA kernel for the regular boxes when available
+  int f64_emu = 1;              // FP64 fields: emulated FP64 cell (1) or FP64 cell (0)
 };
 
 namespace {
@@ -546,8 +549,10 @@ bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->nco
 // of T2 on s) or hidden (boundary set + halo on the high-priority stream,
 // inner block on the low-priority stream, s joins both).
 int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const void *Ci,
-                 igg_dtype dt, const Coef &c, bool with_halo, cudaStream_t s) {
+                 igg_dtype dt, const Coef &c0, bool with_halo, cudaStream_t s) {
   cudaError_t e;
+  Coef c = c0;
+  c.f64_emu = g->f64_emu;
   const int V = grid_vec(g, dt);
   if (!widths) {
     TileSet *full = nullptr;
@@ -1047,12 +1052,14 @@ int igg_device_status(igg_grid *g, unsigned *status, int clear) {
 int igg_grid_set_option(igg_grid *g, int option, int value) {
   clear_error();
   if (int rc = check_grid(g)) return rc;
-  if (option != IGG_OPT_TMA) return set_error(IGG_EINVAL, "unknown option %d", option);
+  if (option != IGG_OPT_TMA && option != IGG_OPT_F64_EMU)
+    return set_error(IGG_EINVAL, "unknown option %d", option);
   DeviceGuard dg(g->device);
   cudaError_t e1 = cudaStreamSynchronize(g->hi), e2 = cudaStreamSynchronize(g->lo);
   if (e1 != cudaSuccess) return cuda_error(e1, "set_option");
   if (e2 != cudaSuccess) return cuda_error(e2, "set_option");
-  g->tma_enabled = value != 0;
+  if (option == IGG_OPT_TMA) g->tma_enabled = value != 0;
+  else g->f64_emu = value != 0 ? 1 : 0;
   // tile tables and graphs depend on the kernel choice
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();

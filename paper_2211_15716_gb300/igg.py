@@ -182,6 +182,7 @@ class Grid:
         return [t.numpy() for t in out]
 
     OPT_TMA = 1
+    OPT_F64_EMU = 2
 
     def set_option(self, option: int, value: int):
         """igg_grid_set_option (OPT_TMA: 1 = TMA kernel for regular boxes)."""

@@ -106,7 +106,7 @@ def test_halo_several_fields_one_call():
         assert np.array_equal(ta.cpu().numpy(), ra) and np.array_equal(tb.cpu().numpy(), rb)
 
 
-def _run_both(n, dims, periods, overlap, nt, widths, seed=0, tkind="gaussian_rough"):
+def _run_both(n, dims, periods, overlap, nt, widths, seed=0, tkind="gaussian_rough", f64_emu=1):
     T0o, Cio, dd, ng = oracle_fields(n, dims, periods, overlap, seed, tkind)
     dt_o = oracle.cfl_dt(*dd, 1.0, Cio.max())
     ref = oracle.run_decomposed(T0o, Cio, nt, 1.0, dt_o, *dd, dims, periods, overlap)
@@ -118,6 +118,7 @@ def _run_both(n, dims, periods, overlap, nt, widths, seed=0, tkind="gaussian_rou
         w = wl.Workload("t", n, dims, periods, overlap)
         dx, dy, dz, dt = wl.setup(w, g, Cd)
         assert (dx, dy, dz, dt) == (*dd, dt_o)
+        g.set_option(g.OPT_F64_EMU, f64_emu)
         res = g.run(nt, T, T2, Cd, 1.0, dt, dx, dy, dz, widths=widths)
         torch.cuda.synchronize()
         return res.cpu().numpy(), ref
@@ -125,9 +126,10 @@ def _run_both(n, dims, periods, overlap, nt, widths, seed=0, tkind="gaussian_rou
 
 @pytest.mark.parametrize("n,dims,periods,overlap", CASES)
 @pytest.mark.parametrize("hidden", [False, True])
-def test_fp64_run_matches_oracle(n, dims, periods, overlap, hidden):
+@pytest.mark.parametrize("emu", [1, 0])
+def test_fp64_run_matches_oracle(n, dims, periods, overlap, hidden, emu):
     widths = tuple(max(2, o) for o in overlap) if hidden else None
-    gpu, ref = _run_both(n, dims, periods, overlap, nt=7, widths=widths)
+    gpu, ref = _run_both(n, dims, periods, overlap, nt=7, widths=widths, f64_emu=emu)
     assert rel_err(gpu, ref) <= FP64_TOL
     # halo points are copies of computed points: compare them too (all points)
     assert np.isfinite(gpu).all()
@@ -307,3 +309,48 @@ def test_tma_full_size_decomposed_matches_oracle():
     ref = oracle.run_decomposed(T0, Cih, 2, w.lam, dt, dx, dy, dz, w.dims, w.periods, w.overlap,
                                 widths=w.widths)
     assert rel_err(gpu, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("emu", [1, 0])
+def test_fp64_stationarity_bit_exact(emu):
+    """A constant field is a fixed point bit for bit, in both FP64 cells."""
+    n = (64, 20, 18)
+    with igg.Grid(n) as g:
+        g.set_option(g.OPT_F64_EMU, emu)
+        T = torch.full(g.shape, 1.7, dtype=torch.float64, device="cuda")
+        Ci = dev(grid_fields(g, 3)[1])
+        T2 = g.run(5, T, T.clone(), Ci, 1.0, 1e-5, 0.01, 0.01, 0.01)
+        assert torch.equal(T2, torch.full_like(T2, 1.7))
+
+
+@pytest.mark.parametrize("kind", ["sign_changes", "wide_exponents", "binade_crossing"])
+def test_fp64_emulation_hard_fields(kind):
+    """Fields that send many points to the FP64 fallback of the emulated cell
+    (values of both signs, near zero, exponents spanning 10^-30..10^30, values
+    straddling powers of two) still match the oracle within 1e-12, and the
+    emulated and FP64 cells agree to a few FP64 roundings."""
+    n = (64, 24, 20)
+    g1 = [np.arange(k) for k in n]
+    rng = np.random.default_rng(12)
+    base = np.ascontiguousarray(synth.gaussian_bump(*g1, n, sigma=0.2) * np.ones((n[2], n[1], n[0])))
+    if kind == "sign_changes":
+        T0 = base - 2.2 + 1e-3 * rng.standard_normal(base.shape)
+    elif kind == "wide_exponents":
+        T0 = np.exp(rng.uniform(-69, 69, base.shape)) * (1 + 0.01 * base)
+    else:
+        T0 = 2.0 + 0.05 * rng.standard_normal(base.shape)
+    Ci = np.ascontiguousarray(synth.ci_uniform_c0(1, *g1, n))
+    dd = [oracle.spacing(1.0, k) for k in n]
+    dt = oracle.cfl_dt(*dd, 1.0, Ci.max())
+    nt = 6
+    ref = oracle.run(np.ascontiguousarray(T0), Ci, nt, 1.0, dt, *dd)
+    outs = []
+    with igg.Grid(n) as g:
+        for emu in (1, 0):
+            g.set_option(g.OPT_F64_EMU, emu)
+            T = torch.from_numpy(T0).cuda().view(g.shape)
+            outs.append(g.run(nt, T.clone(), T.clone(), dev(Ci).view(g.shape), 1.0, dt, *dd).cpu().numpy()[0])
+    for o in outs:
+        assert np.abs(o - ref).max() <= 1e-12 * np.abs(ref).max()
+    scale = np.abs(ref)
+    assert (np.abs(outs[0] - outs[1]) <= 16 * np.finfo(float).eps * scale + 1e-300).all()
