@@ -119,8 +119,9 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 //   T2 = fma(Ci, S*u, fma(Ci, C*u, T))
 // in FP64 (S*u and C*u widened to FP64 exactly by bit manipulation).
 //
-// Points whose values differ in sign or exponent, or whose exponent leaves
-// the range of the FP32 scalings, take cell_f64. The choice depends only on
+// For negative values the same holds with u = -2^(e-52). Points whose
+// values differ in sign or exponent, or whose exponent leaves the range of the
+// FP32 scalings, take cell_f64. The choice depends only on
 // the point's inputs, so every kernel makes the same choice and produces the
 // same bits.
 // ---------------------------------------------------------------------------
@@ -187,7 +188,9 @@ __device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Spl
   const float S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
   const float C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
                             __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
-  const float u = __int_as_float((E - 948) << 23);  // 2^(e-52)
+  // +-2^(e-52): the mantissa differences of negative values carry the
+  // opposite sign of the value differences
+  const float u = __int_as_float(((E - 948) << 23) | (int)(e & 0x80000000u));
   return __fma_rn(ci, f2d_bits(__fmul_rn(S, u)), __fma_rn(ci, f2d_bits(__fmul_rn(C, u)), tc));
 }
 
