@@ -110,8 +110,10 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // [2^23, 2^24). The second difference in units u = 2^(e-52) is the integer
 //   D_d = (Mh[+d] + Mh[-d] - 2 Mh)*2^29 + (Ml[+d] + Ml[-d] - 2 Ml),
 // Ml the low 29 bits; the Mh part lies in (-2^24, 2^24) and the Ml part in
-// (-2^30, 2^30), so A = dMh*2^29, B1 = dMl rounded down to a multiple of 128
-// and B2 = dMl mod 128 are exact FP32 numbers with D_d = A + B1 + B2. An
+// (-2^30, 2^30). For |dMh| < 2^22 (the fast path), A = dMh*2^29,
+// B1 = dMl rounded down to a multiple of 256 and B2 = dMl mod 256 are exact
+// FP32 numbers, formed through the FP32 significand without conversion
+// instructions, with D_d = A + B1 + B2. An
 // error-free two-sum gives D_d = s_d + t_d to about 2^-48 relative; the
 // weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is formed with exact FMA
 // product splits and two-sums of the three leading products (S) plus the
@@ -120,8 +122,9 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // in FP64 (S*u and C*u widened to FP64 exactly by bit manipulation).
 //
 // For negative values the same holds with u = -2^(e-52). Points whose
-// values differ in sign or exponent, or whose exponent leaves the range of the
-// FP32 scalings, take cell_f64. The choice depends only on
+// values differ in sign or exponent, whose exponent leaves the range of the
+// FP32 scalings, or with |dMh| >= 2^22 in some dimension (second differences
+// of a quarter of the value) take cell_f64. The choice depends only on
 // the point's inputs, so every kernel makes the same choice and produces the
 // same bits.
 // ---------------------------------------------------------------------------
@@ -158,6 +161,12 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   return s;
 }
 
+// exact FP32 value of an integer |q| < 2^22 (through the significand of
+// 1.5*2^23; FP32 pipe only)
+__device__ __forceinline__ float i22_to_f(int q) {
+  return __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f);
+}
+
 // One point from pre-split values: sc the centre, sn[6] the neighbours in the
 // order x-, x+, y-, y+, z-, z+ with their doubles in tn[6] (read only by the
 // fallback).
@@ -167,16 +176,22 @@ __device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Spl
   const unsigned diff = (sn[0].eh ^ e) | (sn[1].eh ^ e) | (sn[2].eh ^ e) | (sn[3].eh ^ e) |
                         (sn[4].eh ^ e) | (sn[5].eh ^ e);
   const int E = (int)((e >> 20) & 0x7FFu);
-  if (diff != 0u || E < 949 || E > 1147)
+  int dmh[3], dml[3];
+  bool small = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dmh[d] = sn[2 * d].mh + sn[2 * d + 1].mh - 2 * sc.mh;
+    dml[d] = sn[2 * d].ml + sn[2 * d + 1].ml - 2 * sc.ml;
+    small = small && (unsigned)(dmh[d] + (1 << 22)) < (1u << 23);
+  }
+  if (diff != 0u || E < 949 || E > 1147 || !small)
     return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
   float P[3], X[3], R[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const int dmh = sn[2 * d].mh + sn[2 * d + 1].mh - 2 * sc.mh;
-    const int dml = sn[2 * d].ml + sn[2 * d + 1].ml - 2 * sc.ml;
-    const float A = __fmul_rn(__int2float_rn(dmh), 536870912.0f);  // dMh * 2^29, exact
-    const float B1 = __int2float_rn(dml & ~127);                    // exact
-    const float B2 = __int2float_rn(dml & 127);                     // exact
+    const float A = __fmul_rn(i22_to_f(dmh[d]), 536870912.0f);         // dMh * 2^29, exact
+    const float B1 = __fmul_rn(i22_to_f(dml[d] >> 8), 256.0f);          // exact
+    const float B2 = __fsub_rn(__int_as_float(0x4B000000 | (dml[d] & 255)), 8388608.0f);  // exact
     float err;
     const float sd = two_sum(A, B1, err);
     const float td = __fadd_rn(err, B2);

@@ -119,6 +119,56 @@ __device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);
 }
 
+// V points of one row: centre vector c, x neighbours from c and the points
+// beyond it (left, right), y and z neighbour vectors.
+template <class S>
+__device__ __forceinline__ void compute_vec(const Vec<S> &c, typename Num<S>::C left,
+                                            typename Num<S>::C right, const Vec<S> &ym,
+                                            const Vec<S> &yp, const Vec<S> &zm, const Vec<S> &zp,
+                                            const Vec<S> &ci, const W<typename Num<S>::C> &w,
+                                            Vec<S> &out) {
+  constexpr int V = Vec<S>::V;
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+    const auto xm = i == 0 ? left : c.v[i - 1];
+    const auto xp = i == V - 1 ? right : c.v[i + 1];
+    out.v[i] = cell(c.v[i], xm, xp, ym.v[i], yp.v[i], zm.v[i], zp.v[i], ci.v[i], w);
+  }
+}
+
+// FP64: with the emulated cell, split every value once and share the splits
+// between the two points of the vector (same results as cell()).
+template <>
+__device__ __forceinline__ void compute_vec<double>(const Vec<double> &c, double left,
+                                                    double right, const Vec<double> &ym,
+                                                    const Vec<double> &yp, const Vec<double> &zm,
+                                                    const Vec<double> &zp, const Vec<double> &ci,
+                                                    const W<double> &w, Vec<double> &out) {
+  if (!w.emu) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const double xm = i == 0 ? left : c.v[0];
+      const double xp = i == 1 ? right : c.v[1];
+      out.v[i] = cell_f64(c.v[i], xm, xp, ym.v[i], yp.v[i], zm.v[i], zp.v[i], ci.v[i], w);
+    }
+    return;
+  }
+  const Split c0 = split64(c.v[0]), c1 = split64(c.v[1]);
+  const Split sl = split64(left), sr = split64(right);
+  {
+    const Split sn[6] = {sl, c1, split64(ym.v[0]), split64(yp.v[0]), split64(zm.v[0]),
+                         split64(zp.v[0])};
+    const double tn[6] = {left, c.v[1], ym.v[0], yp.v[0], zm.v[0], zp.v[0]};
+    out.v[0] = cell_emu(c.v[0], c0, sn, tn, ci.v[0], w);
+  }
+  {
+    const Split sn[6] = {c0, sr, split64(ym.v[1]), split64(yp.v[1]), split64(zm.v[1]),
+                         split64(zp.v[1])};
+    const double tn[6] = {c.v[0], right, ym.v[1], yp.v[1], zm.v[1], zp.v[1]};
+    out.v[1] = cell_emu(c.v[1], c1, sn, tn, ci.v[1], w);
+  }
+}
+
 // SWAP = false: rows along y, march along z (box {BW, BH, 1}); SWAP = true:
 // rows along z, march along y (box {BW, 1, BH}), for boxes thin in y. The
 // cell arithmetic gets the y and z neighbour pairs in their own slots either
@@ -239,16 +289,10 @@ __global__ void __launch_bounds__(32 * 9)
         if (sl == LPR - 1) right = Num<S>::cv(row[V]);
         if (comp[j]) {
           Vec<S> out;
-#pragma unroll
-          for (int i = 0; i < V; ++i) {
-            const C xm = i == 0 ? left : c.v[i - 1];
-            const C xp = i == V - 1 ? right : c.v[i + 1];
-            // (up, dn) are the row pair, (zm, zp) the march pair
-            if (!SWAP)
-              out.v[i] = cell(c.v[i], xm, xp, up.v[i], dn.v[i], zm[j].v[i], zp.v[i], ci.v[i], w);
-            else
-              out.v[i] = cell(c.v[i], xm, xp, zm[j].v[i], zp.v[i], up.v[i], dn.v[i], ci.v[i], w);
-          }
+          // (up, dn) are the row pair, (zm, zp) the march pair
+          Vec<S> ym = SWAP ? zm[j] : up, yp = SWAP ? zp : dn;
+          Vec<S> zmm = SWAP ? up : zm[j], zpp = SWAP ? dn : zp;
+          compute_vec<S>(c, left, right, ym, yp, zmm, zpp, ci, w, out);
           S *dst = T2 + t.base + xs + srow * (t.r0 + r) + smarch * m;
           if (full_vec) {
             *reinterpret_cast<uint4 *>(dst) = pack(out);
