@@ -161,6 +161,15 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   return s;
 }
 
+// The FP64 cell as an out-of-line call: the fallback of the emulated cell
+// must stay a branch (inlined, the compiler would evaluate it for every point
+// and select, which costs the FP64 instructions the emulation saves).
+__device__ __noinline__ double cell_f64_call(double t, double xm, double xp, double ym,
+                                             double yp, double zm, double zp, double ci,
+                                             const W<double> &w) {
+  return cell_f64(t, xm, xp, ym, yp, zm, zp, ci, w);
+}
+
 // exact FP32 value of an integer |q| < 2^22 (through the significand of
 // 1.5*2^23; FP32 pipe only)
 __device__ __forceinline__ float i22_to_f(int q) {
@@ -185,7 +194,7 @@ __device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Spl
     small = small && (unsigned)(dmh[d] + (1 << 22)) < (1u << 23);
   }
   if (diff != 0u || E < 949 || E > 1147 || !small)
-    return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+    return cell_f64_call(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
   float P[3], X[3], R[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
