@@ -110,23 +110,21 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // [2^23, 2^24). The second difference in units u = 2^(e-52) is the integer
 //   D_d = (Mh[+d] + Mh[-d] - 2 Mh)*2^29 + (Ml[+d] + Ml[-d] - 2 Ml),
 // Ml the low 29 bits; the Mh part lies in (-2^24, 2^24) and the Ml part in
-// (-2^30, 2^30). For |dMh| < 2^22 (the fast path), A = dMh*2^29,
-// B1 = dMl rounded down to a multiple of 256 and B2 = dMl mod 256 are exact
-// FP32 numbers, formed through the FP32 significand without conversion
-// instructions, with D_d = A + B1 + B2. An
+// (-2^30, 2^30), so A = dMh*2^29, B1 = dMl rounded down to a multiple of 128
+// and B2 = dMl mod 128 are exact FP32 numbers with D_d = A + B1 + B2. An
 // error-free two-sum gives D_d = s_d + t_d to about 2^-48 relative; the
 // weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is formed with exact FMA
 // product splits and two-sums of the three leading products (S) plus the
 // small terms (C), to about 2^-44 of sum_d |w_d D_d|. Finally
 //   T2 = fma(Ci, S*u, fma(Ci, C*u, T))
-// in FP64 (S*u and C*u widened to FP64 exactly by bit manipulation).
+// in FP64 (S*u and C*u widened to FP64 exactly by bit manipulation). For
+// negative values the same holds with u = -2^(e-52).
 //
-// For negative values the same holds with u = -2^(e-52). Points whose
-// values differ in sign or exponent, whose exponent leaves the range of the
-// FP32 scalings, or with |dMh| >= 2^22 in some dimension (second differences
-// of a quarter of the value) take cell_f64. The choice depends only on
-// the point's inputs, so every kernel makes the same choice and produces the
-// same bits.
+// Stencils with mixed signs or exponents (about 1 % of the points of a smooth
+// field: the shells where it crosses a power of two) or exponents outside
+// the range of the FP32 scalings take cell_f64. The choice depends only on the
+// point's inputs, so every kernel makes the same choice and produces the same
+// bits.
 // ---------------------------------------------------------------------------
 struct Split {
   int mh;       // top 24 bits of the 53-bit mantissa (with the hidden 1)
@@ -143,13 +141,13 @@ __device__ __forceinline__ Split split64(double v) {
   return s;
 }
 
-// float -> double by bit manipulation (exact for normal floats; zero and
-// subnormal floats give a signed zero)
+// float -> double by bit manipulation, exact for normal floats. Only used on
+// products added to a T of magnitude >= 2^-74 (the exponent range of the fast
+// path); a zero or subnormal float gives a value below 2^-126 there, far
+// below half an ulp of T, which leaves T2 unchanged.
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned b = __float_as_uint(f);
-  const unsigned sign = b & 0x80000000u, mag = b & 0x7FFFFFFFu;
-  if ((mag & 0x7F800000u) == 0u) return __hiloint2double((int)sign, 0);
-  const unsigned hi = sign | ((mag >> 3) + (896u << 20));
+  const unsigned hi = (b & 0x80000000u) | (((b & 0x7FFFFFFFu) >> 3) + (896u << 20));
   return __hiloint2double((int)hi, (int)(b << 29));
 }
 
@@ -161,46 +159,18 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   return s;
 }
 
-// The FP64 cell as an out-of-line call: the fallback of the emulated cell
-// must stay a branch (inlined, the compiler would evaluate it for every point
-// and select, which costs the FP64 instructions the emulation saves).
-__device__ __noinline__ double cell_f64_call(double t, double xm, double xp, double ym,
-                                             double yp, double zm, double zp, double ci,
-                                             const W<double> &w) {
-  return cell_f64(t, xm, xp, ym, yp, zm, zp, ci, w);
-}
-
-// exact FP32 value of an integer |q| < 2^22 (through the significand of
-// 1.5*2^23; FP32 pipe only)
-__device__ __forceinline__ float i22_to_f(int q) {
-  return __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f);
-}
-
-// One point from pre-split values: sc the centre, sn[6] the neighbours in the
-// order x-, x+, y-, y+, z-, z+ with their doubles in tn[6] (read only by the
-// fallback).
-__device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Split *sn,
-                                           const double *tn, double ci, const W<double> &w) {
-  const unsigned e = sc.eh;
-  const unsigned diff = (sn[0].eh ^ e) | (sn[1].eh ^ e) | (sn[2].eh ^ e) | (sn[3].eh ^ e) |
-                        (sn[4].eh ^ e) | (sn[5].eh ^ e);
-  const int E = (int)((e >> 20) & 0x7FFu);
-  int dmh[3], dml[3];
-  bool small = true;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    dmh[d] = sn[2 * d].mh + sn[2 * d + 1].mh - 2 * sc.mh;
-    dml[d] = sn[2 * d].ml + sn[2 * d + 1].ml - 2 * sc.ml;
-    small = small && (unsigned)(dmh[d] + (1 << 22)) < (1u << 23);
-  }
-  if (diff != 0u || E < 949 || E > 1147 || !small)
-    return cell_f64_call(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+// Emulated update from the integer second differences dmh[d]*2^29 + dml[d]
+// (units u = +-2^(E-1075), E the biased exponent): |dmh| < 2^24 and
+// |dml| < 2^30, so dmh*2^29, dml rounded down to a multiple of 128 and
+// dml mod 128 convert to FP32 exactly.
+__device__ __forceinline__ double emu_core(double tc, const int *dmh, const int *dml, int E,
+                                           unsigned sign, double ci, const W<double> &w) {
   float P[3], X[3], R[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float A = __fmul_rn(i22_to_f(dmh[d]), 536870912.0f);         // dMh * 2^29, exact
-    const float B1 = __fmul_rn(i22_to_f(dml[d] >> 8), 256.0f);          // exact
-    const float B2 = __fsub_rn(__int_as_float(0x4B000000 | (dml[d] & 255)), 8388608.0f);  // exact
+    const float A = __fmul_rn(__int2float_rn(dmh[d]), 536870912.0f);  // dMh * 2^29
+    const float B1 = __int2float_rn(dml[d] & ~127);
+    const float B2 = __int2float_rn(dml[d] & 127);
     float err;
     const float sd = two_sum(A, B1, err);
     const float td = __fadd_rn(err, B2);
@@ -212,10 +182,31 @@ __device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Spl
   const float S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
   const float C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
                             __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
-  // +-2^(e-52): the mantissa differences of negative values carry the
-  // opposite sign of the value differences
-  const float u = __int_as_float(((E - 948) << 23) | (int)(e & 0x80000000u));
+  // the mantissa differences of negative values carry the opposite sign of
+  // the value differences
+  const float u = __int_as_float(((E - 948) << 23) | (int)sign);
   return __fma_rn(ci, f2d_bits(__fmul_rn(S, u)), __fma_rn(ci, f2d_bits(__fmul_rn(C, u)), tc));
+}
+
+// One point from pre-split values: sc the centre, sn[6] the neighbours in the
+// order x-, x+, y-, y+, z-, z+ with their doubles in tn[6] (read only by the
+// FP64 fallback). The fallback stays inline: as a call it costs the fast path
+// more (call-site register constraints) than the ~1 % of points that take it.
+__device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Split *sn,
+                                           const double *tn, double ci, const W<double> &w) {
+  const unsigned e = sc.eh;
+  const unsigned diff = (sn[0].eh ^ e) | (sn[1].eh ^ e) | (sn[2].eh ^ e) | (sn[3].eh ^ e) |
+                        (sn[4].eh ^ e) | (sn[5].eh ^ e);
+  const int E = (int)((e >> 20) & 0x7FFu);
+  if (diff != 0u || E < 949 || E > 1139)
+    return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+  int dmh[3], dml[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dmh[d] = sn[2 * d].mh + sn[2 * d + 1].mh - 2 * sc.mh;
+    dml[d] = sn[2 * d].ml + sn[2 * d + 1].ml - 2 * sc.ml;
+  }
+  return emu_core(tc, dmh, dml, E, e & 0x80000000u, ci, w);
 }
 
 // The FP64 update used by every kernel: the emulated cell or the FP64 cell.

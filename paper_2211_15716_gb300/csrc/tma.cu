@@ -27,6 +27,11 @@
 #include "cell.cuh"
 #include "igg_internal.h"
 
+// resident CTAs per SM the TMA kernels are compiled for (register budget)
+#ifndef IGG_TMA_MIN_BLOCKS
+#define IGG_TMA_MIN_BLOCKS 3
+#endif
+
 namespace igg {
 namespace {
 
@@ -174,7 +179,7 @@ __device__ __forceinline__ void compute_vec<double>(const Vec<double> &c, double
 // cell arithmetic gets the y and z neighbour pairs in their own slots either
 // way, so both orientations give the same bits.
 template <class S, int LPR_, int H_, bool SWAP>
-__global__ void __launch_bounds__(32 * 9)
+__global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
                   unsigned *__restrict__ dev_err) {
