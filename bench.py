@@ -97,15 +97,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel_file: str, key: str):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+KERNEL_SOURCES = ("tma.cu", "cell.cuh", "igg_internal.h")
+
+
+def kernel_source_sha256() -> str:
+    """Hash of the sources of the stencil kernel the roofline reports."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2211_15716_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_for(key: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)[key]
-        src = open(os.path.join(ROOT, "paper_2211_15716_gb300", "csrc", kernel_file), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        if kernel_source_sha256() != rec["source_sha256"]:
             return None
         return float(rec["dram_bytes_per_launch"])
     except Exception:
@@ -144,6 +154,15 @@ def oracle_baseline(budget_s: float = 12.0):
             "cell_updates_per_s": inner * reps / el}
 
 
+def grid_launches_per_hidden_step(grid, w) -> int:
+    """Kernel launches of one hidden step: the boundary launches (z slabs, y
+    slabs, x ends; empty ones are skipped), three halo dimensions (copies in a
+    dimension without neighbours are skipped) and the inner block."""
+    n, dims, periods = grid.n, grid.dims, grid.periods
+    halo = sum(1 for d in range(3) if dims[d] > 1 or periods[d])
+    return 3 + halo + 1
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -158,6 +177,191 @@ def run_reference(args, ws, rank):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# --forms: the reduced-precision, batched and adjoint forms, each against the
+# FP64 form on the same GPU, one JSON line each (not the headline line)
+# ---------------------------------------------------------------------------
+def _timed(fn, reps):
+    import torch as _t
+    fn()
+    _t.cuda.synchronize()
+    a, b = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    _t.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def form_precision(steps):
+    """1024^3 grid, T0 = 1.7 + 8 sine modes, Ci ~ U[0.4, 0.67]: ms/step and
+    T_eff per storage type; error against the FP64 oracle after 1000 steps at
+    128^3 with the same recipe."""
+    import oracle
+    import synth
+    import paper_2211_15716_gb300 as igg
+    from paper_2211_15716_gb300 import workloads as wl
+
+    out = {"form": "precision", "workload": "1024^3 single grid, sine modes, nt timed " + str(steps)}
+    n = 1024
+    w = wl.WORKLOADS["precision_1024"]
+    g = igg.Grid((n, n, n))
+    ng = g.global_size()
+    idx = np.arange(n)
+    res = {}
+    C64 = g.empty(torch.float64)
+    for z0 in range(0, n, 128):
+        gz = idx[z0:z0 + 128]
+        C64[0, z0:z0 + 128] = torch.from_numpy(np.ascontiguousarray(synth.ci_uniform(w.seed, idx, idx, gz, ng)))
+    dx, dy, dz, dt = wl.setup(w, g, C64)
+    T64 = g.empty(torch.float64)
+    for z0 in range(0, n, 128):
+        gz = idx[z0:z0 + 128]
+        T64[0, z0:z0 + 128] = torch.from_numpy(np.ascontiguousarray(synth.sine_modes(w.seed, idx, idx, gz, ng)))
+
+    def storage(x, tdt):  # FP64 -> FP32 -> BF16, each nearest-even (the inputs' definition)
+        return x if tdt == torch.float64 else (x.float() if tdt == torch.float32 else x.float().to(tdt))
+
+    for name, tdt in (("f64_emulated", torch.float64), ("f64_cell", torch.float64),
+                      ("f32", torch.float32), ("bf16", torch.bfloat16)):
+        T = storage(T64, tdt).clone()
+        Ci = storage(C64, tdt)
+        T2 = T.clone()
+        g.set_option(g.OPT_F64_EMU, 0 if name == "f64_cell" else 1)
+        ms = _timed(lambda: g.run(steps, T, T2, Ci, w.lam, dt, dx, dy, dz), 1) / steps
+        nb = 3 * n ** 3 * T.element_size()
+        res[name] = {"ms_per_step": round(ms, 4), "T_eff_GB_s": round(nb / (ms * 1e-3) / 1e9, 1),
+                     "cell_updates_per_s": (n - 2) ** 3 / (ms * 1e-3)}
+        del T, T2, Ci
+        torch.cuda.empty_cache()
+    g.set_option(g.OPT_F64_EMU, 1)
+    g.finalize()
+    del C64, T64
+    # accuracy at 128^3, nt = 1000, against the FP64 oracle
+    m, nt = 128, 1000
+    wa = wl.WORKLOADS["precision_128"]
+    ga = igg.Grid((m, m, m))
+    T0, Ci = wl.host_fields(wa, ga, 0)
+    T0, Ci = np.ascontiguousarray(T0), np.ascontiguousarray(Ci)
+    dd = [oracle.spacing(1.0, m)] * 3
+    dt_o = oracle.cfl_dt(*dd, 1.0, Ci.max())
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    ref = oracle.run(T0, Ci, nt, 1.0, dt_o, *dd)
+    scale = np.abs(ref).max()
+    errs = {}
+    for name, tdt, emu in (("f64_emulated", torch.float64, 1), ("f64_cell", torch.float64, 0),
+                           ("f32", torch.float32, 1), ("bf16", torch.bfloat16, 1)):
+        T, T2, Cd = wl.make_fields(wa, ga, tdt)
+        ga.set_option(ga.OPT_F64_EMU, emu)
+        r = ga.run(nt, T, T2, Cd, 1.0, dt_o, *dd).double().cpu().numpy()[0]
+        d = r - ref
+        errs[name] = {"max_abs_err_rel_to_max_T": float(np.abs(d).max() / scale),
+                      "rel_L2": float(np.linalg.norm(d) / np.linalg.norm(ref))}
+    errs["change_of_T_over_run_rel"] = float(np.abs(ref - T0).max() / scale)
+    ga.finalize()
+    out.update({"results": res, "error_vs_fp64_oracle_128cube_nt1000": errs})
+    return out
+
+
+def form_batched(steps):
+    """256 independent FP32 problems, dims uniform on {32..192}: one
+    persistent launch per step, CUDA-graph loop, autotuned tiling."""
+    import oracle
+    import synth
+    import paper_2211_15716_gb300 as igg
+    from paper_2211_15716_gb300 import workloads as wl
+
+    sizes, lam, ci, dd, dt = wl.batch_problems()
+    B = igg.Batch(sizes, torch.float32)
+    B.set_coefs(lam, dt, [d[0] for d in dd], [d[1] for d in dd], [d[2] for d in dd])
+    T, T2, Ci = wl.make_batch_fields(B, ci)
+    best = B.autotune(T2, T, Ci, reps=3)
+    T2.copy_(T)
+    ms = _timed(lambda: B.run(steps, T, T2, Ci), 1) / steps
+    cells = sum(a * b * c for a, b, c in sizes)
+    inner = sum((a - 2) * (b - 2) * (c - 2) for a, b, c in sizes)
+    # accuracy: 4 sampled problems after 200 steps against the oracle
+    T, T2, Ci = wl.make_batch_fields(B, ci)
+    nt = 200
+    res = B.run(nt, T, T2, Ci)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for b in (0, 63, 128, 255):
+        nx, ny, nz = sizes[b]
+        g = [np.arange(nx), np.arange(ny), np.arange(nz)]
+        T0 = np.ascontiguousarray(np.broadcast_to(synth.gaussian_bump(*g, (nx, ny, nz)), (nz, ny, nx)))
+        ref = oracle.run(T0, np.full(T0.shape, float(ci[b])), nt, float(lam[b]), dt[b], *dd[b])
+        gpu = B.view(res, b).double().cpu().numpy()
+        worst = max(worst, float(np.abs(gpu - ref).max() / np.abs(ref).max()))
+    B.destroy()
+    return {"form": "batched", "workload": "256 FP32 problems, dims U{32..192}, lam U[0.5,2]",
+            "ms_per_step": round(ms, 4), "T_eff_GB_s": round(3 * cells * 4 / (ms * 1e-3) / 1e9, 1),
+            "cell_updates_per_s": inner / (ms * 1e-3), "cells": cells, "autotuned": best,
+            "max_err_rel_vs_fp64_oracle_nt200_4problems": worst}
+
+
+def form_adjoint():
+    """256^3 FP64 and FP32, nt = 200, misfit gradient through the checkpointed
+    adjoint (checkpoint every 16): time against the plain forward run, and a
+    central finite difference of J along a random direction of Ci."""
+    import synth
+    import paper_2211_15716_gb300 as igg
+    from paper_2211_15716_gb300 import autograd as ag
+    from paper_2211_15716_gb300 import workloads as wl
+
+    n, nt, every = 256, 200, 16
+    g = igg.Grid((n, n, n))
+    gi = [np.arange(n)] * 3
+    out = {"form": "adjoint", "workload": "256^3, nt 200, checkpoint every 16"}
+    Ci_star = synth.ci_smooth(4, *gi, (n, n, n))
+    T0 = np.broadcast_to(synth.gaussian_bump(*gi, (n, n, n), sigma=0.15), (n, n, n))
+    dd = [wl.spacing(1.0, n)] * 3
+    dt = wl.cfl_dt(*dd, 1.0, max(Ci_star.max(), 0.53))
+    noise = 1e-3 * synth.normal(4, 20, np.arange(n ** 3, dtype=np.uint64)).reshape(n, n, n)
+    for name, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        cs = torch.from_numpy(np.ascontiguousarray(Ci_star)).to(tdt).cuda().view(g.shape)
+        t0 = torch.from_numpy(np.ascontiguousarray(T0)).to(tdt).cuda().view(g.shape)
+        obs = g.run(nt, t0.clone(), t0.clone(), cs, 1.0, dt, *dd)
+        obs = obs + torch.from_numpy(noise).to(tdt).cuda().view(g.shape)
+        C = torch.full(g.shape, 0.53, dtype=tdt, device="cuda")
+        t_fwd = _timed(lambda: g.run(nt, t0.clone(), t0.clone(), C, 1.0, dt, *dd), 2)
+
+        def grad():
+            T_nt, ck = ag.forward_checkpointed(g, nt, every, t0, C, 1.0, dt, *dd)
+            lam_nt = ag.residual(T_nt, obs)
+            return ag.adjoint_checkpointed(g, nt, every, ck, C, lam_nt, 1.0, dt, *dd)
+
+        t_grad = _timed(grad, 2)
+        gT, gC = grad()
+
+        def J(Cx):
+            T_nt = g.run(nt, t0.clone(), t0.clone(), Cx, 1.0, dt, *dd)
+            return 0.5 * igg.reduce(igg.RED_SUM_SQDIFF, T_nt, obs).item()
+
+        v = torch.from_numpy(synth.normal(4, 30, np.arange(n ** 3, dtype=np.uint64)).reshape(g.shape)).cuda()
+        h = 1e-4 if tdt == torch.float32 else 1e-7
+        fd = (J(C + (h * v).to(tdt)) - J(C - (h * v).to(tdt))) / (2 * h)
+        ad = float((gC * v).sum())
+        out[name] = {"forward_ms": round(t_fwd, 3), "gradient_ms": round(t_grad, 3),
+                     "gradient_over_forward": round(t_grad / t_fwd, 2),
+                     "fd_vs_adjoint_rel": abs(fd - ad) / abs(ad)}
+    g.finalize()
+    return out
+
+
+def run_forms(args):
+    import paper_2211_15716_gb300  # noqa: F401
+    from paper_2211_15716_gb300 import build as igg_build
+    igg_build.build()
+    for fn in (lambda: form_precision(max(20, args.steps // 5)), lambda: form_batched(max(20, args.steps)),
+               form_adjoint):
+        print(json.dumps(fn()), flush=True)
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -168,10 +372,14 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="decomposed_2x2x2_512x256x256 (default) or a smaller case for profiling")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--forms", action="store_true",
+                    help="measure the precision, batched and adjoint forms (extra JSON lines)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.forms:
+        return run_forms(args)
     if args.warmup < 3:
         args.warmup = 3
 
@@ -243,6 +451,30 @@ def main():
     clocks = sampler.stop()
     k_ms = k0.elapsed_time(k1) / kreps
 
+    # ---- variants (outside the timed region): plain step, FP64 cell -------
+    variants = {}
+    vsteps = max(10, args.steps // 4)
+
+    def time_run(widths):
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        grid.run(2, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=widths)
+        v0.record(stream)
+        grid.run(vsteps, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=widths)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        return v0.elapsed_time(v1) / vsteps
+
+    t_plain = time_run(None)
+    variants["plain_step_no_hiding"] = {"ms_per_step": round(t_plain, 4),
+                                        "GB_s": round(bytes_step / (t_plain * 1e-3) / 1e9, 1)}
+    if tdtype == torch.float64:
+        grid.set_option(grid.OPT_F64_EMU, 0)
+        t_nat = time_run(w.widths)
+        grid.set_option(grid.OPT_F64_EMU, 1)
+        variants["hidden_step_fp64_cell"] = {"ms_per_step": round(t_nat, 4),
+                                             "GB_s": round(bytes_step / (t_nat * 1e-3) / 1e9, 1)}
+    status = grid.device_status()
+
     # ---- end to end: host inputs -> K steps -> host result ----------------
     Th = torch.empty(T.shape, dtype=T.dtype, pin_memory=True)
     Ch = torch.empty(Ci.shape, dtype=Ci.dtype, pin_memory=True)
@@ -269,9 +501,11 @@ def main():
     assert torch.isfinite(Rh[0, 5, 5, :8].float()).all()
 
     hbm, hbm_kind = peaks()
+    # our kernels per hidden step: boundary launches + 3 halo dims + inner block
+    launches_per_step = grid_launches_per_hidden_step(grid, w)
     value = ws * bytes_step / (ms_step * 1e-3) / 1e9
     achieved = bytes_step / (k_ms * 1e-3) / 1e9
-    traffic = traffic_for("stencil.cu", f"stencil {args.dtype} full step {args.workload}")
+    traffic = traffic_for(f"full step {args.dtype} {args.workload}")
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -287,15 +521,21 @@ def main():
         "frac_of_8TBs": round(value / ws / 8000.0, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": traffic,
-                     "kernel": f"stencil kernel, {args.dtype} (full step, all subdomains)",
+                     "kernel": f"k_stencil_tma<{args.dtype}> (TMA-pipelined, full step, all subdomains)",
                      "peak_kind": hbm_kind, "kernel_ms": round(k_ms, 4)},
         "e2e": {"value": round(ws * bytes_step * args.steps / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": int(3 * N * s / args.steps),
                 "d2h_bytes_per_step": int(N * s / args.steps),
                 "note": "one job: H2D of T, T2 (= copy(T)) and Ci from pinned memory, K steps, D2H of T"},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
+        "variants": variants,
+        "device_status": status,
     }
+    if tdtype == torch.float64:
+        line["f64_cell"] = ("emulated: exact integer second differences, float-float weights, "
+                            "2 FP64 FMAs per point; FP64 cell for stencils that cross a sign or "
+                            "a power of two")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         line["cpu_baseline"] = oracle_baseline()
     if rank == 0:
