@@ -188,25 +188,36 @@ __device__ __forceinline__ double emu_core(double tc, const int *dmh, const int 
   return __fma_rn(ci, f2d_bits(__fmul_rn(S, u)), __fma_rn(ci, f2d_bits(__fmul_rn(C, u)), tc));
 }
 
-// One point from pre-split values: sc the centre, sn[6] the neighbours in the
-// order x-, x+, y-, y+, z-, z+ with their doubles in tn[6] (read only by the
-// FP64 fallback). The fallback stays inline: as a call it costs the fast path
-// more (call-site register constraints) than the ~1 % of points that take it.
-__device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Split *sn,
-                                           const double *tn, double ci, const W<double> &w) {
+// The emulated cell's fast path alone: false (and no value) for the points
+// that cell_emu hands to the FP64 cell. Used by kernels that defer those
+// points to a separate pass.
+__device__ __forceinline__ bool emu_fast_ok(const Split &sc, const Split *sn) {
   const unsigned e = sc.eh;
   const unsigned diff = (sn[0].eh ^ e) | (sn[1].eh ^ e) | (sn[2].eh ^ e) | (sn[3].eh ^ e) |
                         (sn[4].eh ^ e) | (sn[5].eh ^ e);
   const int E = (int)((e >> 20) & 0x7FFu);
-  if (diff != 0u || E < 949 || E > 1139)
-    return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+  return diff == 0u && E >= 949 && E <= 1139;
+}
+
+__device__ __forceinline__ double cell_emu_fast(double tc, const Split &sc, const Split *sn,
+                                                double ci, const W<double> &w) {
   int dmh[3], dml[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     dmh[d] = sn[2 * d].mh + sn[2 * d + 1].mh - 2 * sc.mh;
     dml[d] = sn[2 * d].ml + sn[2 * d + 1].ml - 2 * sc.ml;
   }
-  return emu_core(tc, dmh, dml, E, e & 0x80000000u, ci, w);
+  return emu_core(tc, dmh, dml, (int)((sc.eh >> 20) & 0x7FFu), sc.eh & 0x80000000u, ci, w);
+}
+
+// One point from pre-split values: sc the centre, sn[6] the neighbours in the
+// order x-, x+, y-, y+, z-, z+ with their doubles in tn[6] (read only by the
+// FP64 fallback). The fallback stays inline: as a call it costs the fast path
+// more (call-site register constraints) than the ~1 % of points that take it.
+__device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Split *sn,
+                                           const double *tn, double ci, const W<double> &w) {
+  if (!emu_fast_ok(sc, sn)) return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+  return cell_emu_fast(tc, sc, sn, ci, w);
 }
 
 // The FP64 update used by every kernel: the emulated cell or the FP64 cell.

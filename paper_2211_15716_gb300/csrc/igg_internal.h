@@ -120,9 +120,12 @@ bool tma_available();
 // Sets the kernel's shared-memory attribute and returns its resident CTAs per
 // SM; call before launching (and before any stream capture).
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
+// FP64 fields with the emulated cell need `fix` (one byte per tile, written by
+// the launch) and run a fix-up launch after the kernel on the same stream.
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
-                               long long nzt, const Coef &c, unsigned *dev_err, cudaStream_t s);
+                               long long nzt, const Coef &c, unsigned *dev_err,
+                               unsigned char *fix, cudaStream_t s);
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.

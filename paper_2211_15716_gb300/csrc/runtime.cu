@@ -81,6 +81,7 @@ struct TileSet {
   int n = 0;
   int V = 1;
   int tma = -1;
+  unsigned char *fix = nullptr;  // per-tile fix-up flags (FP64 TMA tile sets)
 };
 
 // The split: boundary set (one launch per tile kind) and inner block.
@@ -305,8 +306,24 @@ int upload_vec(const std::vector<TT> &v, TileSet *out) {
 int upload_tiles(const TileLists &v, int V, TileSet *out, int tma = -1) {
   out->V = V;
   out->tma = tma;
-  if (tma >= 0) return upload_vec(v.tma, out);
+  out->fix = nullptr;
+  if (tma >= 0) {
+    if (int rc = upload_vec(v.tma, out)) return rc;
+    if (V == 2 && out->n > 0) {  // FP64: flags of the emulated cell's fix-up
+      cudaError_t e = cudaMalloc(&out->fix, (size_t)out->n);
+      if (e == cudaSuccess) e = cudaMemset(out->fix, 0, (size_t)out->n);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fix-up flags)");
+    }
+    return IGG_OK;
+  }
   return V > 1 ? upload_vec(v.vec, out) : upload_vec(v.scalar, out);
+}
+
+void free_tiles(TileSet &t) {
+  cudaFree(t.dev);
+  cudaFree(t.fix);
+  t.dev = nullptr;
+  t.fix = nullptr;
 }
 
 }  // namespace
@@ -490,8 +507,8 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
     }
   }
   if (rc != IGG_OK) {
-    for (auto &b : st.boundary) cudaFree(b.dev);
-    cudaFree(st.inner.dev);
+    for (auto &b : st.boundary) free_tiles(b);
+    free_tiles(st.inner);
     return rc;
   }
   auto res = g->split.emplace(key, st);
@@ -503,7 +520,7 @@ cudaError_t launch_tiles(const igg_grid *g, int V, igg_dtype dt, const TileSet &
                          const void *T, const void *Ci, const Coef &c, cudaStream_t s) {
   if (ts.tma >= 0)
     return launch_stencil_tma(dt, ts.tma, (const TmaTile *)ts.dev, ts.n, T2, T, Ci, g->n[0],
-                              g->n[1], (long long)g->nsub * g->n[2], c, g->dev_err, s);
+                              g->n[1], (long long)g->nsub * g->n[2], c, g->dev_err, ts.fix, s);
   if (V > 1) return launch_stencil_vec(dt, (const VTile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
   return launch_stencil(dt, (const Tile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
@@ -599,10 +616,10 @@ void destroy_grid(igg_grid *g) {
   if (!g) return;
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &kv : g->split) {
-    for (auto &b : kv.second.boundary) cudaFree(b.dev);
-    cudaFree(kv.second.inner.dev);
+    for (auto &b : kv.second.boundary) free_tiles(b);
+    free_tiles(kv.second.inner);
   }
-  for (auto &kv : g->full) cudaFree(kv.second.dev);
+  for (auto &kv : g->full) free_tiles(kv.second);
   for (int d = 0; d < 3; ++d) cudaFree(g->copies[d]);
   cudaFree(g->dev_err);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
@@ -1064,11 +1081,11 @@ int igg_grid_set_option(igg_grid *g, int option, int value) {
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();
   for (auto &kv : g->split) {
-    for (auto &b : kv.second.boundary) cudaFree(b.dev);
-    cudaFree(kv.second.inner.dev);
+    for (auto &b : kv.second.boundary) free_tiles(b);
+    free_tiles(kv.second.inner);
   }
   g->split.clear();
-  for (auto &kv : g->full) cudaFree(kv.second.dev);
+  for (auto &kv : g->full) free_tiles(kv.second);
   g->full.clear();
   return IGG_OK;
 }

@@ -124,15 +124,23 @@ __device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);
 }
 
+// How a TMA kernel computes its points: MODE_CELL = the shared cell() of the
+// storage type (FP32, BF16); for FP64 fields, MODE_F64 = the FP64 cell and
+// MODE_EMU = the emulated cell's fast path, leaving the points it hands to the
+// FP64 cell unwritten and flagging their tile for k_fixup_f64.
+enum { MODE_CELL = 0, MODE_F64 = 1, MODE_EMU = 2 };
+
 // V points of one row: centre vector c, x neighbours from c and the points
-// beyond it (left, right), y and z neighbour vectors.
-template <class S>
+// beyond it (left, right), y and z neighbour vectors. ok gets bit i for each
+// point written to out.
+template <class S, int MODE>
 __device__ __forceinline__ void compute_vec(const Vec<S> &c, typename Num<S>::C left,
                                             typename Num<S>::C right, const Vec<S> &ym,
                                             const Vec<S> &yp, const Vec<S> &zm, const Vec<S> &zp,
                                             const Vec<S> &ci, const W<typename Num<S>::C> &w,
-                                            Vec<S> &out) {
+                                            Vec<S> &out, unsigned &ok) {
   constexpr int V = Vec<S>::V;
+  ok = (1u << V) - 1u;
 #pragma unroll
   for (int i = 0; i < V; ++i) {
     const auto xm = i == 0 ? left : c.v[i - 1];
@@ -141,48 +149,47 @@ __device__ __forceinline__ void compute_vec(const Vec<S> &c, typename Num<S>::C 
   }
 }
 
-// FP64: with the emulated cell, split every value once and share the splits
-// between the two points of the vector (same results as cell()).
 template <>
-__device__ __forceinline__ void compute_vec<double>(const Vec<double> &c, double left,
-                                                    double right, const Vec<double> &ym,
-                                                    const Vec<double> &yp, const Vec<double> &zm,
-                                                    const Vec<double> &zp, const Vec<double> &ci,
-                                                    const W<double> &w, Vec<double> &out) {
-  if (!w.emu) {
+__device__ __forceinline__ void compute_vec<double, MODE_F64>(
+    const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
+    const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
+    Vec<double> &out, unsigned &ok) {
+  ok = 3u;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const double xm = i == 0 ? left : c.v[0];
-      const double xp = i == 1 ? right : c.v[1];
-      out.v[i] = cell_f64(c.v[i], xm, xp, ym.v[i], yp.v[i], zm.v[i], zp.v[i], ci.v[i], w);
-    }
-    return;
+  for (int i = 0; i < 2; ++i) {
+    const double xm = i == 0 ? left : c.v[0];
+    const double xp = i == 1 ? right : c.v[1];
+    out.v[i] = cell_f64(c.v[i], xm, xp, ym.v[i], yp.v[i], zm.v[i], zp.v[i], ci.v[i], w);
   }
+}
+
+// Emulated fast path: every value split once, splits shared between the two
+// points of the vector; points outside the fast path are left to the fix-up.
+template <>
+__device__ __forceinline__ void compute_vec<double, MODE_EMU>(
+    const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
+    const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
+    Vec<double> &out, unsigned &ok) {
   const Split c0 = split64(c.v[0]), c1 = split64(c.v[1]);
-  const Split sl = split64(left), sr = split64(right);
-  {
-    const Split sn[6] = {sl, c1, split64(ym.v[0]), split64(yp.v[0]), split64(zm.v[0]),
-                         split64(zp.v[0])};
-    const double tn[6] = {left, c.v[1], ym.v[0], yp.v[0], zm.v[0], zp.v[0]};
-    out.v[0] = cell_emu(c.v[0], c0, sn, tn, ci.v[0], w);
-  }
-  {
-    const Split sn[6] = {c0, sr, split64(ym.v[1]), split64(yp.v[1]), split64(zm.v[1]),
-                         split64(zp.v[1])};
-    const double tn[6] = {c.v[0], right, ym.v[1], yp.v[1], zm.v[1], zp.v[1]};
-    out.v[1] = cell_emu(c.v[1], c1, sn, tn, ci.v[1], w);
-  }
+  const Split sn0[6] = {split64(left), c1, split64(ym.v[0]), split64(yp.v[0]), split64(zm.v[0]),
+                        split64(zp.v[0])};
+  const Split sn1[6] = {c0, split64(right), split64(ym.v[1]), split64(yp.v[1]), split64(zm.v[1]),
+                        split64(zp.v[1])};
+  const bool ok0 = emu_fast_ok(c0, sn0), ok1 = emu_fast_ok(c1, sn1);
+  ok = (ok0 ? 1u : 0u) | (ok1 ? 2u : 0u);
+  out.v[0] = ok0 ? cell_emu_fast(c.v[0], c0, sn0, ci.v[0], w) : 0.0;
+  out.v[1] = ok1 ? cell_emu_fast(c.v[1], c1, sn1, ci.v[1], w) : 0.0;
 }
 
 // SWAP = false: rows along y, march along z (box {BW, BH, 1}); SWAP = true:
 // rows along z, march along y (box {BW, 1, BH}), for boxes thin in y. The
 // cell arithmetic gets the y and z neighbour pairs in their own slots either
 // way, so both orientations give the same bits.
-template <class S, int LPR_, int H_, bool SWAP>
+template <class S, int LPR_, int H_, bool SWAP, int MODE>
 __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
-                  unsigned *__restrict__ dev_err) {
+                  unsigned *__restrict__ dev_err, unsigned char *__restrict__ fix) {
   using Sh = TmaShape<S, LPR_, H_>;
   using C = typename Num<S>::C;
   constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
@@ -191,7 +198,8 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
   const unsigned full0 = sbase + NS * Sh::STAGE;
   const unsigned empty0 = full0 + NS * 8;
   volatile int *flags = reinterpret_cast<volatile int *>(smem + NS * Sh::STAGE + 2 * NS * 8);
-  // flags[0]: abort; flags[1]: loads issued; flags[2]: loads consumed
+  // flags[0]: abort; flags[1]: loads issued; flags[2]: loads consumed;
+  // flags[3]: some point of the tile left to the fix-up (MODE_EMU)
 
   const TmaTile t = tiles[blockIdx.x];
   const int K = (t.m1 - t.m0) + 2;
@@ -205,6 +213,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     flags[0] = 0;
     flags[1] = 0;
     flags[2] = 0;
+    flags[3] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -252,6 +261,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     const long long sy = nx, sz = (long long)nx * ny;
     const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
     Vec<S> zm[Sh::RPT];
+    bool deferred = false;
     bool ok = mbar_wait(full0, 0);
     if (!ok) {
       atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
@@ -297,14 +307,18 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
           // (up, dn) are the row pair, (zm, zp) the march pair
           Vec<S> ym = SWAP ? zm[j] : up, yp = SWAP ? zp : dn;
           Vec<S> zmm = SWAP ? up : zm[j], zpp = SWAP ? dn : zp;
-          compute_vec<S>(c, left, right, ym, yp, zmm, zpp, ci, w, out);
+          unsigned okm;
+          compute_vec<S, MODE>(c, left, right, ym, yp, zmm, zpp, ci, w, out, okm);
           S *dst = T2 + t.base + xs + srow * (t.r0 + r) + smarch * m;
-          if (full_vec) {
+          if (full_vec && okm == (1u << V) - 1u) {
             *reinterpret_cast<uint4 *>(dst) = pack(out);
           } else {
 #pragma unroll
-            for (int i = 0; i < V; ++i)
-              if (xs + i >= t.xb && xs + i < t.xe) Num<S>::st(dst + i, out.v[i]);
+            for (int i = 0; i < V; ++i) {
+              const bool in = xs + i >= t.xb && xs + i < t.xe;
+              if (in && (okm >> i & 1u)) Num<S>::st(dst + i, out.v[i]);
+              deferred = deferred || (in && !(okm >> i & 1u));
+            }
           }
         }
         zm[j] = c;
@@ -313,8 +327,10 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       if (lane == 0) mbar_arrive(empty0 + 8 * s);
     }
     if (warp == 0 && lane == 0) flags[2] = consumed;
+    if (MODE == MODE_EMU && __any_sync(0xffffffffu, deferred) && lane == 0) flags[3] = 1;
   }
   __syncthreads();
+  if (MODE == MODE_EMU && threadIdx.x == 0) fix[blockIdx.x] = flags[3] ? 1 : 0;
   // After an abort, wait (bounded) for copies issued but never consumed, so
   // that no bulk copy writes into this CTA's shared memory after it exits.
   if (threadIdx.x == 0 && flags[0]) {
@@ -324,6 +340,37 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
         break;
       }
     }
+  }
+}
+
+// Fix-up of a MODE_EMU launch: in every flagged tile, the points outside the
+// emulated cell's fast path get the FP64 cell (the same choice and the same
+// arithmetic as cell() everywhere else). One CTA per tile of the launch.
+template <bool SWAP>
+__global__ void __launch_bounds__(256)
+    k_fixup_f64(const TmaTile *__restrict__ tiles, const unsigned char *__restrict__ fix,
+                double *__restrict__ T2, const double *__restrict__ T,
+                const double *__restrict__ Ci, int nx, int ny, Coef c0) {
+  if (!fix[blockIdx.x]) return;
+  const TmaTile t = tiles[blockIdx.x];
+  const W<double> w = make_w(c0, 0.0);
+  const long long sy = nx, sz = (long long)nx * ny;
+  const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
+  const int nxr = t.xe - t.xb, nr = t.re - t.r0;
+  const long long npts = (long long)nxr * nr * (t.m1 - t.m0);
+  for (long long i = threadIdx.x; i < npts; i += blockDim.x) {
+    const int x = t.xb + (int)(i % nxr);
+    const int r = t.r0 + (int)((i / nxr) % nr);
+    const int m = t.m0 + (int)(i / ((long long)nxr * nr));
+    const long long p = t.base + x + srow * r + smarch * m;
+    const double tc = __ldg(T + p);
+    const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
+                          __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
+    Split sn[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sn[k] = split64(tn[k]);
+    if (!emu_fast_ok(split64(tc), sn))
+      T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
   }
 }
 
@@ -360,21 +407,21 @@ bool encode(CUtensorMap *m, const void *base, int nx, int ny, long long nzt, int
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <class S, class Shp, bool SWAP>
+template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t prepare_t(int *ctas_per_sm) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
-  cudaError_t e = cudaFuncSetAttribute(k_stencil_tma<S, Shp::LPR, Shp::H, SWAP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  auto kern = k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   if (e == cudaSuccess && ctas_per_sm)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        ctas_per_sm, k_stencil_tma<S, Shp::LPR, Shp::H, SWAP>, 32 * (Sh::CONSUMERS + 1), Sh::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, 32 * (Sh::CONSUMERS + 1),
+                                                      Sh::SMEM);
   return e;
 }
 
-template <class S, class Shp, bool SWAP>
+template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     cudaStream_t s) {
+                     unsigned char *fix, cudaStream_t s) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
   CUtensorMap mT, mC;
   const bool ok = SWAP ? encode<S>(&mT, T, nx, ny, nzt, Sh::BW, 1, Sh::BH) &&
@@ -382,29 +429,62 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
                        : encode<S>(&mT, T, nx, ny, nzt, Sh::BW, Sh::BH, 1) &&
                              encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, Sh::H, 1);
   if (!ok) return cudaErrorInvalidValue;
-  k_stencil_tma<S, Shp::LPR, Shp::H, SWAP><<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(
-      mT, mC, tiles, (S *)T2, nx, ny, c, dev_err);
-  return cudaGetLastError();
+  k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>
+      <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
+                                                          dev_err, fix);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && MODE == MODE_EMU) {
+    k_fixup_f64<SWAP><<<ntiles, 256, 0, s>>>(tiles, fix, (double *)T2, (const double *)T,
+                                             (const double *)Ci, nx, ny, c);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
+// FP64 fields pick the kernel of the grid's FP64 mode; other types the cell.
 template <class S>
 cudaError_t prepare_v(int variant, int *ctas) {
-  switch (variant) {
-    case TMA_WIDE: return prepare_t<S, WideShape<S>, false>(ctas);
-    case TMA_WIDE_SWAP: return prepare_t<S, WideShape<S>, true>(ctas);
+  if (variant != TMA_WIDE && variant != TMA_WIDE_SWAP) return cudaErrorInvalidValue;
+  const bool swap = variant == TMA_WIDE_SWAP;
+  if constexpr (sizeof(S) == 8) {
+    cudaError_t e = swap ? prepare_t<S, WideShape<S>, true, MODE_F64>(nullptr)
+                         : prepare_t<S, WideShape<S>, false, MODE_F64>(nullptr);
+    if (e != cudaSuccess) return e;
+    return swap ? prepare_t<S, WideShape<S>, true, MODE_EMU>(ctas)
+                : prepare_t<S, WideShape<S>, false, MODE_EMU>(ctas);
+  } else {
+    return swap ? prepare_t<S, WideShape<S>, true, MODE_CELL>(ctas)
+                : prepare_t<S, WideShape<S>, false, MODE_CELL>(ctas);
   }
-  return cudaErrorInvalidValue;
+}
+
+template <class S, bool SWAP>
+cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
+                     int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
+                     unsigned char *fix, cudaStream_t s) {
+  if constexpr (sizeof(S) == 8) {
+    if (c.f64_emu) {
+      if (!fix) return cudaErrorInvalidValue;
+      return launch_t<S, WideShape<S>, SWAP, MODE_EMU>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
+                                                       dev_err, fix, s);
+    }
+    return launch_t<S, WideShape<S>, SWAP, MODE_F64>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
+                                                     dev_err, fix, s);
+  } else {
+    return launch_t<S, WideShape<S>, SWAP, MODE_CELL>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
+                                                      dev_err, fix, s);
+  }
 }
 
 template <class S>
 cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, const void *T,
                      const void *Ci, int nx, int ny, long long nzt, const Coef &c,
-                     unsigned *dev_err, cudaStream_t s) {
+                     unsigned *dev_err, unsigned char *fix, cudaStream_t s) {
   switch (variant) {
     case TMA_WIDE:
-      return launch_t<S, WideShape<S>, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+      return launch_m<S, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
     case TMA_WIDE_SWAP:
-      return launch_t<S, WideShape<S>, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+      return launch_m<S, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -442,15 +522,17 @@ cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
 
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
-                               long long nzt, const Coef &c, unsigned *dev_err, cudaStream_t s) {
+                               long long nzt, const Coef &c, unsigned *dev_err,
+                               unsigned char *fix, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   switch (dt) {
     case IGG_F64:
-      return launch_v<double>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+      return launch_v<double>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
     case IGG_F32:
-      return launch_v<float>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+      return launch_v<float>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
     case IGG_BF16:
-      return launch_v<__nv_bfloat16>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, s);
+      return launch_v<__nv_bfloat16>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err,
+                                     fix, s);
   }
   return cudaErrorInvalidValue;
 }
