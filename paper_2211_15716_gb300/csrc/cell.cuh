@@ -105,49 +105,41 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // spends two FP64 FMAs per point and does the rest on the FP32, integer and
 // conversion pipes.
 //
-// When the seven values of a stencil share sign and exponent e, each is
-// M * 2^(e-52) with an integer mantissa M < 2^53 whose top 24 bits Mh lie in
-// [2^23, 2^24). The second difference in units u = 2^(e-52) is the integer
-//   D_d = (Mh[+d] + Mh[-d] - 2 Mh)*2^29 + (Ml[+d] + Ml[-d] - 2 Ml),
-// Ml the low 29 bits; the Mh part lies in (-2^24, 2^24) and the Ml part in
-// (-2^30, 2^30), so A = dMh*2^29, B1 = dMl rounded down to a multiple of 128
-// and B2 = dMl mod 128 are exact FP32 numbers with D_d = A + B1 + B2. An
-// error-free two-sum gives D_d = s_d + t_d to about 2^-48 relative; the
-// weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is formed with exact FMA
-// product splits and two-sums of the three leading products (S) plus the
-// small terms (C), to about 2^-44 of sum_d |w_d D_d|. Finally
-//   T2 = fma(Ci, S*u, fma(Ci, C*u, T))
-// in FP64 (S*u and C*u widened to FP64 exactly by bit manipulation). For
-// negative values the same holds with u = -2^(e-52).
+// When the seven values of a stencil share sign and exponent field E, their
+// IEEE bit patterns, read as 64-bit integers, are K + M with a common K (sign
+// and exponent) and 52-bit fractions M, so the second difference in units
+// u = 2^(E-1075) is the exact integer
+//   D_d = bits(T[-d]) + bits(T[+d]) - 2 bits(T)   (mod 2^64),  |D_d| < 2^53,
+// negated for negative values. With D_d = hi*2^29 + lo (hi = D_d >> 29,
+// |hi| <= 2^24; 0 <= lo < 2^29), A = hi*2^29, B1 = lo rounded down to a
+// multiple of 128 and B2 = lo mod 128 are exact FP32 numbers with
+// D_d = A + B1 + B2. An error-free two-sum gives D_d = s_d + t_d to about
+// 2^-48 relative; the weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is
+// formed with exact FMA product splits and two-sums of the three leading
+// products (S) plus the small terms (C), to about 2^-44 of sum_d |w_d D_d|.
+// Finally
+//   T2 = fma(+-Ci, S*u, fma(+-Ci, C*u, T))
+// in FP64, S*u and C*u widened to FP64 exactly by bit manipulation (the
+// scaling by u is an exponent offset folded into the widening).
 //
-// Stencils with mixed signs or exponents (about 1 % of the points of a smooth
-// field: the shells where it crosses a power of two) or exponents outside
-// the range of the FP32 scalings take cell_f64. The choice depends only on the
-// point's inputs, so every kernel makes the same choice and produces the same
-// bits.
+// Stencils with mixed signs or exponents (the shells where a smooth field
+// crosses a power of two) or with E outside [949, 1139] take cell_f64. The
+// choice depends only on the point's inputs, so every kernel makes the same
+// choice and produces the same bits.
 // ---------------------------------------------------------------------------
-struct Split {
-  int mh;       // top 24 bits of the 53-bit mantissa (with the hidden 1)
-  int ml;       // low 29 bits
-  unsigned eh;  // sign and exponent field (upper 12 bits of the high word)
-};
-
-__device__ __forceinline__ Split split64(double v) {
-  const unsigned H = (unsigned)__double2hiint(v), L = (unsigned)__double2loint(v);
-  Split s;
-  s.eh = H & 0xFFF00000u;
-  s.mh = (int)__funnelshift_l(L, (H & 0x000FFFFFu) | 0x00100000u, 3);
-  s.ml = (int)(L & 0x1FFFFFFFu);
-  return s;
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
 }
+__device__ __forceinline__ unsigned dhi(double v) { return (unsigned)__double2hiint(v); }
 
-// float -> double by bit manipulation, exact for normal floats. Only used on
-// products added to a T of magnitude >= 2^-74 (the exponent range of the fast
-// path); a zero or subnormal float gives a value below 2^-126 there, far
-// below half an ulp of T, which leaves T2 unchanged.
-__device__ __forceinline__ double f2d_bits(float f) {
+// float f -> double f * 2^(E-1075), exact for normal f, by moving the float's
+// exponent and fraction into the double's fields with the exponent offset
+// eoff = (E - 179) << 20 (1023 - 127 + E - 1075 = E - 179). A zero or
+// subnormal f gives a value below 2^(E-1201), under 2^-178 of T's magnitude,
+// which leaves T2 unchanged.
+__device__ __forceinline__ double f2d_scaled(float f, unsigned eoff) {
   const unsigned b = __float_as_uint(f);
-  const unsigned hi = (b & 0x80000000u) | (((b & 0x7FFFFFFFu) >> 3) + (896u << 20));
+  const unsigned hi = (b & 0x80000000u) | (((b & 0x7FFFFFFFu) >> 3) + eoff);
   return __hiloint2double((int)hi, (int)(b << 29));
 }
 
@@ -159,18 +151,31 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   return s;
 }
 
-// Emulated update from the integer second differences dmh[d]*2^29 + dml[d]
-// (units u = +-2^(E-1075), E the biased exponent): |dmh| < 2^24 and
-// |dml| < 2^30, so dmh*2^29, dml rounded down to a multiple of 128 and
-// dml mod 128 convert to FP32 exactly.
-__device__ __forceinline__ double emu_core(double tc, const int *dmh, const int *dml, int E,
-                                           unsigned sign, double ci, const W<double> &w) {
+// Fast-path test from the high words: hc of the centre, hn[6] of the
+// neighbours. True when all seven share sign and exponent and E lies in
+// [949, 1139].
+__device__ __forceinline__ bool emu_fast_ok(unsigned hc, const unsigned *hn) {
+  const unsigned diff = ((hn[0] ^ hc) | (hn[1] ^ hc) | (hn[2] ^ hc) | (hn[3] ^ hc) |
+                         (hn[4] ^ hc) | (hn[5] ^ hc)) &
+                        0xFFF00000u;
+  const unsigned E = (hc >> 20) & 0x7FFu;
+  return diff == 0u && E - 949u <= 190u;
+}
+
+// The emulated update of a fast-path point: tc the centre, nb[6] the bit
+// patterns of the neighbours in the order x-, x+, y-, y+, z-, z+. Any input
+// runs without faults; the value means something only where emu_fast_ok.
+__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
+                                                double ci, const W<double> &w) {
+  const unsigned long long c2 = dbits(tc) << 1;
   float P[3], X[3], R[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float A = __fmul_rn(__int2float_rn(dmh[d]), 536870912.0f);  // dMh * 2^29
-    const float B1 = __int2float_rn(dml[d] & ~127);
-    const float B2 = __int2float_rn(dml[d] & 127);
+    const long long D = (long long)(nb[2 * d] + nb[2 * d + 1] - c2);
+    const unsigned lo = (unsigned)D;
+    const float A = __fmul_rn(__int2float_rn((int)(D >> 29)), 536870912.0f);  // hi * 2^29
+    const float B1 = __uint2float_rn(lo & 0x1FFFFF80u);
+    const float B2 = __uint2float_rn(lo & 0x7Fu);
     float err;
     const float sd = two_sum(A, B1, err);
     const float td = __fadd_rn(err, B2);
@@ -182,42 +187,27 @@ __device__ __forceinline__ double emu_core(double tc, const int *dmh, const int 
   const float S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
   const float C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
                             __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
-  // the mantissa differences of negative values carry the opposite sign of
-  // the value differences
-  const float u = __int_as_float(((E - 948) << 23) | (int)sign);
-  return __fma_rn(ci, f2d_bits(__fmul_rn(S, u)), __fma_rn(ci, f2d_bits(__fmul_rn(C, u)), tc));
+  const unsigned hc = dhi(tc);
+  const unsigned eoff = (hc & 0x7FF00000u) - (179u << 20);
+  // the bit differences of negative values carry the opposite sign of the
+  // value differences: flip Ci instead
+  const double sci = __hiloint2double((int)((unsigned)__double2hiint(ci) ^ (hc & 0x80000000u)),
+                                      __double2loint(ci));
+  return __fma_rn(sci, f2d_scaled(S, eoff), __fma_rn(sci, f2d_scaled(C, eoff), tc));
 }
 
-// The emulated cell's fast path alone: false (and no value) for the points
-// that cell_emu hands to the FP64 cell. Used by kernels that defer those
-// points to a separate pass.
-__device__ __forceinline__ bool emu_fast_ok(const Split &sc, const Split *sn) {
-  const unsigned e = sc.eh;
-  const unsigned diff = (sn[0].eh ^ e) | (sn[1].eh ^ e) | (sn[2].eh ^ e) | (sn[3].eh ^ e) |
-                        (sn[4].eh ^ e) | (sn[5].eh ^ e);
-  const int E = (int)((e >> 20) & 0x7FFu);
-  return diff == 0u && E >= 949 && E <= 1139;
-}
-
-__device__ __forceinline__ double cell_emu_fast(double tc, const Split &sc, const Split *sn,
-                                                double ci, const W<double> &w) {
-  int dmh[3], dml[3];
+// One point: the emulated cell where its fast path applies, else cell_f64.
+__device__ __forceinline__ double cell_emu(double tc, const double *tn, double ci,
+                                           const W<double> &w) {
+  unsigned hn[6];
+  unsigned long long nb[6];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    dmh[d] = sn[2 * d].mh + sn[2 * d + 1].mh - 2 * sc.mh;
-    dml[d] = sn[2 * d].ml + sn[2 * d + 1].ml - 2 * sc.ml;
+  for (int i = 0; i < 6; ++i) {
+    hn[i] = dhi(tn[i]);
+    nb[i] = dbits(tn[i]);
   }
-  return emu_core(tc, dmh, dml, (int)((sc.eh >> 20) & 0x7FFu), sc.eh & 0x80000000u, ci, w);
-}
-
-// One point from pre-split values: sc the centre, sn[6] the neighbours in the
-// order x-, x+, y-, y+, z-, z+ with their doubles in tn[6] (read only by the
-// FP64 fallback). The fallback stays inline: as a call it costs the fast path
-// more (call-site register constraints) than the ~1 % of points that take it.
-__device__ __forceinline__ double cell_emu(double tc, const Split &sc, const Split *sn,
-                                           const double *tn, double ci, const W<double> &w) {
-  if (!emu_fast_ok(sc, sn)) return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
-  return cell_emu_fast(tc, sc, sn, ci, w);
+  if (!emu_fast_ok(dhi(tc), hn)) return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+  return cell_emu_fast(tc, nb, ci, w);
 }
 
 // The FP64 update used by every kernel: the emulated cell or the FP64 cell.
@@ -225,10 +215,7 @@ __device__ __forceinline__ double cell(double t, double xm, double xp, double ym
                                        double zm, double zp, double ci, const W<double> &w) {
   if (!w.emu) return cell_f64(t, xm, xp, ym, yp, zm, zp, ci, w);
   const double tn[6] = {xm, xp, ym, yp, zm, zp};
-  Split sn[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) sn[i] = split64(tn[i]);
-  return cell_emu(t, split64(t), sn, tn, ci, w);
+  return cell_emu(t, tn, ci, w);
 }
 
 __device__ __forceinline__ float cell(float t, float xm, float xp, float ym,

@@ -120,12 +120,16 @@ bool tma_available();
 // Sets the kernel's shared-memory attribute and returns its resident CTAs per
 // SM; call before launching (and before any stream capture).
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
-// FP64 fields with the emulated cell need `fix` (one byte per tile, written by
-// the launch) and run a fix-up launch after the kernel on the same stream.
+// FP64 fields with the emulated cell need `fix`: kFixWords words per tile row
+// (rows of tma_tile_rows), zero on entry, bit m marking march plane m0 + m of
+// the row for the fix-up launch that follows the kernel on the same stream
+// and clears the words again. FP64 tiles march at most kMaxTmaMarch planes.
+constexpr int kFixWords = 4;
+constexpr int kMaxTmaMarch = 32 * kFixWords;
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               unsigned char *fix, cudaStream_t s);
+                               unsigned *fix, cudaStream_t s);
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.

@@ -81,7 +81,7 @@ struct TileSet {
   int n = 0;
   int V = 1;
   int tma = -1;
-  unsigned char *fix = nullptr;  // per-tile fix-up flags (FP64 TMA tile sets)
+  unsigned *fix = nullptr;  // fix-up bits per tile row (FP64 TMA tile sets)
 };
 
 // The split: boundary set (one launch per tile kind) and inner block.
@@ -309,9 +309,14 @@ int upload_tiles(const TileLists &v, int V, TileSet *out, int tma = -1) {
   out->fix = nullptr;
   if (tma >= 0) {
     if (int rc = upload_vec(v.tma, out)) return rc;
-    if (V == 2 && out->n > 0) {  // FP64: flags of the emulated cell's fix-up
-      cudaError_t e = cudaMalloc(&out->fix, (size_t)out->n);
-      if (e == cudaSuccess) e = cudaMemset(out->fix, 0, (size_t)out->n);
+    if (V == 2 && out->n > 0) {  // FP64: marks of the emulated cell's fix-up
+      for (const TmaTile &t : v.tma)
+        if (t.m1 - t.m0 > kMaxTmaMarch)
+          return set_error(IGG_ESTATE, "TMA tile marches %d planes (at most %d)", t.m1 - t.m0,
+                           kMaxTmaMarch);
+      const size_t bytes = (size_t)out->n * tma_tile_rows(IGG_F64, tma) * kFixWords * sizeof(unsigned);
+      cudaError_t e = cudaMalloc(&out->fix, bytes);
+      if (e == cudaSuccess) e = cudaMemset(out->fix, 0, bytes);
       if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fix-up flags)");
     }
     return IGG_OK;

@@ -163,22 +163,27 @@ __device__ __forceinline__ void compute_vec<double, MODE_F64>(
   }
 }
 
-// Emulated fast path: every value split once, splits shared between the two
-// points of the vector; points outside the fast path are left to the fix-up.
+// Emulated fast path for both points, computed unconditionally (no branch
+// in the common case); ok marks the points whose fast path applies, the
+// others are left to the fix-up.
 template <>
 __device__ __forceinline__ void compute_vec<double, MODE_EMU>(
     const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
     const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
     Vec<double> &out, unsigned &ok) {
-  const Split c0 = split64(c.v[0]), c1 = split64(c.v[1]);
-  const Split sn0[6] = {split64(left), c1, split64(ym.v[0]), split64(yp.v[0]), split64(zm.v[0]),
-                        split64(zp.v[0])};
-  const Split sn1[6] = {c0, split64(right), split64(ym.v[1]), split64(yp.v[1]), split64(zm.v[1]),
-                        split64(zp.v[1])};
-  const bool ok0 = emu_fast_ok(c0, sn0), ok1 = emu_fast_ok(c1, sn1);
-  ok = (ok0 ? 1u : 0u) | (ok1 ? 2u : 0u);
-  out.v[0] = ok0 ? cell_emu_fast(c.v[0], c0, sn0, ci.v[0], w) : 0.0;
-  out.v[1] = ok1 ? cell_emu_fast(c.v[1], c1, sn1, ci.v[1], w) : 0.0;
+  const unsigned long long nb0[6] = {dbits(left),     dbits(c.v[1]),  dbits(ym.v[0]),
+                                     dbits(yp.v[0]),  dbits(zm.v[0]), dbits(zp.v[0])};
+  const unsigned long long nb1[6] = {dbits(c.v[0]),   dbits(right),   dbits(ym.v[1]),
+                                     dbits(yp.v[1]),  dbits(zm.v[1]), dbits(zp.v[1])};
+  unsigned hn0[6], hn1[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    hn0[i] = (unsigned)(nb0[i] >> 32);
+    hn1[i] = (unsigned)(nb1[i] >> 32);
+  }
+  ok = (emu_fast_ok(dhi(c.v[0]), hn0) ? 1u : 0u) | (emu_fast_ok(dhi(c.v[1]), hn1) ? 2u : 0u);
+  out.v[0] = cell_emu_fast(c.v[0], nb0, ci.v[0], w);
+  out.v[1] = cell_emu_fast(c.v[1], nb1, ci.v[1], w);
 }
 
 // SWAP = false: rows along y, march along z (box {BW, BH, 1}); SWAP = true:
@@ -189,7 +194,7 @@ template <class S, int LPR_, int H_, bool SWAP, int MODE>
 __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
-                  unsigned *__restrict__ dev_err, unsigned char *__restrict__ fix) {
+                  unsigned *__restrict__ dev_err, unsigned *__restrict__ fix) {
   using Sh = TmaShape<S, LPR_, H_>;
   using C = typename Num<S>::C;
   constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
@@ -198,8 +203,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
   const unsigned full0 = sbase + NS * Sh::STAGE;
   const unsigned empty0 = full0 + NS * 8;
   volatile int *flags = reinterpret_cast<volatile int *>(smem + NS * Sh::STAGE + 2 * NS * 8);
-  // flags[0]: abort; flags[1]: loads issued; flags[2]: loads consumed;
-  // flags[3]: some point of the tile left to the fix-up (MODE_EMU)
+  // flags[0]: abort; flags[1]: loads issued; flags[2]: loads consumed
 
   const TmaTile t = tiles[blockIdx.x];
   const int K = (t.m1 - t.m0) + 2;
@@ -213,7 +217,6 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     flags[0] = 0;
     flags[1] = 0;
     flags[2] = 0;
-    flags[3] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -261,8 +264,9 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     const long long sy = nx, sz = (long long)nx * ny;
     const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
     Vec<S> zm[Sh::RPT];
-    bool deferred = false;
-    bool ok = mbar_wait(full0, 0);
+    // loads 0 and 1 (K >= 2 always); afterwards step k waits load k + 1 only,
+    // load k having been waited by step k - 1
+    bool ok = mbar_wait(full0, 0) && mbar_wait(full0 + 8, 0);
     if (!ok) {
       atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
       flags[0] = 1;
@@ -273,12 +277,11 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0);
     }
-    int consumed = 1;
+    int consumed = 2;
     for (int m = t.m0; ok && m < t.m1; ++m) {
       const int k = m - t.m0 + 1;
       const int s = k % NS, s1 = (k + 1) % NS;
-      if (!mbar_wait(full0 + 8 * s, (k / NS) & 1) ||
-          !mbar_wait(full0 + 8 * s1, ((k + 1) / NS) & 1)) {
+      if (!mbar_wait(full0 + 8 * s1, ((k + 1) / NS) & 1)) {
         atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
         flags[0] = 1;
         ok = false;
@@ -313,11 +316,18 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
           if (full_vec && okm == (1u << V) - 1u) {
             *reinterpret_cast<uint4 *>(dst) = pack(out);
           } else {
+            bool deferred = false;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
               const bool in = xs + i >= t.xb && xs + i < t.xe;
               if (in && (okm >> i & 1u)) Num<S>::st(dst + i, out.v[i]);
               deferred = deferred || (in && !(okm >> i & 1u));
+            }
+            // mark (row, plane) of the tile for the fix-up
+            if (MODE == MODE_EMU && deferred) {
+              const int mi = m - t.m0;
+              atomicOr(fix + ((size_t)blockIdx.x * Sh::H + r) * kFixWords + (mi >> 5),
+                       1u << (mi & 31));
             }
           }
         }
@@ -327,10 +337,8 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       if (lane == 0) mbar_arrive(empty0 + 8 * s);
     }
     if (warp == 0 && lane == 0) flags[2] = consumed;
-    if (MODE == MODE_EMU && __any_sync(0xffffffffu, deferred) && lane == 0) flags[3] = 1;
   }
   __syncthreads();
-  if (MODE == MODE_EMU && threadIdx.x == 0) fix[blockIdx.x] = flags[3] ? 1 : 0;
   // After an abort, wait (bounded) for copies issued but never consumed, so
   // that no bulk copy writes into this CTA's shared memory after it exits.
   if (threadIdx.x == 0 && flags[0]) {
@@ -343,34 +351,50 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
   }
 }
 
-// Fix-up of a MODE_EMU launch: in every flagged tile, the points outside the
-// emulated cell's fast path get the FP64 cell (the same choice and the same
-// arithmetic as cell() everywhere else). One CTA per tile of the launch.
+// Fix-up of a MODE_EMU launch: in every marked (row, plane) of a tile, the
+// points outside the emulated cell's fast path get the FP64 cell (the same
+// choice and the same arithmetic as cell() everywhere else). One warp per
+// tile row reads and clears the row's plane bits and handles its marked
+// planes, two points per lane (FP64 tiles are 64 points wide).
 template <bool SWAP>
 __global__ void __launch_bounds__(256)
-    k_fixup_f64(const TmaTile *__restrict__ tiles, const unsigned char *__restrict__ fix,
+    k_fixup_f64(const TmaTile *__restrict__ tiles, int ntiles, unsigned *__restrict__ fix,
                 double *__restrict__ T2, const double *__restrict__ T,
                 const double *__restrict__ Ci, int nx, int ny, Coef c0) {
-  if (!fix[blockIdx.x]) return;
-  const TmaTile t = tiles[blockIdx.x];
+  using Sh = TmaShape<double, WideShape<double>::LPR, WideShape<double>::H>;
+  static_assert(Sh::W == 64 && kFixWords <= 32, "fix-up layout");
+  const int gw = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int tile = gw / Sh::H, row = gw % Sh::H;
+  if (tile >= ntiles) return;
+  unsigned *wp = fix + (size_t)gw * kFixWords;
+  const unsigned bits = lane < kFixWords ? wp[lane] : 0u;
+  if (__ballot_sync(0xffffffffu, bits != 0u) == 0u) return;
+  if (bits) wp[lane] = 0u;
+  const TmaTile t = tiles[tile];
   const W<double> w = make_w(c0, 0.0);
   const long long sy = nx, sz = (long long)nx * ny;
   const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
-  const int nxr = t.xe - t.xb, nr = t.re - t.r0;
-  const long long npts = (long long)nxr * nr * (t.m1 - t.m0);
-  for (long long i = threadIdx.x; i < npts; i += blockDim.x) {
-    const int x = t.xb + (int)(i % nxr);
-    const int r = t.r0 + (int)((i / nxr) % nr);
-    const int m = t.m0 + (int)(i / ((long long)nxr * nr));
-    const long long p = t.base + x + srow * r + smarch * m;
-    const double tc = __ldg(T + p);
-    const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
-                          __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-    Split sn[6];
+  const int r = t.r0 + row;
+  for (int wd = 0; wd < kFixWords; ++wd) {
+    unsigned b = __shfl_sync(0xffffffffu, bits, wd);
+    while (b) {
+      const int m = t.m0 + wd * 32 + __ffs(b) - 1;
+      b &= b - 1;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) sn[k] = split64(tn[k]);
-    if (!emu_fast_ok(split64(tc), sn))
-      T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+      for (int i = 0; i < 2; ++i) {
+        const int x = t.x0 + 2 * lane + i;
+        if (x < t.xb || x >= t.xe) continue;
+        const long long p = t.base + x + srow * r + smarch * m;
+        const double tc = __ldg(T + p);
+        const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
+                              __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
+        unsigned hn[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) hn[k] = dhi(tn[k]);
+        if (!emu_fast_ok(dhi(tc), hn))
+          T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+      }
+    }
   }
 }
 
@@ -421,7 +445,7 @@ cudaError_t prepare_t(int *ctas_per_sm) {
 template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     unsigned char *fix, cudaStream_t s) {
+                     unsigned *fix, cudaStream_t s) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
   CUtensorMap mT, mC;
   const bool ok = SWAP ? encode<S>(&mT, T, nx, ny, nzt, Sh::BW, 1, Sh::BH) &&
@@ -434,7 +458,8 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
                                                           dev_err, fix);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && MODE == MODE_EMU) {
-    k_fixup_f64<SWAP><<<ntiles, 256, 0, s>>>(tiles, fix, (double *)T2, (const double *)T,
+    const int blocks = (int)(((long long)ntiles * Sh::H + 7) / 8);
+    k_fixup_f64<SWAP><<<blocks, 256, 0, s>>>(tiles, ntiles, fix, (double *)T2, (const double *)T,
                                              (const double *)Ci, nx, ny, c);
     e = cudaGetLastError();
   }
@@ -461,7 +486,7 @@ cudaError_t prepare_v(int variant, int *ctas) {
 template <class S, bool SWAP>
 cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     unsigned char *fix, cudaStream_t s) {
+                     unsigned *fix, cudaStream_t s) {
   if constexpr (sizeof(S) == 8) {
     if (c.f64_emu) {
       if (!fix) return cudaErrorInvalidValue;
@@ -479,7 +504,7 @@ cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
 template <class S>
 cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, const void *T,
                      const void *Ci, int nx, int ny, long long nzt, const Coef &c,
-                     unsigned *dev_err, unsigned char *fix, cudaStream_t s) {
+                     unsigned *dev_err, unsigned *fix, cudaStream_t s) {
   switch (variant) {
     case TMA_WIDE:
       return launch_m<S, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
@@ -523,7 +548,7 @@ cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               unsigned char *fix, cudaStream_t s) {
+                               unsigned *fix, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   switch (dt) {
     case IGG_F64:
