@@ -113,8 +113,9 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // negated for negative values. With D_d = hi*2^29 + lo (hi = D_d >> 29,
 // |hi| <= 2^24; 0 <= lo < 2^29), A = hi*2^29, B1 = lo rounded down to a
 // multiple of 128 and B2 = lo mod 128 are exact FP32 numbers with
-// D_d = A + B1 + B2. An error-free two-sum gives D_d = s_d + t_d to about
-// 2^-48 relative; the weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is
+// D_d = A + B1 + B2. An error-free sum of A and B1 gives D_d = s_d + t_d to
+// about 2^-48 relative (A is zero or at least 2^29 > B1 in magnitude, so Dekker's
+// fast two-sum is exact); the weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is
 // formed with exact FMA product splits and two-sums of the three leading
 // products (S) plus the small terms (C), to about 2^-44 of sum_d |w_d D_d|.
 // Finally
@@ -151,6 +152,13 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e) {
   return s;
 }
 
+// error-free sum when |a| >= |b| or a == 0 (Dekker): a + b = s + e exactly
+__device__ __forceinline__ float fast_two_sum(float a, float b, float &e) {
+  const float s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+  return s;
+}
+
 // Fast-path test from the high words: hc of the centre, hn[6] of the
 // neighbours. True when all seven share sign and exponent and E lies in
 // [949, 1139].
@@ -177,7 +185,7 @@ __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long l
     const float B1 = __uint2float_rn(lo & 0x1FFFFF80u);
     const float B2 = __uint2float_rn(lo & 0x7Fu);
     float err;
-    const float sd = two_sum(A, B1, err);
+    const float sd = fast_two_sum(A, B1, err);  // A a multiple of 2^29, 0 <= B1 < 2^29
     const float td = __fadd_rn(err, B2);
     P[d] = __fmul_rn(w.wh[d], sd);
     X[d] = __fmaf_rn(w.wh[d], sd, -P[d]);
