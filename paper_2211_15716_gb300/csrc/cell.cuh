@@ -62,6 +62,7 @@ struct W<double> {
   double wx, wy, wz, wc;
   float wh[3], wl[3];
   bool emu;
+  int ng;  // weight groups (weight_groups)
 };
 
 __device__ __forceinline__ W<double> make_w(const Coef &c, double) {
@@ -77,6 +78,7 @@ __device__ __forceinline__ W<double> make_w(const Coef &c, double) {
     w.wl[i] = __double2float_rn(__dsub_rn(d[i], (double)w.wh[i]));
   }
   w.emu = c.f64_emu != 0;
+  w.ng = weight_groups(c.wx, c.wy, c.wz);
   return w;
 }
 __device__ __forceinline__ W<float> make_w(const Coef &c, float) {
@@ -110,14 +112,17 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // and exponent) and 52-bit fractions M, so the second difference in units
 // u = 2^(E-1075) is the exact integer
 //   D_d = bits(T[-d]) + bits(T[+d]) - 2 bits(T)   (mod 2^64),  |D_d| < 2^53,
-// negated for negative values. With D_d = hi*2^29 + lo (hi = D_d >> 29,
-// |hi| <= 2^24; 0 <= lo < 2^29), A = hi*2^29, B1 = lo rounded down to a
-// multiple of 128 and B2 = lo mod 128 are exact FP32 numbers with
-// D_d = A + B1 + B2. An error-free sum of A and B1 gives D_d = s_d + t_d to
-// about 2^-48 relative (A is zero or at least 2^29 > B1 in magnitude, so Dekker's
-// fast two-sum is exact); the weighted sum l = sum_d (wh_d + wl_d)(s_d + t_d) is
-// formed with exact FMA product splits and two-sums of the three leading
-// products (S) plus the small terms (C), to about 2^-44 of sum_d |w_d D_d|.
+// negated for negative values. Dimensions of equal weight are grouped: their
+// D_d add exactly into one integer G_g (|G_g| < 2^55), so that the weighted
+// sum l = sum_g w_g G_g has one, two or three products. With
+// G_g = hi*2^31 + lo (hi = G_g >> 31, |hi| <= 2^24; 0 <= lo < 2^31),
+// A = hi*2^31, B1 = lo rounded down to a multiple of 128 and B2 = lo mod 128
+// are exact FP32 numbers with G_g = A + B1 + B2. An error-free sum of A and
+// B1 gives G_g = s_g + t_g to about 2^-48 relative (A is zero or at least
+// 2^31 > B1 in magnitude, so Dekker's fast two-sum is exact); l is formed
+// with exact FMA product splits (wh_g + wl_g)(s_g + t_g) and two-sums of the
+// leading products (S) plus the small terms (C), to about 2^-44 of
+// sum_g |w_g G_g|.
 // Finally
 //   T2 = fma(+-Ci, S*u, fma(+-Ci, C*u, T))
 // in FP64, S*u and C*u widened to FP64 exactly by bit manipulation (the
@@ -170,31 +175,56 @@ __device__ __forceinline__ bool emu_fast_ok(unsigned hc, const unsigned *hn) {
   return diff == 0u && E - 949u <= 190u;
 }
 
-// The emulated update of a fast-path point: tc the centre, nb[6] the bit
-// patterns of the neighbours in the order x-, x+, y-, y+, z-, z+. Any input
-// runs without faults; the value means something only where emu_fast_ok.
+// The emulated update of a fast-path point with NG weight groups: tc the
+// centre, nb[6] the bit patterns of the neighbours in the order x-, x+, y-,
+// y+, z-, z+. Any input runs without faults; the value means something only
+// where emu_fast_ok.
+template <int NG>
 __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
                                                 double ci, const W<double> &w) {
   const unsigned long long c2 = dbits(tc) << 1;
-  float P[3], X[3], R[3];
+  long long D[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const long long D = (long long)(nb[2 * d] + nb[2 * d + 1] - c2);
-    const unsigned lo = (unsigned)D;
-    const float A = __fmul_rn(__int2float_rn((int)(D >> 29)), 536870912.0f);  // hi * 2^29
-    const float B1 = __uint2float_rn(lo & 0x1FFFFF80u);
+  for (int d = 0; d < 3; ++d) D[d] = (long long)(nb[2 * d] + nb[2 * d + 1] - c2);
+  long long G[NG];
+  if constexpr (NG == 1) {
+    G[0] = D[0] + D[1] + D[2];
+  } else if constexpr (NG == 2) {
+    G[0] = D[0];
+    G[1] = D[1] + D[2];
+  } else {
+    G[0] = D[0];
+    G[1] = D[1];
+    G[2] = D[2];
+  }
+  float P[NG], X[NG], R[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const unsigned lo = (unsigned)G[g];
+    const float A = __fmul_rn(__int2float_rn((int)(G[g] >> 31)), 2147483648.0f);  // hi * 2^31
+    const float B1 = __uint2float_rn(lo & 0x7FFFFF80u);
     const float B2 = __uint2float_rn(lo & 0x7Fu);
     float err;
-    const float sd = fast_two_sum(A, B1, err);  // A a multiple of 2^29, 0 <= B1 < 2^29
-    const float td = __fadd_rn(err, B2);
-    P[d] = __fmul_rn(w.wh[d], sd);
-    X[d] = __fmaf_rn(w.wh[d], sd, -P[d]);
-    R[d] = __fmaf_rn(w.wl[d], sd, __fmul_rn(w.wh[d], td));
+    const float sg = fast_two_sum(A, B1, err);  // A a multiple of 2^31, 0 <= B1 < 2^31
+    const float tg = __fadd_rn(err, B2);
+    P[g] = __fmul_rn(w.wh[g], sg);
+    X[g] = __fmaf_rn(w.wh[g], sg, -P[g]);
+    R[g] = __fmaf_rn(w.wl[g], sg, __fmul_rn(w.wh[g], tg));
   }
-  float e1, e2;
-  const float S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
-  const float C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
-                            __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
+  float S, C;
+  if constexpr (NG == 1) {
+    S = P[0];
+    C = __fadd_rn(X[0], R[0]);
+  } else if constexpr (NG == 2) {
+    float e1;
+    S = two_sum(P[0], P[1], e1);
+    C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), e1), __fadd_rn(R[0], R[1]));
+  } else {
+    float e1, e2;
+    S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
+    C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
+                  __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
+  }
   const unsigned hc = dhi(tc);
   const unsigned eoff = (hc & 0x7FF00000u) - (179u << 20);
   // the bit differences of negative values carry the opposite sign of the
@@ -202,6 +232,13 @@ __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long l
   const double sci = __hiloint2double((int)((unsigned)__double2hiint(ci) ^ (hc & 0x80000000u)),
                                       __double2loint(ci));
   return __fma_rn(sci, f2d_scaled(S, eoff), __fma_rn(sci, f2d_scaled(C, eoff), tc));
+}
+
+__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
+                                                double ci, const W<double> &w) {
+  if (w.ng == 1) return cell_emu_fast<1>(tc, nb, ci, w);
+  if (w.ng == 2) return cell_emu_fast<2>(tc, nb, ci, w);
+  return cell_emu_fast<3>(tc, nb, ci, w);
 }
 
 // One point: the emulated cell where its fast path applies, else cell_f64.

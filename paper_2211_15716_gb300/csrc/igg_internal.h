@@ -43,6 +43,13 @@ struct Coef {
 
 Coef make_coef(double lam, double dt, double dx, double dy, double dz);
 
+// Weight groups of the emulated FP64 cell: 1 when wx == wy == wz, 2 when
+// wy == wz only (the second differences of equal weights are added exactly
+// before the product), else 3.
+__host__ __device__ inline int weight_groups(double wx, double wy, double wz) {
+  return (wx == wy && wy == wz) ? 1 : (wy == wz ? 2 : 3);
+}
+
 // One face-plane copy of the halo update: the plane whose point with both
 // in-plane indices 0 is at element offset `src` is copied onto the plane at
 // `dst` (same in-plane geometry).

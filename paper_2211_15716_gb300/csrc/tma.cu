@@ -126,9 +126,14 @@ __device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
 
 // How a TMA kernel computes its points: MODE_CELL = the shared cell() of the
 // storage type (FP32, BF16); for FP64 fields, MODE_F64 = the FP64 cell and
-// MODE_EMU = the emulated cell's fast path, leaving the points it hands to the
+// MODE_EMU + (3 - NG) = the emulated cell's fast path with NG weight groups
+// (the grid's weight_groups), leaving the points it hands to the
 // FP64 cell unwritten and flagging their tile for k_fixup_f64.
-enum { MODE_CELL = 0, MODE_F64 = 1, MODE_EMU = 2 };
+enum { MODE_CELL = 0, MODE_F64 = 1, MODE_EMU = 2, MODE_EMU_LAST = 4 };
+__host__ __device__ constexpr bool is_emu(int mode) {
+  return mode >= MODE_EMU && mode <= MODE_EMU_LAST;
+}
+constexpr int emu_mode(int ng) { return MODE_EMU + 3 - ng; }
 
 // V points of one row: centre vector c, x neighbours from c and the points
 // beyond it (left, right), y and z neighbour vectors. ok gets bit i for each
@@ -166,8 +171,8 @@ __device__ __forceinline__ void compute_vec<double, MODE_F64>(
 // Emulated fast path for both points, computed unconditionally (no branch
 // in the common case); ok marks the points whose fast path applies, the
 // others are left to the fix-up.
-template <>
-__device__ __forceinline__ void compute_vec<double, MODE_EMU>(
+template <int NG>
+__device__ __forceinline__ void compute_vec_emu(
     const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
     const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
     Vec<double> &out, unsigned &ok) {
@@ -182,8 +187,29 @@ __device__ __forceinline__ void compute_vec<double, MODE_EMU>(
     hn1[i] = (unsigned)(nb1[i] >> 32);
   }
   ok = (emu_fast_ok(dhi(c.v[0]), hn0) ? 1u : 0u) | (emu_fast_ok(dhi(c.v[1]), hn1) ? 2u : 0u);
-  out.v[0] = cell_emu_fast(c.v[0], nb0, ci.v[0], w);
-  out.v[1] = cell_emu_fast(c.v[1], nb1, ci.v[1], w);
+  out.v[0] = cell_emu_fast<NG>(c.v[0], nb0, ci.v[0], w);
+  out.v[1] = cell_emu_fast<NG>(c.v[1], nb1, ci.v[1], w);
+}
+template <>
+__device__ __forceinline__ void compute_vec<double, MODE_EMU>(
+    const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
+    const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
+    Vec<double> &out, unsigned &ok) {
+  compute_vec_emu<3>(c, left, right, ym, yp, zm, zp, ci, w, out, ok);
+}
+template <>
+__device__ __forceinline__ void compute_vec<double, MODE_EMU + 1>(
+    const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
+    const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
+    Vec<double> &out, unsigned &ok) {
+  compute_vec_emu<2>(c, left, right, ym, yp, zm, zp, ci, w, out, ok);
+}
+template <>
+__device__ __forceinline__ void compute_vec<double, MODE_EMU + 2>(
+    const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
+    const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
+    Vec<double> &out, unsigned &ok) {
+  compute_vec_emu<1>(c, left, right, ym, yp, zm, zp, ci, w, out, ok);
 }
 
 // SWAP = false: rows along y, march along z (box {BW, BH, 1}); SWAP = true:
@@ -324,7 +350,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
               deferred = deferred || (in && !(okm >> i & 1u));
             }
             // mark (row, plane) of the tile for the fix-up
-            if (MODE == MODE_EMU && deferred) {
+            if (is_emu(MODE) && deferred) {
               const int mi = m - t.m0;
               atomicOr(fix + ((size_t)blockIdx.x * Sh::H + r) * kFixWords + (mi >> 5),
                        1u << (mi & 31));
@@ -457,7 +483,7 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
       <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
                                                           dev_err, fix);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && MODE == MODE_EMU) {
+  if (e == cudaSuccess && is_emu(MODE)) {
     const int blocks = (int)(((long long)ntiles * Sh::H + 7) / 8);
     k_fixup_f64<SWAP><<<blocks, 256, 0, s>>>(tiles, ntiles, fix, (double *)T2, (const double *)T,
                                              (const double *)Ci, nx, ny, c);
@@ -474,6 +500,12 @@ cudaError_t prepare_v(int variant, int *ctas) {
   if constexpr (sizeof(S) == 8) {
     cudaError_t e = swap ? prepare_t<S, WideShape<S>, true, MODE_F64>(nullptr)
                          : prepare_t<S, WideShape<S>, false, MODE_F64>(nullptr);
+    if (e == cudaSuccess)
+      e = swap ? prepare_t<S, WideShape<S>, true, MODE_EMU + 1>(nullptr)
+               : prepare_t<S, WideShape<S>, false, MODE_EMU + 1>(nullptr);
+    if (e == cudaSuccess)
+      e = swap ? prepare_t<S, WideShape<S>, true, MODE_EMU + 2>(nullptr)
+               : prepare_t<S, WideShape<S>, false, MODE_EMU + 2>(nullptr);
     if (e != cudaSuccess) return e;
     return swap ? prepare_t<S, WideShape<S>, true, MODE_EMU>(ctas)
                 : prepare_t<S, WideShape<S>, false, MODE_EMU>(ctas);
@@ -490,8 +522,17 @@ cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
   if constexpr (sizeof(S) == 8) {
     if (c.f64_emu) {
       if (!fix) return cudaErrorInvalidValue;
-      return launch_t<S, WideShape<S>, SWAP, MODE_EMU>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
-                                                       dev_err, fix, s);
+      switch (weight_groups(c.wx, c.wy, c.wz)) {
+        case 1:
+          return launch_t<S, WideShape<S>, SWAP, emu_mode(1)>(tiles, ntiles, T2, T, Ci, nx, ny,
+                                                              nzt, c, dev_err, fix, s);
+        case 2:
+          return launch_t<S, WideShape<S>, SWAP, emu_mode(2)>(tiles, ntiles, T2, T, Ci, nx, ny,
+                                                              nzt, c, dev_err, fix, s);
+        default:
+          return launch_t<S, WideShape<S>, SWAP, emu_mode(3)>(tiles, ntiles, T2, T, Ci, nx, ny,
+                                                              nzt, c, dev_err, fix, s);
+      }
     }
     return launch_t<S, WideShape<S>, SWAP, MODE_F64>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
                                                      dev_err, fix, s);
