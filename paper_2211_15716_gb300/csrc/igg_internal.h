@@ -127,12 +127,13 @@ bool tma_available();
 // Sets the kernel's shared-memory attribute and returns its resident CTAs per
 // SM; call before launching (and before any stream capture).
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
-// FP64 fields with the emulated cell need `fix`: kFixWords words per tile row
-// (rows of tma_tile_rows), zero on entry, bit m marking march plane m0 + m of
-// the row for the fix-up launch that follows the kernel on the same stream
-// and clears the words again. FP64 tiles march at most kMaxTmaMarch planes.
-constexpr int kFixWords = 4;
-constexpr int kMaxTmaMarch = 32 * kFixWords;
+// FP64 fields with the emulated cell need `fix`, zero on entry: per tile,
+// two words of point bits (points 0-31 and 32-63 of the 64-wide row) for each
+// row (tma_tile_rows) and each of kMaxTmaMarch march planes, marking the
+// points left to the FP64 cell; after the tiles' masks, one word per tile
+// marking tiles with any mark. The fix-up launch that follows the kernel on
+// the same stream clears them again.
+constexpr int kMaxTmaMarch = 128;
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,

@@ -314,7 +314,9 @@ int upload_tiles(const TileLists &v, int V, TileSet *out, int tma = -1) {
         if (t.m1 - t.m0 > kMaxTmaMarch)
           return set_error(IGG_ESTATE, "TMA tile marches %d planes (at most %d)", t.m1 - t.m0,
                            kMaxTmaMarch);
-      const size_t bytes = (size_t)out->n * tma_tile_rows(IGG_F64, tma) * kFixWords * sizeof(unsigned);
+      const size_t bytes = (size_t)out->n *
+                           ((size_t)tma_tile_rows(IGG_F64, tma) * kMaxTmaMarch * 2 + 1) *
+                           sizeof(unsigned);
       cudaError_t e = cudaMalloc(&out->fix, bytes);
       if (e == cudaSuccess) e = cudaMemset(out->fix, 0, bytes);
       if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fix-up flags)");

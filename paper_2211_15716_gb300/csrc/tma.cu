@@ -304,6 +304,10 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       if (lane == 0) mbar_arrive(empty0);
     }
     int consumed = 2;
+    // FP64: two march steps per iteration (the z-plane registers alternate
+    // instead of being copied; measured faster by a few percent)
+    constexpr int kUnroll = sizeof(S) == 8 ? 2 : 1;
+#pragma unroll kUnroll
     for (int m = t.m0; ok && m < t.m1; ++m) {
       const int k = m - t.m0 + 1;
       const int s = k % NS, s1 = (k + 1) % NS;
@@ -342,18 +346,21 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
           if (full_vec && okm == (1u << V) - 1u) {
             *reinterpret_cast<uint4 *>(dst) = pack(out);
           } else {
-            bool deferred = false;
+            unsigned deferred = 0u;  // bit i: point i left to the fix-up
 #pragma unroll
             for (int i = 0; i < V; ++i) {
               const bool in = xs + i >= t.xb && xs + i < t.xe;
               if (in && (okm >> i & 1u)) Num<S>::st(dst + i, out.v[i]);
-              deferred = deferred || (in && !(okm >> i & 1u));
+              if (in && !(okm >> i & 1u)) deferred |= 1u << i;
             }
-            // mark (row, plane) of the tile for the fix-up
+            // mark the points in the tile's mask of this row and plane, and
+            // the tile as marked
             if (is_emu(MODE) && deferred) {
-              const int mi = m - t.m0;
-              atomicOr(fix + ((size_t)blockIdx.x * Sh::H + r) * kFixWords + (mi >> 5),
-                       1u << (mi & 31));
+              constexpr int PT = Sh::H * kMaxTmaMarch * 2;
+              const int xi = sl * V;  // point index in the row, V divides 32
+              const size_t wi = ((size_t)r * kMaxTmaMarch + (m - t.m0)) * 2 + (xi >> 5);
+              if (atomicOr(fix + (size_t)blockIdx.x * PT + wi, deferred << (xi & 31)) == 0u)
+                fix[(size_t)gridDim.x * PT + blockIdx.x] = 1u;
             }
           }
         }
@@ -377,49 +384,43 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
   }
 }
 
-// Fix-up of a MODE_EMU launch: in every marked (row, plane) of a tile, the
-// points outside the emulated cell's fast path get the FP64 cell (the same
-// choice and the same arithmetic as cell() everywhere else). One warp per
-// tile row reads and clears the row's plane bits and handles its marked
-// planes, two points per lane (FP64 tiles are 64 points wide).
+// Fix-up of an emulated-cell launch: the points left by the kernel get the
+// FP64 cell (the same choice and the same arithmetic as cell() everywhere
+// else). One block per tile; a tile without marks exits at once. Otherwise
+// the block's threads take the tile's point-mask words in turn (two words of
+// 32 points per row and plane, FP64 tiles being 64 points wide), clear the
+// nonzero ones and update their points.
 template <bool SWAP>
 __global__ void __launch_bounds__(256)
     k_fixup_f64(const TmaTile *__restrict__ tiles, int ntiles, unsigned *__restrict__ fix,
                 double *__restrict__ T2, const double *__restrict__ T,
                 const double *__restrict__ Ci, int nx, int ny, Coef c0) {
   using Sh = TmaShape<double, WideShape<double>::LPR, WideShape<double>::H>;
-  static_assert(Sh::W == 64 && kFixWords <= 32, "fix-up layout");
-  const int gw = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  const int tile = gw / Sh::H, row = gw % Sh::H;
-  if (tile >= ntiles) return;
-  unsigned *wp = fix + (size_t)gw * kFixWords;
-  const unsigned bits = lane < kFixWords ? wp[lane] : 0u;
-  if (__ballot_sync(0xffffffffu, bits != 0u) == 0u) return;
-  if (bits) wp[lane] = 0u;
-  const TmaTile t = tiles[tile];
+  static_assert(Sh::W == 64, "fix-up layout: two mask words per row and plane");
+  constexpr int PT = Sh::H * kMaxTmaMarch * 2;  // mask words of one tile
+  unsigned *flag = fix + (size_t)ntiles * PT + blockIdx.x;
+  if (*flag == 0u) return;
+  __syncthreads();  // every thread has read the flag
+  if (threadIdx.x == 0) *flag = 0u;
+  const TmaTile t = tiles[blockIdx.x];
   const W<double> w = make_w(c0, 0.0);
   const long long sy = nx, sz = (long long)nx * ny;
   const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
-  const int r = t.r0 + row;
-  for (int wd = 0; wd < kFixWords; ++wd) {
-    unsigned b = __shfl_sync(0xffffffffu, bits, wd);
-    while (b) {
-      const int m = t.m0 + wd * 32 + __ffs(b) - 1;
-      b &= b - 1;
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int x = t.x0 + 2 * lane + i;
-        if (x < t.xb || x >= t.xe) continue;
-        const long long p = t.base + x + srow * r + smarch * m;
-        const double tc = __ldg(T + p);
-        const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
-                              __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-        unsigned hn[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) hn[k] = dhi(tn[k]);
-        if (!emu_fast_ok(dhi(tc), hn))
-          T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
-      }
+  const int planes = t.m1 - t.m0, per_row = 2 * planes;
+  unsigned *tw = fix + (size_t)blockIdx.x * PT;
+  for (int i = threadIdx.x; i < Sh::H * per_row; i += blockDim.x) {
+    const int row = i / per_row, mi = (i % per_row) >> 1, half = i & 1;
+    unsigned *wp = tw + ((size_t)row * kMaxTmaMarch + mi) * 2 + half;
+    unsigned b = *wp;
+    if (b == 0u) continue;
+    *wp = 0u;
+    const long long prow = t.base + t.x0 + half * 32 + srow * (t.r0 + row) + smarch * (t.m0 + mi);
+    for (; b; b &= b - 1) {
+      const long long p = prow + __ffs(b) - 1;
+      const double tc = __ldg(T + p);
+      const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
+                            __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
+      T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
     }
   }
 }
@@ -484,8 +485,7 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
                                                           dev_err, fix);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && is_emu(MODE)) {
-    const int blocks = (int)(((long long)ntiles * Sh::H + 7) / 8);
-    k_fixup_f64<SWAP><<<blocks, 256, 0, s>>>(tiles, ntiles, fix, (double *)T2, (const double *)T,
+    k_fixup_f64<SWAP><<<ntiles, 256, 0, s>>>(tiles, ntiles, fix, (double *)T2, (const double *)T,
                                              (const double *)Ci, nx, ny, c);
     e = cudaGetLastError();
   }
