@@ -127,13 +127,16 @@ bool tma_available();
 // Sets the kernel's shared-memory attribute and returns its resident CTAs per
 // SM; call before launching (and before any stream capture).
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
-// FP64 fields with the emulated cell need `fix`, zero on entry: per tile,
-// two words of point bits (points 0-31 and 32-63 of the 64-wide row) for each
-// row (tma_tile_rows) and each of kMaxTmaMarch march planes, marking the
-// points left to the FP64 cell; after the tiles' masks, one word per tile
-// marking tiles with any mark. The fix-up launch that follows the kernel on
-// the same stream clears them again.
+// FP64 fields with the emulated cell need `fix`, of tma_fix_words(ntiles)
+// words: per tile, two words of point bits (points 0-31 and 32-63 of the
+// 64-wide row) for each row (tma_tile_rows) and each of kMaxTmaMarch march
+// planes, marking the points left to the FP64 cell, written only where
+// nonzero; then the list of the words written (as many slots as mask words),
+// its length and a block counter, both zero on entry. The fix-up launch that
+// follows the kernel on the same stream updates the listed points and resets
+// the length and the counter.
 constexpr int kMaxTmaMarch = 128;
+size_t tma_fix_words(int ntiles);
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,

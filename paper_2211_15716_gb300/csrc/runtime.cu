@@ -314,9 +314,10 @@ int upload_tiles(const TileLists &v, int V, TileSet *out, int tma = -1) {
         if (t.m1 - t.m0 > kMaxTmaMarch)
           return set_error(IGG_ESTATE, "TMA tile marches %d planes (at most %d)", t.m1 - t.m0,
                            kMaxTmaMarch);
-      const size_t bytes = (size_t)out->n *
-                           ((size_t)tma_tile_rows(IGG_F64, tma) * kMaxTmaMarch * 2 + 1) *
-                           sizeof(unsigned);
+      // word indices of the fix-up list are 32-bit
+      if (tma_fix_words(out->n) >= (1ull << 32))
+        return set_error(IGG_EINVAL, "too many TMA tiles (%d) for the fix-up list", out->n);
+      const size_t bytes = tma_fix_words(out->n) * sizeof(unsigned);
       cudaError_t e = cudaMalloc(&out->fix, bytes);
       if (e == cudaSuccess) e = cudaMemset(out->fix, 0, bytes);
       if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fix-up flags)");

@@ -124,6 +124,25 @@ __device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);
 }
 
+// The list part of a tile set's fix-up buffer (layout in igg_internal.h).
+struct FixList {
+  unsigned *words, *count, *done;
+};
+__device__ __forceinline__ FixList fix_list(unsigned *fix, unsigned ntiles, unsigned per_tile) {
+  unsigned *l = fix + (size_t)ntiles * per_tile;
+  return {l, l + (size_t)ntiles * per_tile, l + (size_t)ntiles * per_tile + 1};
+}
+constexpr int kFixupBlocks = 8 * 152;
+
+// bit i of x (i < 16) to bit 2i
+__device__ __forceinline__ unsigned spread16(unsigned x) {
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}  // one resident wave of 256-thread blocks
+
 // How a TMA kernel computes its points: MODE_CELL = the shared cell() of the
 // storage type (FP32, BF16); for FP64 fields, MODE_F64 = the FP64 cell and
 // MODE_EMU + (3 - NG) = the emulated cell's fast path with NG weight groups
@@ -292,7 +311,9 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     Vec<S> zm[Sh::RPT];
     // loads 0 and 1 (K >= 2 always); afterwards step k waits load k + 1 only,
     // load k having been waited by step k - 1
-    bool ok = mbar_wait(full0, 0) && mbar_wait(full0 + 8, 0);
+    // wait results are made warp-uniform: the warp's votes and __syncwarp
+    // need every lane in the loop
+    bool ok = __all_sync(0xffffffffu, mbar_wait(full0, 0) && mbar_wait(full0 + 8, 0));
     if (!ok) {
       atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
       flags[0] = 1;
@@ -311,7 +332,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     for (int m = t.m0; ok && m < t.m1; ++m) {
       const int k = m - t.m0 + 1;
       const int s = k % NS, s1 = (k + 1) % NS;
-      if (!mbar_wait(full0 + 8 * s1, ((k + 1) / NS) & 1)) {
+      if (!__all_sync(0xffffffffu, mbar_wait(full0 + 8 * s1, ((k + 1) / NS) & 1))) {
         atomicOr(dev_err, IGG_DEV_ERR_TIMEOUT);
         flags[0] = 1;
         ok = false;
@@ -335,6 +356,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
         C right = __shfl_down_sync(0xffffffffu, c.v[0], 1, LPR);
         if (sl == 0) left = Num<S>::cv(row[-1]);
         if (sl == LPR - 1) right = Num<S>::cv(row[V]);
+        unsigned deferred = 0u;  // bit i: point i left to the fix-up
         if (comp[j]) {
           Vec<S> out;
           // (up, dn) are the row pair, (zm, zp) the march pair
@@ -346,21 +368,35 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
           if (full_vec && okm == (1u << V) - 1u) {
             *reinterpret_cast<uint4 *>(dst) = pack(out);
           } else {
-            unsigned deferred = 0u;  // bit i: point i left to the fix-up
 #pragma unroll
             for (int i = 0; i < V; ++i) {
               const bool in = xs + i >= t.xb && xs + i < t.xe;
               if (in && (okm >> i & 1u)) Num<S>::st(dst + i, out.v[i]);
               if (in && !(okm >> i & 1u)) deferred |= 1u << i;
             }
-            // mark the points in the tile's mask of this row and plane, and
-            // the tile as marked
-            if (is_emu(MODE) && deferred) {
-              constexpr int PT = Sh::H * kMaxTmaMarch * 2;
-              const int xi = sl * V;  // point index in the row, V divides 32
-              const size_t wi = ((size_t)r * kMaxTmaMarch + (m - t.m0)) * 2 + (xi >> 5);
-              if (atomicOr(fix + (size_t)blockIdx.x * PT + wi, deferred << (xi & 31)) == 0u)
-                fix[(size_t)gridDim.x * PT + blockIdx.x] = 1u;
+          }
+        }
+        if constexpr (is_emu(MODE)) {
+          // The warp owns the whole row (one row per warp, two points per
+          // lane): it writes the row's point masks for this plane and lists
+          // the nonzero ones for the fix-up.
+          static_assert(LPR == 32 && V == 2, "one FP64 row per warp");
+          if (__any_sync(0xffffffffu, deferred != 0u)) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, deferred & 1u);
+            const unsigned b1 = __ballot_sync(0xffffffffu, deferred & 2u);
+            if (lane < 2) {
+              // points 32*lane .. 32*lane + 31: lanes 16*lane .. 16*lane + 15
+              const unsigned h0 = (b0 >> (16 * lane)) & 0xFFFFu, h1 = (b1 >> (16 * lane)) & 0xFFFFu;
+              const unsigned word = spread16(h0) | (spread16(h1) << 1);
+              if (word) {
+                constexpr int PT = Sh::H * kMaxTmaMarch * 2;
+                const unsigned wi = blockIdx.x * PT +
+                                    ((unsigned)r * kMaxTmaMarch + (unsigned)(m - t.m0)) * 2 +
+                                    (unsigned)lane;
+                fix[wi] = word;
+                const FixList fl = fix_list(fix, gridDim.x, PT);
+                fl.words[atomicAdd(fl.count, 1u)] = wi;
+              }
             }
           }
         }
@@ -386,10 +422,10 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 
 // Fix-up of an emulated-cell launch: the points left by the kernel get the
 // FP64 cell (the same choice and the same arithmetic as cell() everywhere
-// else). One block per tile; a tile without marks exits at once. Otherwise
-// the block's threads take the tile's point-mask words in turn (two words of
-// 32 points per row and plane, FP64 tiles being 64 points wide), clear the
-// nonzero ones and update their points.
+// else). The kernel wrote and listed every nonzero mask word (fix_list); the
+// fix-up's warps take the listed words in turn, lane l updating point l of
+// the word's 32 when its bit is set. The last block to finish resets the
+// list.
 template <bool SWAP>
 __global__ void __launch_bounds__(256)
     k_fixup_f64(const TmaTile *__restrict__ tiles, int ntiles, unsigned *__restrict__ fix,
@@ -398,29 +434,32 @@ __global__ void __launch_bounds__(256)
   using Sh = TmaShape<double, WideShape<double>::LPR, WideShape<double>::H>;
   static_assert(Sh::W == 64, "fix-up layout: two mask words per row and plane");
   constexpr int PT = Sh::H * kMaxTmaMarch * 2;  // mask words of one tile
-  unsigned *flag = fix + (size_t)ntiles * PT + blockIdx.x;
-  if (*flag == 0u) return;
-  __syncthreads();  // every thread has read the flag
-  if (threadIdx.x == 0) *flag = 0u;
-  const TmaTile t = tiles[blockIdx.x];
+  const FixList fl = fix_list(fix, ntiles, PT);
+  const unsigned count = *(volatile unsigned *)fl.count;
   const W<double> w = make_w(c0, 0.0);
   const long long sy = nx, sz = (long long)nx * ny;
   const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
-  const int planes = t.m1 - t.m0, per_row = 2 * planes;
-  unsigned *tw = fix + (size_t)blockIdx.x * PT;
-  for (int i = threadIdx.x; i < Sh::H * per_row; i += blockDim.x) {
-    const int row = i / per_row, mi = (i % per_row) >> 1, half = i & 1;
-    unsigned *wp = tw + ((size_t)row * kMaxTmaMarch + mi) * 2 + half;
-    unsigned b = *wp;
-    if (b == 0u) continue;
-    *wp = 0u;
-    const long long prow = t.base + t.x0 + half * 32 + srow * (t.r0 + row) + smarch * (t.m0 + mi);
-    for (; b; b &= b - 1) {
-      const long long p = prow + __ffs(b) - 1;
-      const double tc = __ldg(T + p);
-      const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
-                            __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-      T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+  const int lane = threadIdx.x & 31;
+  const unsigned warps = gridDim.x * (blockDim.x >> 5);
+  for (unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < count; e += warps) {
+    const unsigned wi = fl.words[e];
+    if (!(fix[wi] >> lane & 1u)) continue;
+    const int tile = (int)(wi / PT), rem = (int)(wi % PT);
+    const int row = rem / (2 * kMaxTmaMarch), mi = (rem >> 1) % kMaxTmaMarch, half = rem & 1;
+    const TmaTile t = tiles[tile];
+    const long long p =
+        t.base + t.x0 + half * 32 + lane + srow * (t.r0 + row) + smarch * (t.m0 + mi);
+    const double tc = __ldg(T + p);
+    const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
+                          __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
+    T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(fl.done, 1u) == gridDim.x - 1) {
+      *fl.count = 0u;
+      *fl.done = 0u;
     }
   }
 }
@@ -485,7 +524,7 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
                                                           dev_err, fix);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && is_emu(MODE)) {
-    k_fixup_f64<SWAP><<<ntiles, 256, 0, s>>>(tiles, ntiles, fix, (double *)T2, (const double *)T,
+    k_fixup_f64<SWAP><<<kFixupBlocks, 256, 0, s>>>(tiles, ntiles, fix, (double *)T2, (const double *)T,
                                              (const double *)Ci, nx, ny, c);
     e = cudaGetLastError();
   }
@@ -576,6 +615,11 @@ int tma_tile_rows(igg_dtype dt, int) {
 }
 
 bool tma_available() { return encode_fn() != nullptr; }
+
+size_t tma_fix_words(int ntiles) {
+  const size_t masks = (size_t)ntiles * WideShape<double>::H * kMaxTmaMarch * 2;
+  return 2 * masks + 2;
+}
 
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
   switch (dt) {
