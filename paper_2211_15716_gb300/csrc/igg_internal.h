@@ -127,20 +127,22 @@ bool tma_available();
 // Sets the kernel's shared-memory attribute and returns its resident CTAs per
 // SM; call before launching (and before any stream capture).
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
-// FP64 fields with the emulated cell need `fix`, of tma_fix_words(ntiles)
-// words: per tile, two words of point bits (points 0-31 and 32-63 of the
-// 64-wide row) for each row (tma_tile_rows) and each of kMaxTmaMarch march
-// planes, marking the points left to the FP64 cell, written only where
-// nonzero; then the list of the words written (as many slots as mask words),
-// its length and a block counter, both zero on entry. The fix-up launch that
-// follows the kernel on the same stream updates the listed points and resets
-// the length and the counter.
-constexpr int kMaxTmaMarch = 128;
-size_t tma_fix_words(int ntiles);
+// Fix-up buffer of an FP64 tile set of the TMA kernel (emulated cell): room
+// for cap entries of 16 bytes (one per 32-point row segment with points left
+// to the FP64 cell, so cap = the set's computed points / 32 suffices), then
+// the entry count and a block counter, both zero on entry. The kernel fills
+// it; the fix-up launch that follows on the same stream updates the listed
+// points and resets the count and the counter.
+struct FixBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+size_t tma_fix_cap(const TmaTile *tiles, int ntiles);
+inline size_t tma_fix_bytes(size_t cap) { return cap * 16 + 2 * sizeof(unsigned); }
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               unsigned *fix, cudaStream_t s);
+                               FixBuf fix, cudaStream_t s);
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.

@@ -81,7 +81,7 @@ struct TileSet {
   int n = 0;
   int V = 1;
   int tma = -1;
-  unsigned *fix = nullptr;  // fix-up bits per tile row (FP64 TMA tile sets)
+  FixBuf fix;  // fix-up list (FP64 TMA tile sets)
 };
 
 // The split: boundary set (one launch per tile kind) and inner block.
@@ -306,21 +306,15 @@ int upload_vec(const std::vector<TT> &v, TileSet *out) {
 int upload_tiles(const TileLists &v, int V, TileSet *out, int tma = -1) {
   out->V = V;
   out->tma = tma;
-  out->fix = nullptr;
+  out->fix = FixBuf();
   if (tma >= 0) {
     if (int rc = upload_vec(v.tma, out)) return rc;
-    if (V == 2 && out->n > 0) {  // FP64: marks of the emulated cell's fix-up
-      for (const TmaTile &t : v.tma)
-        if (t.m1 - t.m0 > kMaxTmaMarch)
-          return set_error(IGG_ESTATE, "TMA tile marches %d planes (at most %d)", t.m1 - t.m0,
-                           kMaxTmaMarch);
-      // word indices of the fix-up list are 32-bit
-      if (tma_fix_words(out->n) >= (1ull << 32))
-        return set_error(IGG_EINVAL, "too many TMA tiles (%d) for the fix-up list", out->n);
-      const size_t bytes = tma_fix_words(out->n) * sizeof(unsigned);
-      cudaError_t e = cudaMalloc(&out->fix, bytes);
-      if (e == cudaSuccess) e = cudaMemset(out->fix, 0, bytes);
-      if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fix-up flags)");
+    if (V == 2 && out->n > 0) {  // FP64: list of the emulated cell's fix-up
+      out->fix.cap = tma_fix_cap(v.tma.data(), out->n);
+      const size_t bytes = tma_fix_bytes(out->fix.cap);
+      cudaError_t e = cudaMalloc(&out->fix.p, bytes);
+      if (e == cudaSuccess) e = cudaMemset(out->fix.p, 0, bytes);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(fix-up list)");
     }
     return IGG_OK;
   }
@@ -329,9 +323,9 @@ int upload_tiles(const TileLists &v, int V, TileSet *out, int tma = -1) {
 
 void free_tiles(TileSet &t) {
   cudaFree(t.dev);
-  cudaFree(t.fix);
+  cudaFree(t.fix.p);
   t.dev = nullptr;
-  t.fix = nullptr;
+  t.fix = FixBuf();
 }
 
 }  // namespace

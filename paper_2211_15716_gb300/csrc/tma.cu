@@ -124,13 +124,21 @@ __device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);
 }
 
-// The list part of a tile set's fix-up buffer (layout in igg_internal.h).
-struct FixList {
-  unsigned *words, *count, *done;
+// A tile set's fix-up buffer (layout in igg_internal.h): the entries, then
+// the entry count and a block counter.
+struct FixEntry {
+  long long p;    // index of the first of 32 consecutive points of a row
+  unsigned bits;  // bit l: point p + l left to the fix-up
+  unsigned pad;
 };
-__device__ __forceinline__ FixList fix_list(unsigned *fix, unsigned ntiles, unsigned per_tile) {
-  unsigned *l = fix + (size_t)ntiles * per_tile;
-  return {l, l + (size_t)ntiles * per_tile, l + (size_t)ntiles * per_tile + 1};
+struct FixList {
+  FixEntry *e;
+  unsigned *count, *done;
+};
+__device__ __forceinline__ FixList fix_list(void *fix, size_t cap) {
+  FixEntry *e = reinterpret_cast<FixEntry *>(fix);
+  unsigned *c = reinterpret_cast<unsigned *>(e + cap);
+  return {e, c, c + 1};
 }
 constexpr int kFixupBlocks = 8 * 152;
 
@@ -239,7 +247,7 @@ template <class S, int LPR_, int H_, bool SWAP, int MODE>
 __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
-                  unsigned *__restrict__ dev_err, unsigned *__restrict__ fix) {
+                  unsigned *__restrict__ dev_err, void *__restrict__ fix, size_t fix_cap) {
   using Sh = TmaShape<S, LPR_, H_>;
   using C = typename Num<S>::C;
   constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
@@ -389,13 +397,12 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
               const unsigned h0 = (b0 >> (16 * lane)) & 0xFFFFu, h1 = (b1 >> (16 * lane)) & 0xFFFFu;
               const unsigned word = spread16(h0) | (spread16(h1) << 1);
               if (word) {
-                constexpr int PT = Sh::H * kMaxTmaMarch * 2;
-                const unsigned wi = blockIdx.x * PT +
-                                    ((unsigned)r * kMaxTmaMarch + (unsigned)(m - t.m0)) * 2 +
-                                    (unsigned)lane;
-                fix[wi] = word;
-                const FixList fl = fix_list(fix, gridDim.x, PT);
-                fl.words[atomicAdd(fl.count, 1u)] = wi;
+                const FixList fl = fix_list(fix, fix_cap);
+                const unsigned k = atomicAdd(fl.count, 1u);
+                if (k < fix_cap) {  // always: one entry per segment, plane and row at most
+                  fl.e[k].p = t.base + t.x0 + 32 * lane + srow * (t.r0 + r) + smarch * m;
+                  fl.e[k].bits = word;
+                }
               }
             }
           }
@@ -422,33 +429,23 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 
 // Fix-up of an emulated-cell launch: the points left by the kernel get the
 // FP64 cell (the same choice and the same arithmetic as cell() everywhere
-// else). The kernel wrote and listed every nonzero mask word (fix_list); the
-// fix-up's warps take the listed words in turn, lane l updating point l of
-// the word's 32 when its bit is set. The last block to finish resets the
-// list.
-template <bool SWAP>
+// else). The kernel listed every 32-point row segment with such points; the
+// fix-up's warps take the entries in turn, lane l updating point p + l when
+// bit l is set. The last block to finish resets the list.
 __global__ void __launch_bounds__(256)
-    k_fixup_f64(const TmaTile *__restrict__ tiles, int ntiles, unsigned *__restrict__ fix,
-                double *__restrict__ T2, const double *__restrict__ T,
-                const double *__restrict__ Ci, int nx, int ny, Coef c0) {
-  using Sh = TmaShape<double, WideShape<double>::LPR, WideShape<double>::H>;
-  static_assert(Sh::W == 64, "fix-up layout: two mask words per row and plane");
-  constexpr int PT = Sh::H * kMaxTmaMarch * 2;  // mask words of one tile
-  const FixList fl = fix_list(fix, ntiles, PT);
-  const unsigned count = *(volatile unsigned *)fl.count;
+    k_fixup_f64(void *__restrict__ fix, size_t cap, double *__restrict__ T2,
+                const double *__restrict__ T, const double *__restrict__ Ci, int nx, int ny,
+                Coef c0) {
+  const FixList fl = fix_list(fix, cap);
+  const unsigned count = (unsigned)min((size_t)*(volatile unsigned *)fl.count, cap);
   const W<double> w = make_w(c0, 0.0);
   const long long sy = nx, sz = (long long)nx * ny;
-  const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
   const int lane = threadIdx.x & 31;
   const unsigned warps = gridDim.x * (blockDim.x >> 5);
   for (unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < count; e += warps) {
-    const unsigned wi = fl.words[e];
-    if (!(fix[wi] >> lane & 1u)) continue;
-    const int tile = (int)(wi / PT), rem = (int)(wi % PT);
-    const int row = rem / (2 * kMaxTmaMarch), mi = (rem >> 1) % kMaxTmaMarch, half = rem & 1;
-    const TmaTile t = tiles[tile];
-    const long long p =
-        t.base + t.x0 + half * 32 + lane + srow * (t.r0 + row) + smarch * (t.m0 + mi);
+    const FixEntry en = fl.e[e];
+    if (!(en.bits >> lane & 1u)) continue;
+    const long long p = en.p + lane;
     const double tc = __ldg(T + p);
     const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
                           __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
@@ -511,7 +508,7 @@ cudaError_t prepare_t(int *ctas_per_sm) {
 template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     unsigned *fix, cudaStream_t s) {
+                     FixBuf fix, cudaStream_t s) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
   CUtensorMap mT, mC;
   const bool ok = SWAP ? encode<S>(&mT, T, nx, ny, nzt, Sh::BW, 1, Sh::BH) &&
@@ -521,11 +518,11 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
   if (!ok) return cudaErrorInvalidValue;
   k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>
       <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
-                                                          dev_err, fix);
+                                                          dev_err, fix.p, fix.cap);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && is_emu(MODE)) {
-    k_fixup_f64<SWAP><<<kFixupBlocks, 256, 0, s>>>(tiles, ntiles, fix, (double *)T2, (const double *)T,
-                                             (const double *)Ci, nx, ny, c);
+    k_fixup_f64<<<kFixupBlocks, 256, 0, s>>>(fix.p, fix.cap, (double *)T2, (const double *)T,
+                                            (const double *)Ci, nx, ny, c);
     e = cudaGetLastError();
   }
   return e;
@@ -557,10 +554,10 @@ cudaError_t prepare_v(int variant, int *ctas) {
 template <class S, bool SWAP>
 cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     unsigned *fix, cudaStream_t s) {
+                     FixBuf fix, cudaStream_t s) {
   if constexpr (sizeof(S) == 8) {
     if (c.f64_emu) {
-      if (!fix) return cudaErrorInvalidValue;
+      if (!fix.p) return cudaErrorInvalidValue;
       switch (weight_groups(c.wx, c.wy, c.wz)) {
         case 1:
           return launch_t<S, WideShape<S>, SWAP, emu_mode(1)>(tiles, ntiles, T2, T, Ci, nx, ny,
@@ -584,7 +581,7 @@ cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
 template <class S>
 cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, const void *T,
                      const void *Ci, int nx, int ny, long long nzt, const Coef &c,
-                     unsigned *dev_err, unsigned *fix, cudaStream_t s) {
+                     unsigned *dev_err, FixBuf fix, cudaStream_t s) {
   switch (variant) {
     case TMA_WIDE:
       return launch_m<S, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
@@ -616,9 +613,14 @@ int tma_tile_rows(igg_dtype dt, int) {
 
 bool tma_available() { return encode_fn() != nullptr; }
 
-size_t tma_fix_words(int ntiles) {
-  const size_t masks = (size_t)ntiles * WideShape<double>::H * kMaxTmaMarch * 2;
-  return 2 * masks + 2;
+size_t tma_fix_cap(const TmaTile *tiles, int ntiles) {
+  size_t cap = 0;
+  for (int i = 0; i < ntiles; ++i) {
+    const TmaTile &t = tiles[i];
+    const size_t segs = (size_t)(t.xe - t.x0 + 31) / 32;  // 32-point segments of a row
+    cap += segs * (size_t)(t.re - t.r0) * (size_t)(t.m1 - t.m0);
+  }
+  return cap;
 }
 
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
@@ -633,7 +635,7 @@ cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               unsigned *fix, cudaStream_t s) {
+                               FixBuf fix, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   switch (dt) {
     case IGG_F64:
