@@ -164,14 +164,14 @@ def oracle_baseline(budget_s: float = 12.0):
 
 
 def grid_launches_per_hidden_step(grid, w, dtype="f64", f64_emu=True) -> int:
-    """Kernel launches of one hidden step: the boundary launches (z slabs, y
-    slabs, x ends), three halo dimensions (copies in a dimension without
-    neighbours are skipped) and the inner block.  With the emulated FP64 cell
-    every stencil launch is followed by its fix-up launch."""
+    """Kernel launches of one hidden step: the two boundary launches (z slabs
+    with the x ends, y slabs), three halo dimensions (copies in a dimension
+    without neighbours are skipped) and the inner block.  With the emulated
+    FP64 cell every stencil launch is followed by its fix-up launch."""
     dims, periods = grid.dims, grid.periods
     halo = sum(1 for d in range(3) if dims[d] > 1 or periods[d])
     per_stencil = 2 if (dtype == "f64" and f64_emu) else 1
-    return per_stencil * (3 + 1) + halo
+    return per_stencil * (2 + 1) + halo
 
 
 def run_reference(args, ws, rank):

@@ -458,7 +458,7 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
     const int Ww = tma_tile_width(d, TMA_WIDE), Hw = tma_tile_rows(d, TMA_WIDE);
     int xlw = std::min(std::max(xl, (xl + Ww - 1) / Ww * Ww), nx - 1);
     int xhw = std::max(xlw, std::min(xh, std::max(1, ((nx - Ww) / V) * V)));
-    TileLists wz, sy, wx;
+    TileLists wzx, sy;  // z slabs and x ends (one launch), y slabs
     const int zbt_i = choose_zb_tma(tma_xy_tiles(xlw, xhw, yl, yh, V, Ww, Hw) * g->nsub,
                                     zh - zl > 0 ? zh - zl : 1, tma_slots(V));
     const int zbt_x = choose_zb_tma(
@@ -467,16 +467,19 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
         zh - zl > 0 ? zh - zl : 1, tma_slots(V));
     for (int s = 0; s < g->nsub; ++s) {
       const long long base = (long long)s * g->nloc, zoff = (long long)s * nz;
-      add_box_tma(wz.tma, base, zoff, 1, nx - 1, 1, ny - 1, 1, zl, 64, V, Ww, Hw);          // z low
-      add_box_tma(wz.tma, base, zoff, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, V, Ww, Hw);     // z high
+      add_box_tma(wzx.tma, base, zoff, 1, xlw, yl, yh, zl, zh, zbt_x, V, Ww, Hw);          // x low
+      add_box_tma(wzx.tma, base, zoff, xhw, nx - 1, yl, yh, zl, zh, zbt_x, V, Ww, Hw);     // x high
       add_box_tma(sy.tma, base, zoff, 1, nx - 1, zl, zh, 1, yl, 64, V, Ww, Hw);            // y low
       add_box_tma(sy.tma, base, zoff, 1, nx - 1, zl, zh, yh, ny - 1, 64, V, Ww, Hw);       // y high
-      add_box_tma(wx.tma, base, zoff, 1, xlw, yl, yh, zl, zh, zbt_x, V, Ww, Hw);           // x low
-      add_box_tma(wx.tma, base, zoff, xhw, nx - 1, yl, yh, zl, zh, zbt_x, V, Ww, Hw);      // x high
       add_box_tma(vi.tma, base, zoff, xlw, xhw, yl, yh, zl, zh, zbt_i, V, Ww, Hw);         // inner
     }
-    const std::pair<TileLists *, int> parts[3] = {
-        {&wz, TMA_WIDE}, {&sy, TMA_WIDE_SWAP}, {&wx, TMA_WIDE}};
+    // the short z-slab tiles after the long x-end tiles in the same launch
+    for (int s = 0; s < g->nsub; ++s) {
+      const long long base = (long long)s * g->nloc, zoff = (long long)s * nz;
+      add_box_tma(wzx.tma, base, zoff, 1, nx - 1, 1, ny - 1, 1, zl, 64, V, Ww, Hw);         // z low
+      add_box_tma(wzx.tma, base, zoff, 1, nx - 1, 1, ny - 1, zh, nz - 1, 64, V, Ww, Hw);    // z high
+    }
+    const std::pair<TileLists *, int> parts[2] = {{&wzx, TMA_WIDE}, {&sy, TMA_WIDE_SWAP}};
     for (auto &pt : parts) {
       if (pt.first->tma.empty()) continue;
       // each kernel variant needs its shared-memory attribute before launch
