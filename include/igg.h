@@ -144,9 +144,20 @@ int igg_device_status(igg_grid *grid, unsigned *status, int clear);
  *     differences are formed exactly in integers, weighted in float-float
  *     and applied with two FP64 FMAs (per-step error about 2^-44 of
  *     sum_d |w_d D_d| plus two FP64 roundings of T2); other points, and all
- *     points with 0, use the FP64 cell (8 FP64 instructions per point). */
+ *     points with 0, use the FP64 cell (8 FP64 instructions per point).
+ *   IGG_OPT_FUSED_HALO (default 1): igg_step_hidden (and igg_run with
+ *     widths) on TMA kernels with n[d] >= 2*overlap[d] in every dimension fuse
+ *     the halo update into the step instead of splitting it: one launch
+ *     computes every inner point and also stores each point of a sent plane
+ *     into the halo cells that the plane copies would give it (all subdomains
+ *     being in the device's memory, nothing is left to overlap); 0 selects
+ *     the boundary/inner split described at igg_step_hidden. Bit-identical
+ *     results for fields whose halo cells at the global boundary agree
+ *     between neighbouring subdomains (as when every subdomain is set from
+ *     one global field). */
 #define IGG_OPT_TMA 1
 #define IGG_OPT_F64_EMU 2
+#define IGG_OPT_FUSED_HALO 3
 int igg_grid_set_option(igg_grid *grid, int option, int value);
 
 /* ---------------------------------------------------------------------------

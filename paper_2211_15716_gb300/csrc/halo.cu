@@ -10,19 +10,34 @@
 namespace igg {
 namespace {
 
-template <class E>
+// One block per (copy, plane row b): the row's na points at stride sa. VEC:
+// rows contiguous (sa = 1) and 16-byte aligned, copied as 16-byte vectors.
+template <class E, bool VEC>
 __global__ void __launch_bounds__(256)
-    k_halo_planes(const PlaneCopy *__restrict__ copies, E *__restrict__ f, int na,
-                  int nb, long long sa, long long sb) {
-  const PlaneCopy c = copies[blockIdx.y];
-  const long long npts = (long long)na * nb;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npts;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long a = i % na;
-    const long long b = i / na;
-    const long long off = a * sa + b * sb;
-    f[c.dst + off] = f[c.src + off];
+    k_halo_planes(const PlaneCopy *__restrict__ copies, E *__restrict__ f, int na, int nb,
+                  long long sa, long long sb) {
+  const int ci = blockIdx.x / nb, b = blockIdx.x % nb;
+  const PlaneCopy c = copies[ci];
+  const long long rb = (long long)b * sb;
+  if (VEC) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(f + c.src + rb);
+    uint4 *dst = reinterpret_cast<uint4 *>(f + c.dst + rb);
+    const int nv = na * (int)sizeof(E) / 16;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = src[i];
+  } else {
+    for (int a = threadIdx.x; a < na; a += blockDim.x) f[c.dst + rb + a * sa] = f[c.src + rb + a * sa];
   }
+}
+
+template <class E>
+cudaError_t launch_e(const PlaneCopy *copies, int ncopies, void *field, int na, int nb,
+                     long long sa, long long sb, bool vec, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((long long)ncopies * nb);
+  if (vec)
+    k_halo_planes<E, true><<<blocks, 256, 0, s>>>(copies, (E *)field, na, nb, sa, sb);
+  else
+    k_halo_planes<E, false><<<blocks, 256, 0, s>>>(copies, (E *)field, na, nb, sa, sb);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -31,27 +46,18 @@ cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
                         void *field, int na, int nb, long long sa, long long sb,
                         cudaStream_t s) {
   if (ncopies <= 0) return cudaSuccess;
-  const long long npts = (long long)na * nb;
-  long long bx = (npts + 255) / 256;
-  if (bx > 1024) bx = 1024;
-  const dim3 grid((unsigned)bx, (unsigned)ncopies);
+  if ((long long)ncopies * nb >= (1ll << 31)) return cudaErrorInvalidValue;
+  // 16-byte vectors: contiguous rows (sa = 1) of a 16-byte multiple whose
+  // starts are multiples of the row length (the halo tables' plane offsets
+  // are multiples of n_x = na for the y and z planes, and so is sb)
+  const bool vec = sa == 1 && ((long long)na * (long long)elem_size) % 16 == 0 && sb % na == 0 &&
+                   reinterpret_cast<uintptr_t>(field) % 16 == 0;
   switch (elem_size) {
-    case 8:
-      k_halo_planes<unsigned long long><<<grid, 256, 0, s>>>(
-          copies, (unsigned long long *)field, na, nb, sa, sb);
-      break;
-    case 4:
-      k_halo_planes<unsigned int><<<grid, 256, 0, s>>>(copies, (unsigned int *)field,
-                                                       na, nb, sa, sb);
-      break;
-    case 2:
-      k_halo_planes<unsigned short><<<grid, 256, 0, s>>>(
-          copies, (unsigned short *)field, na, nb, sa, sb);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case 8: return launch_e<unsigned long long>(copies, ncopies, field, na, nb, sa, sb, vec, s);
+    case 4: return launch_e<unsigned int>(copies, ncopies, field, na, nb, sa, sb, vec, s);
+    case 2: return launch_e<unsigned short>(copies, ncopies, field, na, nb, sa, sb, vec, s);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace igg

@@ -139,10 +139,21 @@ struct FixBuf {
 };
 size_t tma_fix_cap(const TmaTile *tiles, int ntiles);
 inline size_t tma_fix_bytes(size_t cap) { return cap * 16 + 2 * sizeof(unsigned); }
+// x faces of the halo update fused into the boundary launches of the hidden
+// step (all subdomains share the device's memory): every computed point with
+// x = o_x - 1 (x = n_x - o_x) is also stored into plane n_x - 1 (plane 0) of
+// its left (right) x neighbour, where the x plane copy of Fig. 1's
+// update_halo! would put it; the y and z plane copies follow on the same
+// stream. nbr = NULL: no sends.
+struct HaloSend {
+  const int *nbr = nullptr;  // [nsub][3][2]: left, right neighbour per dimension, -1 none
+  int n[3] = {0, 0, 0}, o[3] = {0, 0, 0};
+  long long nloc = 0;
+};
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               FixBuf fix, cudaStream_t s);
+                               FixBuf fix, const HaloSend &send, cudaStream_t s);
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.

@@ -347,8 +347,10 @@ struct igg_grid {
   int ncopies[3] = {0, 0, 0};
   std::map<GraphKey, cudaGraphExec_t> graphs;
   unsigned *dev_err = nullptr;  // device error word of the pipelined kernels
+  int *nbr = nullptr;           // device copy of left/right per subdomain and dimension
   bool tma_enabled = true;      // TMA kernel for the regular boxes when available
   int f64_emu = 1;              // FP64 fields: emulated FP64 cell (1) or FP64 cell (0)
+  bool fused_halo = true;       // hidden steps: halo update fused into one step launch
 };
 
 namespace {
@@ -521,11 +523,25 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
   return IGG_OK;
 }
 
+// The fused halo sends of a grid (HaloSend).
+HaloSend halo_send(const igg_grid *g) {
+  HaloSend h;
+  h.nbr = g->nbr;
+  for (int d = 0; d < 3; ++d) {
+    h.n[d] = g->n[d];
+    h.o[d] = g->overlap[d];
+  }
+  h.nloc = g->nloc;
+  return h;
+}
+
 cudaError_t launch_tiles(const igg_grid *g, int V, igg_dtype dt, const TileSet &ts, void *T2,
-                         const void *T, const void *Ci, const Coef &c, cudaStream_t s) {
+                         const void *T, const void *Ci, const Coef &c, cudaStream_t s,
+                         const HaloSend &send = HaloSend()) {
   if (ts.tma >= 0)
     return launch_stencil_tma(dt, ts.tma, (const TmaTile *)ts.dev, ts.n, T2, T, Ci, g->n[0],
-                              g->n[1], (long long)g->nsub * g->n[2], c, g->dev_err, ts.fix, s);
+                              g->n[1], (long long)g->nsub * g->n[2], c, g->dev_err, ts.fix, send,
+                              s);
   if (V > 1) return launch_stencil_vec(dt, (const VTile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
   return launch_stencil(dt, (const Tile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
@@ -567,6 +583,17 @@ cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
 
 bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->ncopies[2] > 0; }
 
+// Whether hidden steps fuse the halo update into one TMA step launch: the
+// option, TMA tiles, some halo, and n >= 2 o (a point is sent at most one way
+// per dimension).
+bool use_fused_halo(const igg_grid *g, int V) {
+  if (!g->fused_halo || !use_tma(g, V) || !any_halo(g)) return false;
+  for (int d = 0; d < 3; ++d)
+    if (g->n[d] < 2 * g->overlap[d]) return false;
+  return true;
+}
+
+
 // One step of Fig. 1's loop, queued on s: plain (full step, then halo update
 // of T2 on s) or hidden (boundary set + halo on the high-priority stream,
 // inner block on the low-priority stream, s joins both).
@@ -587,6 +614,14 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
     }
     return IGG_OK;
   }
+  if (with_halo && use_fused_halo(g, V)) {
+    // the hidden step as one launch with the halo update fused into it
+    TileSet *full = nullptr;
+    if (int rc = build_full_tiles(g, V, &full)) return rc;
+    e = launch_tiles(g, V, dt, *full, T2, T, Ci, c, s, halo_send(g));
+    if (e != cudaSuccess) return cuda_error(e, "fused step launch");
+    return IGG_OK;
+  }
   SplitTiles *st = nullptr;
   int rc = build_split_tiles(g, widths, V, &st);
   if (rc != IGG_OK) return rc;
@@ -596,7 +631,7 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   e = cudaSuccess;
   for (const TileSet &b : st->boundary)
     if (e == cudaSuccess) e = launch_tiles(g, V, dt, b, T2, T, Ci, c, g->hi);
-  if (e == cudaSuccess && any_halo(g)) e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
+  if (e == cudaSuccess && with_halo && any_halo(g)) e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
   if (e != cudaSuccess) return cuda_error(e, "boundary/halo launch");
   e = launch_tiles(g, V, dt, st->inner, T2, T, Ci, c, g->lo);
   if (e != cudaSuccess) return cuda_error(e, "inner launch");
@@ -627,6 +662,7 @@ void destroy_grid(igg_grid *g) {
   for (auto &kv : g->full) free_tiles(kv.second);
   for (int d = 0; d < 3; ++d) cudaFree(g->copies[d]);
   cudaFree(g->dev_err);
+  cudaFree(g->nbr);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_hi) cudaEventDestroy(g->ev_hi);
   if (g->ev_lo) cudaEventDestroy(g->ev_lo);
@@ -735,6 +771,18 @@ int igg_init_global_grid(int nx, int ny, int nz, const int dims_in[3], int nsub,
     return cuda_error(e, "device error word");
   }
   int rc = build_halo_tables(g);
+  if (rc == IGG_OK) {
+    std::vector<int> nb(6 * (size_t)g->nsub);
+    for (int q = 0; q < g->nsub; ++q)
+      for (int d = 0; d < 3; ++d) {
+        nb[6 * q + 2 * d] = g->left[3 * q + d];
+        nb[6 * q + 2 * d + 1] = g->right[3 * q + d];
+      }
+    e = cudaMalloc(&g->nbr, nb.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->nbr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_error(e, "neighbour table");
+  }
   if (rc != IGG_OK) {
     destroy_grid(g);
     return rc;
@@ -864,7 +912,7 @@ int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const v
   if (nt >= 2) {
     // tile tables are allocated before the capture starts
     const int V = grid_vec(g, dt);
-    if (widths) {
+    if (widths && !use_fused_halo(g, V)) {
       SplitTiles *st = nullptr;
       if (int rc = build_split_tiles(g, widths, V, &st)) return rc;
     } else {
@@ -1074,14 +1122,15 @@ int igg_device_status(igg_grid *g, unsigned *status, int clear) {
 int igg_grid_set_option(igg_grid *g, int option, int value) {
   clear_error();
   if (int rc = check_grid(g)) return rc;
-  if (option != IGG_OPT_TMA && option != IGG_OPT_F64_EMU)
+  if (option != IGG_OPT_TMA && option != IGG_OPT_F64_EMU && option != IGG_OPT_FUSED_HALO)
     return set_error(IGG_EINVAL, "unknown option %d", option);
   DeviceGuard dg(g->device);
   cudaError_t e1 = cudaStreamSynchronize(g->hi), e2 = cudaStreamSynchronize(g->lo);
   if (e1 != cudaSuccess) return cuda_error(e1, "set_option");
   if (e2 != cudaSuccess) return cuda_error(e2, "set_option");
   if (option == IGG_OPT_TMA) g->tma_enabled = value != 0;
-  else g->f64_emu = value != 0 ? 1 : 0;
+  else if (option == IGG_OPT_F64_EMU) g->f64_emu = value != 0 ? 1 : 0;
+  else g->fused_halo = value != 0;
   // tile tables and graphs depend on the kernel choice
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
   g->graphs.clear();

@@ -58,7 +58,7 @@ struct TmaShape {
   static constexpr int TBA = (TB + 127) / 128 * 128;
   static constexpr int CB = W * H * (int)sizeof(S);     // Ci box bytes
   static constexpr int STAGE = (TBA + CB + 127) / 128 * 128;
-  static constexpr int SMEM = NS * STAGE + 2 * NS * 8 + 64;
+  static constexpr int SMEM = NS * STAGE + 2 * NS * 8 + 64 + 128;  // + flags, send table
   static_assert(H % ROWS_PER_PASS == 0, "rows per tile");
   static_assert(BW <= 256 && BH <= 256, "TMA box dims");
 };
@@ -141,6 +141,106 @@ __device__ __forceinline__ FixList fix_list(void *fix, size_t cap) {
   return {e, c, c + 1};
 }
 constexpr int kFixupBlocks = 8 * 152;
+
+// Halo update fused into the step (HaloSend). A point's send option in
+// dimension d: 0 = none, 1 = to plane n - 1 of the left neighbour
+// (coordinate o - 1), 2 = to plane 0 of the right neighbour (coordinate
+// n - o); fused steps need n >= 2 o, so that at most one option applies.
+__device__ __forceinline__ int send_opt(const HaloSend &h, int d, int c) {
+  return c == h.o[d] - 1 ? 1 : (c == h.n[d] - h.o[d] ? 2 : 0);
+}
+
+// Subdomain reached from sub by the options (ix, iy, iz) taken in the order
+// x, y, z, as the plane copies go; -1 where a neighbour is missing.
+__device__ __forceinline__ int send_sub(const HaloSend &h, int sub, int ix, int iy, int iz) {
+  if (ix && sub >= 0) sub = h.nbr[6 * sub + 0 + ix - 1];
+  if (iy && sub >= 0) sub = h.nbr[6 * sub + 2 + iy - 1];
+  if (iz && sub >= 0) sub = h.nbr[6 * sub + 4 + iz - 1];
+  return sub;
+}
+
+// Stores v, the new value of point (x, y, z) with options (ox, oy, oz), into
+// every halo cell that the plane copies in the order x, y, z give it: for
+// each nonempty subset of its send dimensions, the cell of the subdomain
+// reached through those neighbours with those coordinates replaced.
+// nbc(k): the subdomain reached by the options of index k = ix + 3 iy + 9 iz.
+template <class S, class NB>
+__device__ __forceinline__ void send_value(const HaloSend &h, const NB &nbc, S *T2, int x, int y,
+                                           int z, int ox, int oy, int oz,
+                                           typename Num<S>::C v) {
+  const int x2 = ox == 1 ? h.n[0] - 1 : 0, y2 = oy == 1 ? h.n[1] - 1 : 0,
+            z2 = oz == 1 ? h.n[2] - 1 : 0;
+  const long long sx = 1, sy = h.n[0], sz = (long long)h.n[0] * h.n[1];
+  // a point on one sent plane only (all but the edges and corners): one cell
+  if ((ox != 0) + (oy != 0) + (oz != 0) == 1) {
+    const int sd = nbc(ox + 3 * oy + 9 * oz);
+    if (sd >= 0)
+      Num<S>::st(T2 + (long long)sd * h.nloc + sx * (ox ? x2 : x) + sy * (oy ? y2 : y) +
+                     sz * (oz ? z2 : z),
+                 v);
+    return;
+  }
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    if (((k & 1) && !ox) || ((k & 2) && !oy) || ((k & 4) && !oz)) continue;
+    const int sd = nbc(((k & 1) ? ox : 0) + 3 * ((k & 2) ? oy : 0) + 9 * ((k & 4) ? oz : 0));
+    if (sd < 0) continue;
+    Num<S>::st(T2 + (long long)sd * h.nloc + sx * ((k & 1) ? x2 : x) + sy * ((k & 2) ? y2 : y) +
+                   sz * ((k & 4) ? z2 : z),
+               v);
+  }
+}
+
+// The halo sends of one tile, after its points are stored (the block's
+// stores are visible to it after a barrier): its points on sent planes are
+// read back from T2 and stored to their halo cells. Points left to the
+// fix-up send stale values here; the fix-up sends them again afterwards.
+// Three disjoint groups: points on a sent march plane, the other points on
+// a sent row, the other points on a sent x column.
+template <class S, bool SWAP>
+__device__ __noinline__ void send_tile(const HaloSend &h, const int *nbc, const TmaTile &t,
+                                       S *T2) {
+  const int dr = SWAP ? 2 : 1, dm = SWAP ? 1 : 2;  // dimensions of rows and march
+  const long long sx = 1, sy = h.n[0], sz = (long long)h.n[0] * h.n[1];
+  const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
+  const int nxr = t.xe - t.xb, nr = t.re - t.r0;
+  const auto nb = [nbc](int k) { return nbc[k]; };
+  auto one = [&](int x, int r, int m) {
+    const int y = SWAP ? m : r, z = SWAP ? r : m;
+    const int ox = send_opt(h, 0, x), oy = send_opt(h, 1, y), oz = send_opt(h, 2, z);
+    const S *p = T2 + t.base + sx * x + sy * y + sz * z;
+    send_value<S>(h, nb, T2, x, y, z, ox, oy, oz, Num<S>::cv(*(volatile const S *)p));
+  };
+  const int mp[2] = {h.o[dm] - 1, h.n[dm] - h.o[dm]};  // sent march planes
+  const int rp[2] = {h.o[dr] - 1, h.n[dr] - h.o[dr]};  // sent rows
+  const int xp[2] = {h.o[0] - 1, h.n[0] - h.o[0]};     // sent x columns
+  for (int q = 0; q < 2; ++q) {
+    const int m = mp[q];
+    if (m < t.m0 || m >= t.m1) continue;
+    for (int i = threadIdx.x; i < nxr * nr; i += blockDim.x) one(t.xb + i % nxr, t.r0 + i / nxr, m);
+  }
+  const int nm = t.m1 - t.m0;
+  for (int q = 0; q < 2; ++q) {
+    const int r = rp[q];
+    if (r < t.r0 || r >= t.re) continue;
+    for (int i = threadIdx.x; i < nxr * nm; i += blockDim.x) {
+      const int m = t.m0 + i / nxr;
+      if (m == mp[0] || m == mp[1]) continue;
+      one(t.xb + i % nxr, r, m);
+    }
+  }
+  for (int q = 0; q < 2; ++q) {
+    const int x = xp[q];
+    if (x < t.xb || x >= t.xe) continue;
+    for (int i = threadIdx.x; i < nr * nm; i += blockDim.x) {
+      const int r = t.r0 + i % nr, m = t.m0 + i / nr;
+      if (m == mp[0] || m == mp[1] || r == rp[0] || r == rp[1]) continue;
+      one(x, r, m);
+    }
+  }
+  (void)srow;
+  (void)smarch;
+}
 
 // bit i of x (i < 16) to bit 2i
 __device__ __forceinline__ unsigned spread16(unsigned x) {
@@ -243,11 +343,12 @@ __device__ __forceinline__ void compute_vec<double, MODE_EMU + 2>(
 // rows along z, march along y (box {BW, 1, BH}), for boxes thin in y. The
 // cell arithmetic gets the y and z neighbour pairs in their own slots either
 // way, so both orientations give the same bits.
-template <class S, int LPR_, int H_, bool SWAP, int MODE>
+template <class S, int LPR_, int H_, bool SWAP, int MODE, bool SEND>
 __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
-                  unsigned *__restrict__ dev_err, void *__restrict__ fix, size_t fix_cap) {
+                  unsigned *__restrict__ dev_err, void *__restrict__ fix, size_t fix_cap,
+                  const HaloSend send) {
   using Sh = TmaShape<S, LPR_, H_>;
   using C = typename Num<S>::C;
   constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
@@ -260,6 +361,12 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 
   const TmaTile t = tiles[blockIdx.x];
   const int K = (t.m1 - t.m0) + 2;
+  // SEND: the subdomains reached by each combination of send options
+  int *nbc = reinterpret_cast<int *>(smem + NS * Sh::STAGE + 2 * NS * 8 + 64);
+  if (SEND && threadIdx.x < 27) {
+    const int k = threadIdx.x;
+    nbc[k] = send_sub(send, (int)(t.base / send.nloc), k % 3, (k / 3) % 3, k / 9);
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -314,6 +421,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       comp[j] = (t.r0 + rowi[j] < t.re) && xs + V > t.xb && xs < t.xe;
     }
     const bool full_vec = xs >= t.xb && xs + V <= t.xe;
+
     const long long sy = nx, sz = (long long)nx * ny;
     const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
     Vec<S> zm[Sh::RPT];
@@ -415,6 +523,9 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     if (warp == 0 && lane == 0) flags[2] = consumed;
   }
   __syncthreads();
+  if constexpr (SEND) {
+    if (!flags[0]) send_tile<S, SWAP>(send, nbc, t, T2);
+  }
   // After an abort, wait (bounded) for copies issued but never consumed, so
   // that no bulk copy writes into this CTA's shared memory after it exits.
   if (threadIdx.x == 0 && flags[0]) {
@@ -435,7 +546,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 __global__ void __launch_bounds__(256)
     k_fixup_f64(void *__restrict__ fix, size_t cap, double *__restrict__ T2,
                 const double *__restrict__ T, const double *__restrict__ Ci, int nx, int ny,
-                Coef c0) {
+                Coef c0, const HaloSend send) {
   const FixList fl = fix_list(fix, cap);
   const unsigned count = (unsigned)min((size_t)*(volatile unsigned *)fl.count, cap);
   const W<double> w = make_w(c0, 0.0);
@@ -449,7 +560,20 @@ __global__ void __launch_bounds__(256)
     const double tc = __ldg(T + p);
     const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
                           __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-    T2[p] = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+    const double v = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+    T2[p] = v;
+    if (send.nbr) {
+      const int sub = (int)(p / send.nloc);
+      const long long q = p % send.nloc;
+      const int x = (int)(q % nx), y = (int)((q / nx) % ny), z = (int)(q / sz);
+      const int ox = send_opt(send, 0, x), oy = send_opt(send, 1, y), oz = send_opt(send, 2, z);
+      if (ox | oy | oz) {
+        const auto nb = [&send, sub](int k) {
+          return send_sub(send, sub, k % 3, (k / 3) % 3, k / 9);
+        };
+        send_value<double>(send, nb, T2, x, y, z, ox, oy, oz, v);
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -497,8 +621,11 @@ bool encode(CUtensorMap *m, const void *base, int nx, int ny, long long nzt, int
 template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t prepare_t(int *ctas_per_sm) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
-  auto kern = k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>;
+  auto kern = k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   if (e == cudaSuccess && ctas_per_sm)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, 32 * (Sh::CONSUMERS + 1),
                                                       Sh::SMEM);
@@ -508,7 +635,7 @@ cudaError_t prepare_t(int *ctas_per_sm) {
 template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     FixBuf fix, cudaStream_t s) {
+                     FixBuf fix, const HaloSend &send, cudaStream_t s) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
   CUtensorMap mT, mC;
   const bool ok = SWAP ? encode<S>(&mT, T, nx, ny, nzt, Sh::BW, 1, Sh::BH) &&
@@ -516,13 +643,18 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
                        : encode<S>(&mT, T, nx, ny, nzt, Sh::BW, Sh::BH, 1) &&
                              encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, Sh::H, 1);
   if (!ok) return cudaErrorInvalidValue;
-  k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>
-      <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
-                                                          dev_err, fix.p, fix.cap);
+  if (send.nbr)
+    k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, true>
+        <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
+                                                            dev_err, fix.p, fix.cap, send);
+  else
+    k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, false>
+        <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
+                                                            dev_err, fix.p, fix.cap, send);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && is_emu(MODE)) {
     k_fixup_f64<<<kFixupBlocks, 256, 0, s>>>(fix.p, fix.cap, (double *)T2, (const double *)T,
-                                            (const double *)Ci, nx, ny, c);
+                                            (const double *)Ci, nx, ny, c, send);
     e = cudaGetLastError();
   }
   return e;
@@ -554,39 +686,39 @@ cudaError_t prepare_v(int variant, int *ctas) {
 template <class S, bool SWAP>
 cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     FixBuf fix, cudaStream_t s) {
+                     FixBuf fix, const HaloSend &send, cudaStream_t s) {
   if constexpr (sizeof(S) == 8) {
     if (c.f64_emu) {
       if (!fix.p) return cudaErrorInvalidValue;
       switch (weight_groups(c.wx, c.wy, c.wz)) {
         case 1:
           return launch_t<S, WideShape<S>, SWAP, emu_mode(1)>(tiles, ntiles, T2, T, Ci, nx, ny,
-                                                              nzt, c, dev_err, fix, s);
+                                                              nzt, c, dev_err, fix, send, s);
         case 2:
           return launch_t<S, WideShape<S>, SWAP, emu_mode(2)>(tiles, ntiles, T2, T, Ci, nx, ny,
-                                                              nzt, c, dev_err, fix, s);
+                                                              nzt, c, dev_err, fix, send, s);
         default:
           return launch_t<S, WideShape<S>, SWAP, emu_mode(3)>(tiles, ntiles, T2, T, Ci, nx, ny,
-                                                              nzt, c, dev_err, fix, s);
+                                                              nzt, c, dev_err, fix, send, s);
       }
     }
     return launch_t<S, WideShape<S>, SWAP, MODE_F64>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
-                                                     dev_err, fix, s);
+                                                     dev_err, fix, send, s);
   } else {
     return launch_t<S, WideShape<S>, SWAP, MODE_CELL>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
-                                                      dev_err, fix, s);
+                                                      dev_err, fix, send, s);
   }
 }
 
 template <class S>
 cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, const void *T,
                      const void *Ci, int nx, int ny, long long nzt, const Coef &c,
-                     unsigned *dev_err, FixBuf fix, cudaStream_t s) {
+                     unsigned *dev_err, FixBuf fix, const HaloSend &send, cudaStream_t s) {
   switch (variant) {
     case TMA_WIDE:
-      return launch_m<S, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
+      return launch_m<S, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, send, s);
     case TMA_WIDE_SWAP:
-      return launch_m<S, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
+      return launch_m<S, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, send, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -635,16 +767,18 @@ cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               FixBuf fix, cudaStream_t s) {
+                               FixBuf fix, const HaloSend &send, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   switch (dt) {
     case IGG_F64:
-      return launch_v<double>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
+      return launch_v<double>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix,
+                              send, s);
     case IGG_F32:
-      return launch_v<float>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
+      return launch_v<float>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix,
+                             send, s);
     case IGG_BF16:
       return launch_v<__nv_bfloat16>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err,
-                                     fix, s);
+                                     fix, send, s);
   }
   return cudaErrorInvalidValue;
 }

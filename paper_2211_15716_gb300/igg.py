@@ -183,6 +183,7 @@ class Grid:
 
     OPT_TMA = 1
     OPT_F64_EMU = 2
+    OPT_FUSED_HALO = 3
 
     def set_option(self, option: int, value: int):
         """igg_grid_set_option (OPT_TMA: 1 = TMA kernel for regular boxes)."""
