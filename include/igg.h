@@ -208,10 +208,12 @@ int igg_run(igg_grid *grid, int nt, const int widths[3], void *T, void *T2,
  * dx, dy, dz), advanced together by ONE persistent kernel launch per step.
  *
  * Layout: every field of the batch is one device buffer; problem b is an
- * array [nz_b][ny_b][nx_b] (x fastest) starting at element offset
- * offsets[b] (igg_batch_layout), each offset a multiple of 256 bytes; the
- * buffer holds `total` elements of the dtype. Gaps between problems are never
- * read or written.
+ * array [nz_b][ny_b][pitch_b] (x fastest; rows padded to pitch_b >= nx_b
+ * elements, pitch_b * element size a multiple of 16 bytes, igg_batch_pitches)
+ * starting at element offset offsets[b] (igg_batch_layout), each offset a
+ * multiple of 256 bytes; point (x, y, z) of problem b is element
+ * offsets[b] + x + pitch_b*(y + ny_b*z). The buffer holds `total` elements of
+ * the dtype. Row padding and gaps between problems are never written.
  * ------------------------------------------------------------------------- */
 
 /* sizes: nprob triples (nx, ny, nz), each >= 3. Creates the tile table with
@@ -226,16 +228,21 @@ int igg_batch_destroy(igg_batch *batch);
 int igg_batch_layout(const igg_batch *batch, long long *offsets,
                      long long *total);
 
+/* pitches[nprob]: the row pitch of each problem in elements. */
+int igg_batch_pitches(const igg_batch *batch, int *pitches);
+
 /* Per-problem coefficients from host arrays of nprob doubles each; required
  * before the first step. */
 int igg_batch_set_coefs(igg_batch *batch, const double *lam, const double *dt,
                         const double *dx, const double *dy, const double *dz);
 
-/* Tiling: variant 0 = 32x8, 1 = 32x4, 2 = 64x4 columns per tile; zb = z
- * planes per tile (0 = the whole problem depth); ctas_per_sm = CTAs of the
- * persistent grid per SM (0 = as many as are resident; more than resident
- * gives IGG_EINVAL). The arithmetic does not depend on the tiling: every
- * tiling gives the same bits. */
+/* Kernel and tiling: variant 3 (the default) = the 16-byte vector kernel,
+ * one CTA per tile of 8 warps of row segments (ctas_per_sm must be 0);
+ * variants 0, 1, 2 = the persistent scalar kernel with 32x8, 32x4, 64x4
+ * columns per tile and ctas_per_sm CTAs per SM (0 = as many as are
+ * resident; more than resident gives IGG_EINVAL). zb = z planes per tile (0 =
+ * the whole problem depth). The arithmetic does not depend on the kernel or
+ * the tiling: every configuration gives the same bits. */
 int igg_batch_configure(igg_batch *batch, int variant, int zb, int ctas_per_sm);
 
 /* Current tiling {variant, zb, ctas_per_sm} and the number of tiles. */

@@ -5,9 +5,14 @@
 // caller's data.
 //
 // Layout: all problems of a field share one device buffer; problem b is an
-// array [nz_b][ny_b][nx_b] (x fastest) starting at element offset off[b],
-// every offset aligned to 256 bytes. Each problem has its own lam, dt, dx,
-// dy, dz (coefficient table on the device).
+// array [nz_b][ny_b][pitch_b] (x fastest, rows padded to pitch_b >= nx_b
+// elements, a multiple of 16 bytes) starting at element offset off[b], every
+// offset aligned to 256 bytes. Each problem has its own lam, dt, dx, dy, dz
+// (coefficient table on the device).
+//
+// Kernels: variant 3 (default) launches the register-pipelined 16-byte
+// vector kernel, one CTA per tile of rows; variants 0-2 the persistent
+// scalar kernel with 32x8, 32x4 or 64x4 column tiles.
 #include <algorithm>
 #include <array>
 #include <cstring>
@@ -21,6 +26,9 @@ using namespace igg;
 
 namespace {
 
+// the vector-kernel variant (one CTA per tile); below it the persistent ones
+constexpr int kBatchVector = kPersistentVariants;
+
 // CTAs per SM of each persistent variant for this dtype (occupancy query).
 int max_ctas_per_sm(igg_dtype dt, int variant);
 
@@ -32,12 +40,14 @@ struct igg_batch {
   int device = 0;
   int sm_count = 0;
   std::vector<std::array<int, 3>> sizes;
+  std::vector<int> pitch;  // row pitch of each problem (elements)
   std::vector<long long> offsets;
   long long total = 0;
   Coef *coef = nullptr;
   bool have_coef = false;
-  int variant = 0, zb = 32, ctas_per_sm = 0;
-  Tile *tiles = nullptr;
+  int variant = kBatchVector, zb = 32, ctas_per_sm = 0;
+  Tile *tiles = nullptr;    // variants 0-2
+  VTile *vtiles = nullptr;  // variant 3
   int ntiles = 0;
   cudaStream_t cap = nullptr;
   std::map<std::tuple<const void *, const void *, const void *>, cudaGraphExec_t> graphs;
@@ -51,38 +61,56 @@ void drop_graphs(igg_batch *b) {
 }
 
 int build_tiles(igg_batch *b) {
-  int tx = 32, ty = 8;
-  persistent_tile_shape(b->variant, &tx, &ty);
-  std::vector<Tile> v;
-  for (int p = 0; p < b->nprob; ++p) {
-    const int nx = b->sizes[p][0], ny = b->sizes[p][1], nz = b->sizes[p][2];
-    const int zb = b->zb > 0 ? b->zb : nz - 2;
-    for (int z = 1; z < nz - 1; z += zb)
-      for (int y = 1; y < ny - 1; y += ty)
-        for (int x = 1; x < nx - 1; x += tx) {
-          Tile t;
-          t.base = b->offsets[p];
-          t.nx = nx;
-          t.ny = ny;
-          t.x0 = x;
-          t.y0 = y;
-          t.xe = nx - 1;
-          t.ye = ny - 1;
-          t.z0 = z;
-          t.z1 = std::min(z + zb, nz - 1);
-          t.param = p;
-          t.xb = x;
-          v.push_back(t);
-        }
-  }
   cudaFree(b->tiles);
+  cudaFree(b->vtiles);
   b->tiles = nullptr;
-  b->ntiles = (int)v.size();
-  cudaError_t e = cudaMalloc(&b->tiles, v.size() * sizeof(Tile));
-  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(batch tiles)");
-  e = cudaMemcpy(b->tiles, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(batch tiles)");
+  b->vtiles = nullptr;
+  b->ntiles = 0;
   drop_graphs(b);
+  cudaError_t e = cudaSuccess;
+  if (b->variant == kBatchVector) {
+    const int V = vec_width(b->dtype);
+    std::vector<VTile> v;
+    for (int p = 0; p < b->nprob; ++p) {
+      const int nx = b->sizes[p][0], ny = b->sizes[p][1], nz = b->sizes[p][2];
+      add_box_vec_pitched(v, b->offsets[p], nx, b->pitch[p], ny, 1, nx - 1, 1, ny - 1, 1, nz - 1,
+                          b->zb > 0 ? b->zb : nz - 2, p, V);
+    }
+    b->ntiles = (int)v.size();
+    e = cudaMalloc(&b->vtiles, v.size() * sizeof(VTile));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->vtiles, v.data(), v.size() * sizeof(VTile), cudaMemcpyHostToDevice);
+  } else {
+    int tx = 32, ty = 8;
+    persistent_tile_shape(b->variant, &tx, &ty);
+    std::vector<Tile> v;
+    for (int p = 0; p < b->nprob; ++p) {
+      const int nx = b->sizes[p][0], ny = b->sizes[p][1], nz = b->sizes[p][2];
+      const int zb = b->zb > 0 ? b->zb : nz - 2;
+      for (int z = 1; z < nz - 1; z += zb)
+        for (int y = 1; y < ny - 1; y += ty)
+          for (int x = 1; x < nx - 1; x += tx) {
+            Tile t;
+            t.base = b->offsets[p];
+            t.nx = b->pitch[p];  // row stride
+            t.ny = ny;
+            t.x0 = x;
+            t.y0 = y;
+            t.xe = nx - 1;
+            t.ye = ny - 1;
+            t.z0 = z;
+            t.z1 = std::min(z + zb, nz - 1);
+            t.param = p;
+            t.xb = x;
+            v.push_back(t);
+          }
+    }
+    b->ntiles = (int)v.size();
+    e = cudaMalloc(&b->tiles, v.size() * sizeof(Tile));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->tiles, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "batch tile table");
   return IGG_OK;
 }
 
@@ -97,9 +125,14 @@ int check_fields(const igg_batch *b, const void *T2, const void *T, const void *
 }
 
 int enqueue(igg_batch *b, void *T2, const void *T, const void *Ci, cudaStream_t s) {
-  const int nctas = b->sm_count * b->ctas_per_sm;
-  cudaError_t e = launch_stencil_persistent(b->dtype, b->variant, b->tiles, b->ntiles, nctas, T2,
-                                            T, Ci, b->coef, s);
+  cudaError_t e;
+  if (b->variant == kBatchVector) {
+    e = launch_stencil_vec(b->dtype, b->vtiles, b->ntiles, T2, T, Ci, Coef(), b->coef, s);
+  } else {
+    const int nctas = b->sm_count * b->ctas_per_sm;
+    e = launch_stencil_persistent(b->dtype, b->variant, b->tiles, b->ntiles, nctas, T2, T, Ci,
+                                  b->coef, s);
+  }
   if (e != cudaSuccess) return cuda_error(e, "batched stencil launch");
   return IGG_OK;
 }
@@ -130,6 +163,7 @@ int igg_batch_create(int nprob, const int *sizes, igg_dtype dt, igg_batch **out)
   b->nprob = nprob;
   b->dtype = dt;
   const long long align = 256 / (long long)dtype_size(dt);
+  const int V = vec_width(dt);
   long long off = 0;
   for (int p = 0; p < nprob; ++p) {
     std::array<int, 3> n = {sizes[3 * p], sizes[3 * p + 1], sizes[3 * p + 2]};
@@ -139,8 +173,9 @@ int igg_batch_create(int nprob, const int *sizes, igg_dtype dt, igg_batch **out)
         return set_error(IGG_EINVAL, "problem %d: size %d < 3 in dim %d", p, n[d], d);
       }
     b->sizes.push_back(n);
+    b->pitch.push_back((n[0] + V - 1) / V * V);
     b->offsets.push_back(off);
-    off += (long long)n[0] * n[1] * n[2];
+    off += (long long)b->pitch.back() * n[1] * n[2];
     off = (off + align - 1) / align * align;
   }
   b->total = off;
@@ -153,7 +188,7 @@ int igg_batch_create(int nprob, const int *sizes, igg_dtype dt, igg_batch **out)
     delete b;
     return cuda_error(e, "batch set-up");
   }
-  b->ctas_per_sm = max_ctas_per_sm(dt, 0);
+  b->ctas_per_sm = 0;
   if (int rc = build_tiles(b)) {
     cudaFree(b->coef);
     cudaStreamDestroy(b->cap);
@@ -171,6 +206,7 @@ int igg_batch_destroy(igg_batch *b) {
   cudaError_t e = cudaStreamSynchronize(b->cap);
   drop_graphs(b);
   cudaFree(b->tiles);
+  cudaFree(b->vtiles);
   cudaFree(b->coef);
   cudaStreamDestroy(b->cap);
   delete b;
@@ -183,6 +219,14 @@ int igg_batch_layout(const igg_batch *b, long long *offsets, long long *total) {
   if (!b) return set_error(IGG_EINVAL, "batch is NULL");
   if (offsets) std::memcpy(offsets, b->offsets.data(), b->nprob * sizeof(long long));
   if (total) *total = b->total;
+  return IGG_OK;
+}
+
+int igg_batch_pitches(const igg_batch *b, int *pitches) {
+  clear_error();
+  if (!b) return set_error(IGG_EINVAL, "batch is NULL");
+  if (!pitches) return set_error(IGG_EINVAL, "pitches is NULL");
+  std::memcpy(pitches, b->pitch.data(), b->nprob * sizeof(int));
   return IGG_OK;
 }
 
@@ -208,14 +252,20 @@ int igg_batch_set_coefs(igg_batch *b, const double *lam, const double *dt, const
 int igg_batch_configure(igg_batch *b, int variant, int zb, int ctas_per_sm) {
   clear_error();
   if (!b) return set_error(IGG_EINVAL, "batch is NULL");
-  if (variant < 0 || variant >= kPersistentVariants)
-    return set_error(IGG_EINVAL, "variant %d outside [0, %d)", variant, kPersistentVariants);
+  if (variant < 0 || variant > kBatchVector)
+    return set_error(IGG_EINVAL, "variant %d outside [0, %d]", variant, kBatchVector);
   if (zb < 0) return set_error(IGG_EINVAL, "zb < 0");
   DevGuard g(b->device);
-  const int cmax = max_ctas_per_sm(b->dtype, variant);
-  if (ctas_per_sm <= 0) ctas_per_sm = cmax;
-  if (ctas_per_sm > cmax)
-    return set_error(IGG_EINVAL, "ctas_per_sm %d above the resident maximum %d", ctas_per_sm, cmax);
+  if (variant == kBatchVector) {
+    if (ctas_per_sm != 0)
+      return set_error(IGG_EINVAL, "ctas_per_sm must be 0 for the vector variant (one CTA per tile)");
+  } else {
+    const int cmax = max_ctas_per_sm(b->dtype, variant);
+    if (ctas_per_sm <= 0) ctas_per_sm = cmax;
+    if (ctas_per_sm > cmax)
+      return set_error(IGG_EINVAL, "ctas_per_sm %d above the resident maximum %d", ctas_per_sm,
+                       cmax);
+  }
   b->variant = variant;
   b->zb = zb;
   b->ctas_per_sm = ctas_per_sm;
@@ -302,8 +352,9 @@ int igg_batch_autotune(igg_batch *b, void *T2, const void *T, const void *Ci, in
   float best = 1e30f;
   int bv = b->variant, bz = b->zb, bc = b->ctas_per_sm;
   int rc = IGG_OK;
-  for (int v = 0; v < kPersistentVariants && rc == IGG_OK; ++v) {
-    const int cmax = max_ctas_per_sm(b->dtype, v);
+  for (int v = 0; v <= kBatchVector && rc == IGG_OK; ++v) {
+    const bool vec = v == kBatchVector;
+    const int cmax = vec ? 0 : max_ctas_per_sm(b->dtype, v);
     const int cands[2] = {cmax, std::max(1, cmax / 2)};
     for (int zb : zbs) {
       for (int ci = 0; ci < (cmax > 1 ? 2 : 1); ++ci) {

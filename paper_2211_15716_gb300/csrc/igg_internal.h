@@ -3,8 +3,9 @@
 
 #include <cuda_runtime.h>
 
-#include <cstdint>
 #include <cstdarg>
+#include <cstdint>
+#include <vector>
 
 #include "../../include/igg.h"
 
@@ -89,6 +90,11 @@ struct VTile {
 };
 static_assert(sizeof(VTile) == 64, "VTile layout");
 constexpr int kVecWarps = 8;
+// Vector-kernel tiles of the box [x0,x1) x [y0,y1) x [z0,z1) of one array
+// [nz][ny][pitch] (rows of pitch >= nx elements, 16-byte aligned) at element
+// offset base; zb planes per tile, coefficient-table row param.
+void add_box_vec_pitched(std::vector<VTile> &v, long long base, int nx, int pitch, int ny, int x0,
+                         int x1, int y0, int y1, int z0, int z1, int zb, int param, int V);
 int vec_width(igg_dtype dt);  // V
 cudaError_t launch_stencil_vec(igg_dtype dt, const VTile *tiles, int ntiles, void *T2,
                                const void *T, const void *Ci, const Coef &c,

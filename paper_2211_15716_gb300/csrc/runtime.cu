@@ -173,14 +173,16 @@ void add_box(std::vector<Tile> &v, long long base, int nx, int ny, int x0, int x
 // in y (fewer than kVecWarps rows) and longer in z: then rows run along z and
 // the tiles march along y. A row of a tile is a segment of lpr lanes, the
 // smallest power of two (<= 32) that covers the box's width in vectors.
-void add_box_vec(std::vector<VTile> &v, long long base, int nx, int ny, int x0, int x1, int y0,
-                 int y1, int z0, int z1, int zb, int param, int V) {
+}  // namespace
+
+void add_box_vec_pitched(std::vector<VTile> &v, long long base, int nx, int pitch, int ny, int x0,
+                         int x1, int y0, int y1, int z0, int z1, int zb, int param, int V) {
   if (x0 >= x1 || y0 >= y1 || z0 >= z1) return;
-  const long long sxy = (long long)nx * ny;
+  const long long sxy = (long long)pitch * ny;
   const bool swap = (y1 - y0) < kVecWarps && (z1 - z0) > (y1 - y0);
   const int r0 = swap ? z0 : y0, r1 = swap ? z1 : y1;
   const int m0 = swap ? y0 : z0, m1 = swap ? y1 : z1;
-  const long long sr = swap ? sxy : nx, sm = swap ? nx : sxy;
+  const long long sr = swap ? sxy : pitch, sm = swap ? pitch : sxy;
   const int mb = swap ? (m1 - m0) : zb;
   const int a0 = (x0 / V) * V;
   const int nvec = (x1 - a0 + V - 1) / V;
@@ -209,6 +211,13 @@ void add_box_vec(std::vector<VTile> &v, long long base, int nx, int ny, int x0, 
         t.swap = swap ? 1 : 0;
         v.push_back(t);
       }
+}
+
+namespace {
+
+void add_box_vec(std::vector<VTile> &v, long long base, int nx, int ny, int x0, int x1, int y0,
+                 int y1, int z0, int z1, int zb, int param, int V) {
+  add_box_vec_pitched(v, base, nx, nx, ny, x0, x1, y0, y1, z0, z1, zb, param, V);
 }
 
 // dtype whose vector width is V (V = 16 / element size)

@@ -287,13 +287,15 @@ def _batch_sigs():
     L.igg_batch_create.argtypes = [I, IP, I, ctypes.POINTER(P)]
     L.igg_batch_destroy.argtypes = [P]
     L.igg_batch_layout.argtypes = [P, LLP, LLP]
+    L.igg_batch_pitches.argtypes = [P, IP]
     L.igg_batch_set_coefs.argtypes = [P, DP, DP, DP, DP, DP]
     L.igg_batch_configure.argtypes = [P, I, I, I]
     L.igg_batch_get_config.argtypes = [P, IP, IP]
     L.igg_batch_step.argtypes = [P, P, P, P, P]
     L.igg_batch_run.argtypes = [P, I, P, P, P, P]
     L.igg_batch_autotune.argtypes = [P, P, P, P, I, P, IP, ctypes.POINTER(ctypes.c_float)]
-    for n in ("igg_batch_create", "igg_batch_destroy", "igg_batch_layout", "igg_batch_set_coefs",
+    for n in ("igg_batch_create", "igg_batch_destroy", "igg_batch_layout", "igg_batch_pitches",
+              "igg_batch_set_coefs",
               "igg_batch_configure", "igg_batch_get_config", "igg_batch_step", "igg_batch_run",
               "igg_batch_autotune"):
         getattr(L, n).restype = I
@@ -303,8 +305,8 @@ def _batch_sigs():
 
 class Batch:
     """Many independent problems of uneven sizes, packed in one buffer per
-    field (problem b at element offset offsets[b], shape (nz, ny, nx)),
-    advanced by one persistent launch per step."""
+    field (problem b at element offset offsets[b], shape (nz, ny, nx) with
+    rows of pitches[b] elements), advanced by one launch per step."""
 
     def __init__(self, sizes, dtype=torch.float32):
         L = _batch_sigs()
@@ -319,6 +321,9 @@ class Batch:
         _check(L.igg_batch_layout(h, offs, ctypes.byref(tot)))
         self.offsets = list(offs)
         self.total = tot.value
+        pit = (ctypes.c_int * len(self.sizes))()
+        _check(L.igg_batch_pitches(h, pit))
+        self.pitches = list(pit)
 
     def destroy(self):
         if self._h:
@@ -341,16 +346,17 @@ class Batch:
         return torch.empty(self.total, dtype=self.dtype, device=device)
 
     def view(self, field: torch.Tensor, b: int) -> torch.Tensor:
+        """Problem b of a batch field as a (nz, ny, nx) view (rows of pitch_b)."""
         nx, ny, nz = self.sizes[b]
-        o = self.offsets[b]
-        return field[o:o + nx * ny * nz].view(nz, ny, nx)
+        o, pt = self.offsets[b], self.pitches[b]
+        return field[o:o + pt * ny * nz].view(nz, ny, pt)[:, :, :nx]
 
     def set_coefs(self, lam, dt, dx, dy, dz):
         n = len(self.sizes)
         arrs = [(ctypes.c_double * n)(*[float(v) for v in a]) for a in (lam, dt, dx, dy, dz)]
         _check(_batch_sigs().igg_batch_set_coefs(self._h, *arrs))
 
-    def configure(self, variant=0, zb=32, ctas_per_sm=0):
+    def configure(self, variant=3, zb=32, ctas_per_sm=0):
         _check(_batch_sigs().igg_batch_configure(self._h, int(variant), int(zb), int(ctas_per_sm)))
 
     def config(self):
