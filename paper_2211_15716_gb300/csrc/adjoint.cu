@@ -9,10 +9,13 @@
 //   lam_out[q] = lam_in[q] + sum_d w_d (v[q-e_d] + v[q+e_d] - 2 v[q]),
 //                on every point q (neighbours outside the array are 0),
 //   gCi[p]    += lam_in[p] * l(T_n)[p] on inner p (accumulated in FP64).
-// The v and l sums use the same arithmetic as the forward kernels.
+// FP64 fields form l(T_n) with the emulated cell's exact differences where the
+// stencil allows it (cell.cuh), else in FP64; the v sums are FP64 (lam_in
+// changes sign from point to point, which the emulation cannot take).
 #include <algorithm>
 #include <cstring>
 
+#include "cell.cuh"
 #include "igg_internal.h"
 
 namespace igg {
@@ -36,6 +39,9 @@ struct AdjNum<double> {
     return __fma_rn(wz, sz, l);
   }
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) {
+    return __fma_rn(a, b, c);
+  }
 };
 template <>
 struct AdjNum<float> {
@@ -54,11 +60,63 @@ struct AdjNum<float> {
     return __fmaf_rn(wz, ez, l);
   }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) {
+    return __fmaf_rn(a, b, c);
+  }
 };
 
-constexpr int kAdjX = 32, kAdjY = 8;
+constexpr int kAdjX = 32, kAdjY = 8, kAdjRing = 2 * (kAdjX + 2) + 2 * kAdjY;
 
-// One thread per (x, y) column of a z-chunk; every point of the array.
+// l(T_n) * lam_in added to gCi on inner points: FP64 fields use the emulated
+// cell's exact second differences where the stencil shares sign and exponent
+// (T_n is a forward state, smooth), else the FP64 sum; FP32 fields their
+// FP32 sum. `inner` is the same for the whole warp's call; the FP64 sum is
+// reached only by warps with a point that needs it (a branch on a warp vote,
+// so that it is not evaluated, predicated off, on every point).
+__device__ __forceinline__ void gci_update(double *gp, bool inner, double la, double t, double xm,
+                                           double xp, double ym, double yp, double zm, double zp,
+                                           const W<double> &w) {
+  const double tn[6] = {xm, xp, ym, yp, zm, zp};
+  unsigned hn[6];
+  unsigned long long nb[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    hn[i] = dhi(tn[i]);
+    nb[i] = dbits(tn[i]);
+  }
+  const bool ok = emu_fast_ok(dhi(t), hn);
+  if (__all_sync(0xffffffffu, ok || !inner)) {
+    if (!inner) return;
+    const double g = *gp;
+    if (w.ng == 1) *gp = emu_apply(g, la, emu_lap<1>(t, nb, w));
+    else if (w.ng == 2) *gp = emu_apply(g, la, emu_lap<2>(t, nb, w));
+    else *gp = emu_apply(g, la, emu_lap<3>(t, nb, w));
+  } else if (inner) {
+    const double g = *gp;
+    if (ok) {
+      if (w.ng == 1) *gp = emu_apply(g, la, emu_lap<1>(t, nb, w));
+      else if (w.ng == 2) *gp = emu_apply(g, la, emu_lap<2>(t, nb, w));
+      else *gp = emu_apply(g, la, emu_lap<3>(t, nb, w));
+    } else {
+      *gp = __fma_rn(la, AdjNum<double>::lsum(t, xm, xp, ym, yp, zm, zp, w.wx, w.wy, w.wz, w.wc),
+                     g);
+    }
+  }
+}
+__device__ __forceinline__ void gci_update(double *gp, bool inner, float la, float t, float xm,
+                                           float xp, float ym, float yp, float zm, float zp,
+                                           const W<float> &w) {
+  if (inner)
+    *gp = __fma_rn((double)la,
+                   (double)AdjNum<float>::lsum(t, xm, xp, ym, yp, zm, zp, w.wx, w.wy, w.wz, w.wc),
+                   *gp);
+}
+
+// One CTA per 32x8 block of (x, y) columns and a chunk of zb planes, every
+// point of the array. Per plane, v = Ci*lam_in and T_n of the block and of
+// the ring of one point around it go to shared memory (two buffers, one
+// barrier per plane); each v is formed once, by the thread of its point or
+// of its ring position. The column's planes z-1, z, z+1 stay in registers.
 template <class S>
 __global__ void __launch_bounds__(kAdjX *kAdjY)
     k_adjoint(int nx, int ny, int nz, int zb, S *__restrict__ lam_out,
@@ -66,42 +124,81 @@ __global__ void __launch_bounds__(kAdjX *kAdjY)
               const S *__restrict__ Ci, double *__restrict__ gCi, Coef c) {
   using N = AdjNum<S>;
   using C = typename N::C;
-  const int x = blockIdx.x * kAdjX + threadIdx.x;
-  const int y = blockIdx.y * kAdjY + threadIdx.y;
-  if (x >= nx || y >= ny) return;
-  const int z0 = blockIdx.z * zb;
-  const int z1 = min(z0 + zb, nz);
-  const C wx = (C)c.wx, wy = (C)c.wy, wz = (C)c.wz, wc = (C)c.wc;
+  __shared__ C vs[2][kAdjY + 2][kAdjX + 2];
+  __shared__ C ts[2][kAdjY + 2][kAdjX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kAdjX + tx;
+  const int x0 = blockIdx.x * kAdjX, y0 = blockIdx.y * kAdjY;
+  const int x = x0 + tx, y = y0 + ty;
+  const int z0 = blockIdx.z * zb, z1 = min(z0 + zb, nz);
+  const W<C> w = make_w(c, C(0));
   const long long sy = nx, sz = (long long)nx * ny;
-  const bool in_xy = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
-  // v at (x, y, z) of this column, 0 off the inner points
-  auto vcol = [&](int z) -> C {
-    if (!in_xy || z <= 0 || z >= nz - 1) return C(0);
-    const long long p = x + sy * y + sz * z;
-    return N::mul(N::ld(Ci + p), N::ld(lam_in + p));
-  };
-  auto vat = [&](int xx, int yy, int z) -> C {
-    if (xx <= 0 || xx >= nx - 1 || yy <= 0 || yy >= ny - 1 || z <= 0 || z >= nz - 1) return C(0);
-    const long long p = xx + sy * yy + sz * z;
-    return N::mul(N::ld(Ci + p), N::ld(lam_in + p));
-  };
-  C vm = vcol(z0 - 1), vc = vcol(z0);
-  for (int z = z0; z < z1; ++z) {
-    const C vp = vcol(z + 1);
-    const long long p = x + sy * y + sz * z;
-    const C la = N::ld(lam_in + p);
-    const C adj = N::lsum(vc, vat(x - 1, y, z), vat(x + 1, y, z), vat(x, y - 1, z),
-                          vat(x, y + 1, z), vm, vp, wx, wy, wz, wc);
-    lam_out[p] = (S)N::add(la, adj);
-    if (in_xy && z > 0 && z < nz - 1) {
-      const C t = N::ld(Tn + p);
-      const C l = N::lsum(t, N::ld(Tn + p - 1), N::ld(Tn + p + 1), N::ld(Tn + p - sy),
-                          N::ld(Tn + p + sy), N::ld(Tn + p - sz), N::ld(Tn + p + sz), wx, wy, wz,
-                          wc);
-      gCi[p] = __fma_rn((double)la, (double)l, gCi[p]);
+  // ring position of this thread (tid < kAdjRing): rows y0-1 and y0+kAdjY
+  // over x0-1 .. x0+kAdjX, then columns x0-1 and x0+kAdjX over y0 .. y0+kAdjY-1
+  int rx = 0, ry = 0, sxr = 0, syr = 0;
+  if (tid < kAdjRing) {
+    if (tid < 2 * (kAdjX + 2)) {
+      const int i = tid % (kAdjX + 2);
+      rx = x0 - 1 + i;
+      ry = tid < kAdjX + 2 ? y0 - 1 : y0 + kAdjY;
+    } else {
+      const int i = tid - 2 * (kAdjX + 2);
+      rx = i < kAdjY ? x0 - 1 : x0 + kAdjX;
+      ry = y0 + (i % kAdjY);
     }
+    sxr = rx - x0 + 1;
+    syr = ry - y0 + 1;
+  }
+  const bool own = x < nx && y < ny;
+  const bool ring = tid < kAdjRing && rx >= 0 && rx < nx && ry >= 0 && ry < ny;
+  const bool in_xy = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
+  const bool rin_xy = rx > 0 && rx < nx - 1 && ry > 0 && ry < ny - 1;
+  // v and T at (xx, yy, z): v = 0 off the inner points, T = 0 off the array
+  auto vload = [&](bool ok, bool inner, long long p, int z) -> C {
+    return (ok && inner && z > 0 && z < nz - 1) ? N::mul(N::ld(Ci + p), N::ld(lam_in + p)) : C(0);
+  };
+  auto tload = [&](bool ok, long long p, int z) -> C {
+    return (ok && z >= 0 && z < nz) ? N::ld(Tn + p) : C(0);
+  };
+  const long long pc = x + sy * y, pr = rx + sy * ry;
+  C vm = vload(own, in_xy, pc + sz * (z0 - 1), z0 - 1), vc = vload(own, in_xy, pc + sz * z0, z0);
+  C tm = tload(own, pc + sz * (z0 - 1), z0 - 1), tc = tload(own, pc + sz * z0, z0);
+  C la = own ? N::ld(lam_in + pc + sz * z0) : C(0);
+  // ring values of the current plane, loaded one plane ahead
+  C rv = vload(ring, rin_xy, pr + sz * z0, z0), rt = tload(ring, pr + sz * z0, z0);
+  for (int z = z0; z < z1; ++z) {
+    const int b = z & 1;
+    const long long p = pc + sz * z;
+    vs[b][ty + 1][tx + 1] = vc;
+    ts[b][ty + 1][tx + 1] = tc;
+    if (tid < kAdjRing) {
+      vs[b][syr][sxr] = rv;
+      ts[b][syr][sxr] = rt;
+      rv = vload(ring, rin_xy, pr + sz * (z + 1), z + 1);
+      rt = tload(ring, pr + sz * (z + 1), z + 1);
+    }
+    const C vp = vload(own, in_xy, p + sz, z + 1);
+    const C tp = tload(own, p + sz, z + 1);
+    const C lap = own && z + 1 < nz ? N::ld(lam_in + p + sz) : C(0);
+    __syncthreads();
+    if (own) {
+      const C vxm = vs[b][ty + 1][tx], vxp = vs[b][ty + 1][tx + 2];
+      const C vym = vs[b][ty][tx + 1], vyp = vs[b][ty + 2][tx + 1];
+      // lam_out = lam_in + wc v + sum_d w_d (v[-d] + v[+d])
+      C acc = N::fma(w.wc, vc, la);
+      acc = N::fma(w.wx, N::add(vxm, vxp), acc);
+      acc = N::fma(w.wy, N::add(vym, vyp), acc);
+      acc = N::fma(w.wz, N::add(vm, vp), acc);
+      lam_out[p] = (S)acc;
+    }
+    // every thread of the warp takes part (warp vote inside)
+    gci_update(gCi + (own ? p : 0), own && in_xy && z > 0 && z < nz - 1, la, tc,
+               ts[b][ty + 1][tx], ts[b][ty + 1][tx + 2], ts[b][ty][tx + 1], ts[b][ty + 2][tx + 1],
+               tm, tp, w);
     vm = vc;
     vc = vp;
+    tm = tc;
+    tc = tp;
+    la = lap;
   }
 }
 

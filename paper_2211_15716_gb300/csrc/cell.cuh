@@ -175,13 +175,19 @@ __device__ __forceinline__ bool emu_fast_ok(unsigned hc, const unsigned *hn) {
   return diff == 0u && E - 949u <= 190u;
 }
 
-// The emulated update of a fast-path point with NG weight groups: tc the
-// centre, nb[6] the bit patterns of the neighbours in the order x-, x+, y-,
-// y+, z-, z+. Any input runs without faults; the value means something only
-// where emu_fast_ok.
+// The emulated weighted Laplacian of a fast-path stencil with NG weight
+// groups: l = sum_g w_g G_g = (S + C) * u, u = +-2^(E-1075) (sign: bit 31 of
+// `sign`; exponent offset for f2d_scaled: eoff). tc is the centre, nb[6] the
+// bit patterns of the neighbours in the order x-, x+, y-, y+, z-, z+. Any input
+// runs without faults; the value means something only where emu_fast_ok.
+struct EmuLap {
+  float S, C;
+  unsigned eoff, sign;
+};
+
 template <int NG>
-__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
-                                                double ci, const W<double> &w) {
+__device__ __forceinline__ EmuLap emu_lap(double tc, const unsigned long long *nb,
+                                          const W<double> &w) {
   const unsigned long long c2 = dbits(tc) << 1;
   long long D[3];
 #pragma unroll
@@ -211,27 +217,41 @@ __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long l
     X[g] = __fmaf_rn(w.wh[g], sg, -P[g]);
     R[g] = __fmaf_rn(w.wl[g], sg, __fmul_rn(w.wh[g], tg));
   }
-  float S, C;
+  EmuLap L;
   if constexpr (NG == 1) {
-    S = P[0];
-    C = __fadd_rn(X[0], R[0]);
+    L.S = P[0];
+    L.C = __fadd_rn(X[0], R[0]);
   } else if constexpr (NG == 2) {
     float e1;
-    S = two_sum(P[0], P[1], e1);
-    C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), e1), __fadd_rn(R[0], R[1]));
+    L.S = two_sum(P[0], P[1], e1);
+    L.C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), e1), __fadd_rn(R[0], R[1]));
   } else {
     float e1, e2;
-    S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
-    C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
-                  __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
+    L.S = two_sum(two_sum(P[0], P[1], e1), P[2], e2);
+    L.C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
+                    __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
   }
   const unsigned hc = dhi(tc);
-  const unsigned eoff = (hc & 0x7FF00000u) - (179u << 20);
+  L.eoff = (hc & 0x7FF00000u) - (179u << 20);
   // the bit differences of negative values carry the opposite sign of the
-  // value differences: flip Ci instead
-  const double sci = __hiloint2double((int)((unsigned)__double2hiint(ci) ^ (hc & 0x80000000u)),
-                                      __double2loint(ci));
-  return __fma_rn(sci, f2d_scaled(S, eoff), __fma_rn(sci, f2d_scaled(C, eoff), tc));
+  // value differences
+  L.sign = hc & 0x80000000u;
+  return L;
+}
+
+// base + m * l for an emulated Laplacian l, with two FP64 FMAs (the sign of
+// l goes into m).
+__device__ __forceinline__ double emu_apply(double base, double m, const EmuLap &L) {
+  const double sm =
+      __hiloint2double((int)((unsigned)__double2hiint(m) ^ L.sign), __double2loint(m));
+  return __fma_rn(sm, f2d_scaled(L.S, L.eoff), __fma_rn(sm, f2d_scaled(L.C, L.eoff), base));
+}
+
+// The emulated update of a fast-path point: tc + ci * l(T).
+template <int NG>
+__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
+                                                double ci, const W<double> &w) {
+  return emu_apply(tc, ci, emu_lap<NG>(tc, nb, w));
 }
 
 __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
