@@ -126,6 +126,20 @@ int igg_subdomain_info(const igg_grid *grid, int sub, int coords[3],
 int igg_update_halo(igg_grid *grid, void *const fields[], int nfields,
                     igg_dtype dtype, void *stream);
 
+/* update_halo! on fields of a staggered grid (Sec. Approach: regular
+ * staggered grids): each of the nfields fields has local size nf (x, y, z;
+ * layout [nsub][nf[2]][nf[1]][nf[0]]) with |nf[d] - n[d]| <= 1, e.g. fluxes
+ * or face velocities one point shorter or longer than the grid's arrays.
+ * The field's overlap is o + (nf - n) per dimension (the staggered points on
+ * a shared face are shared as well): its first plane receives plane nf - o_f
+ * of the left neighbour, its last plane plane o_f - 1 of the right one, in
+ * the order x, y, z as igg_update_halo; a dimension where o_f < 2 exchanges
+ * nothing (neighbours then share one plane and have no halo plane). Plane
+ * tables are built once per size and kept on the grid. IGG_EINVAL for sizes
+ * off by more than one or below 3, NULL or misaligned fields. */
+int igg_update_halo_staggered(igg_grid *grid, void *const fields[], int nfields,
+                              igg_dtype dtype, const int nf[3], void *stream);
+
 /* Device error word of the grid's pipelined kernels: bit 1 = a bounded
  * wait inside a kernel gave up (the kernel stopped early and its output is
  * incomplete), bit 2 = waiting for its own copies in flight gave up.

@@ -251,6 +251,24 @@ def update_halo(field: np.ndarray, dims, periods, overlap):
                                _ptr(field), field.dtype.itemsize)
 
 
+def staggered_overlap(n, nf, overlap):
+    """Overlap of a field of local size nf on a grid of local size n and
+    overlap o: o + (nf - n) per dimension (the staggered points on a shared
+    face are shared too)."""
+    return tuple(int(overlap[d]) + int(nf[d]) - int(n[d]) for d in range(3))
+
+
+def update_halo_staggered(field: np.ndarray, n, dims, periods, overlap):
+    """update_halo! on a staggered field [nsub][nf_z][nf_y][nf_x] whose local
+    size differs from the grid's n by at most one point per dimension: the
+    plain halo update with the field's own overlap (staggered_overlap);
+    dimensions where that is below 2 exchange nothing."""
+    nf = (field.shape[3], field.shape[2], field.shape[1])
+    if any(abs(nf[d] - int(n[d])) > 1 for d in range(3)):
+        raise ValueError("a staggered field differs from the grid by at most one point")
+    update_halo(field, dims, periods, staggered_overlap(n, nf, overlap))
+
+
 def adjoint_step(lam_out, lam_in, Tn, Ci, gCi, lam, dt, dx, dy, dz):
     """One backward step of the adjoint (see oracle.c)."""
     for a in (lam_out, lam_in, Tn, Ci, gCi):

@@ -107,7 +107,9 @@ void oracle_step_part(long nx, long ny, long nz, double *T2, const double *T,
  * or -1 for none (a physical boundary). Whole planes are copied, including the
  * points that lie in other dimensions' halos, so the x, y, z order decides the
  * values of edges and corners. The copy is a byte copy of elem_size bytes per
- * point, so it serves every element type. */
+ * point, so it serves every element type. A dimension whose overlap is below
+ * 2 exchanges nothing (a staggered field's overlap o + (n_f - n) can be 1:
+ * the neighbours then share one plane and have no halo plane to fill). */
 void oracle_update_halo(int nsub, const int *left_nb, const int *right_nb,
                         long nx, long ny, long nz, const long *overlap,
                         void *field, long elem_size) {
@@ -117,6 +119,7 @@ void oracle_update_halo(int nsub, const int *left_nb, const int *right_nb,
   const size_t es = (size_t)elem_size;
   for (int d = 0; d < 3; ++d) {
     const long o = overlap[d];
+    if (o < 2) continue;
     for (int s = 0; s < nsub; ++s) {
       for (int side = 0; side < 2; ++side) {
         int nb = side == 0 ? left_nb[3 * s + d] : right_nb[3 * s + d];

@@ -354,6 +354,12 @@ struct igg_grid {
   std::map<std::array<int, 4>, SplitTiles> split;  // keyed by widths and V
   PlaneCopy *copies[3] = {nullptr, nullptr, nullptr};
   int ncopies[3] = {0, 0, 0};
+  // plane-copy tables of staggered field sizes (igg_update_halo_staggered)
+  struct Tables {
+    PlaneCopy *copies[3] = {nullptr, nullptr, nullptr};
+    int ncopies[3] = {0, 0, 0};
+  };
+  std::map<std::array<int, 3>, Tables> staggered;
   std::map<GraphKey, cudaGraphExec_t> graphs;
   unsigned *dev_err = nullptr;  // device error word of the pipelined kernels
   int *nbr = nullptr;           // device copy of left/right per subdomain and dimension
@@ -555,39 +561,51 @@ cudaError_t launch_tiles(const igg_grid *g, int V, igg_dtype dt, const TileSet &
   return launch_stencil(dt, (const Tile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
 
-// Plane-copy tables of the halo update, one per dimension.
-int build_halo_tables(igg_grid *g) {
-  const long long nx = g->n[0], ny = g->n[1];
-  const long long plane_stride[3] = {1, nx, nx * ny};
+// Plane-copy tables of the halo update of a field of local size nf (the
+// grid's own size, or a staggered one), one per dimension. The field's
+// overlap is o + (nf - n) (staggered points on a shared face are shared);
+// a dimension whose overlap is below 2 exchanges nothing.
+int build_halo_tables(const igg_grid *g, const int nf[3], PlaneCopy *copies[3], int ncopies[3]) {
+  const long long nloc = (long long)nf[0] * nf[1] * nf[2];
+  const long long plane_stride[3] = {1, nf[0], (long long)nf[0] * nf[1]};
   for (int d = 0; d < 3; ++d) {
     std::vector<PlaneCopy> v;
-    const int nd = g->n[d], o = g->overlap[d];
-    for (int s = 0; s < g->nsub; ++s) {
+    const int nd = nf[d], o = g->overlap[d] + nf[d] - g->n[d];
+    for (int s = 0; s < g->nsub && o >= 2; ++s) {
       const int l = g->left[3 * s + d], r = g->right[3 * s + d];
       if (l >= 0)
-        v.push_back({(long long)s * g->nloc + 0 * plane_stride[d],
-                     (long long)l * g->nloc + (long long)(nd - o) * plane_stride[d]});
+        v.push_back({(long long)s * nloc + 0 * plane_stride[d],
+                     (long long)l * nloc + (long long)(nd - o) * plane_stride[d]});
       if (r >= 0)
-        v.push_back({(long long)s * g->nloc + (long long)(nd - 1) * plane_stride[d],
-                     (long long)r * g->nloc + (long long)(o - 1) * plane_stride[d]});
+        v.push_back({(long long)s * nloc + (long long)(nd - 1) * plane_stride[d],
+                     (long long)r * nloc + (long long)(o - 1) * plane_stride[d]});
     }
-    g->ncopies[d] = (int)v.size();
+    ncopies[d] = (int)v.size();
+    copies[d] = nullptr;
     if (v.empty()) continue;
-    cudaError_t e = cudaMalloc(&g->copies[d], v.size() * sizeof(PlaneCopy));
+    cudaError_t e = cudaMalloc(&copies[d], v.size() * sizeof(PlaneCopy));
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(halo table)");
-    e = cudaMemcpy(g->copies[d], v.data(), v.size() * sizeof(PlaneCopy), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(copies[d], v.data(), v.size() * sizeof(PlaneCopy), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(halo table)");
   }
   return IGG_OK;
 }
 
-cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
-  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+int build_halo_tables(igg_grid *g) { return build_halo_tables(g, g->n, g->copies, g->ncopies); }
+
+// The plane copies of a field of local size nf, dimensions x, y, z in order.
+cudaError_t enqueue_halo(PlaneCopy *const copies[3], const int ncopies[3], const int nf[3],
+                         void *field, size_t es, cudaStream_t s) {
+  const int nx = nf[0], ny = nf[1], nz = nf[2];
   const long long sxy = (long long)nx * ny;
-  cudaError_t e = launch_halo(es, g->copies[0], g->ncopies[0], field, ny, nz, nx, sxy, s);
-  if (e == cudaSuccess) e = launch_halo(es, g->copies[1], g->ncopies[1], field, nx, nz, 1, sxy, s);
-  if (e == cudaSuccess) e = launch_halo(es, g->copies[2], g->ncopies[2], field, nx, ny, 1, nx, s);
+  cudaError_t e = launch_halo(es, copies[0], ncopies[0], field, ny, nz, nx, sxy, s);
+  if (e == cudaSuccess) e = launch_halo(es, copies[1], ncopies[1], field, nx, nz, 1, sxy, s);
+  if (e == cudaSuccess) e = launch_halo(es, copies[2], ncopies[2], field, nx, ny, 1, nx, s);
   return e;
+}
+
+cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
+  return enqueue_halo(g->copies, g->ncopies, g->n, field, es, s);
 }
 
 bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->ncopies[2] > 0; }
@@ -670,6 +688,8 @@ void destroy_grid(igg_grid *g) {
   }
   for (auto &kv : g->full) free_tiles(kv.second);
   for (int d = 0; d < 3; ++d) cudaFree(g->copies[d]);
+  for (auto &kv : g->staggered)
+    for (int d = 0; d < 3; ++d) cudaFree(kv.second.copies[d]);
   cudaFree(g->dev_err);
   cudaFree(g->nbr);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
@@ -862,6 +882,41 @@ int igg_update_halo(igg_grid *g, void *const fields[], int nfields, igg_dtype dt
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < nfields; ++i) {
     cudaError_t e = enqueue_halo(g, fields[i], dtype_size(dt), s);
+    if (e != cudaSuccess) return cuda_error(e, "halo launch");
+  }
+  return IGG_OK;
+}
+
+int igg_update_halo_staggered(igg_grid *g, void *const fields[], int nfields, igg_dtype dt,
+                              const int nf[3], void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_dtype(dt)) return rc;
+  if (!nf) return set_error(IGG_EINVAL, "nf is NULL");
+  for (int d = 0; d < 3; ++d) {
+    if (nf[d] < g->n[d] - 1 || nf[d] > g->n[d] + 1)
+      return set_error(IGG_EINVAL, "nf[%d]=%d differs from n[%d]=%d by more than one", d, nf[d], d,
+                       g->n[d]);
+    if (nf[d] < 3) return set_error(IGG_EINVAL, "nf[%d]=%d < 3", d, nf[d]);
+  }
+  if (nfields < 0 || (nfields > 0 && !fields)) return set_error(IGG_EINVAL, "bad field list");
+  for (int i = 0; i < nfields; ++i)
+    if (int rc = check_field(g, fields[i], "field")) return rc;
+  DeviceGuard dg(g->device);
+  const std::array<int, 3> key = {nf[0], nf[1], nf[2]};
+  auto it = g->staggered.find(key);
+  if (it == g->staggered.end()) {
+    igg_grid::Tables t;
+    if (int rc = build_halo_tables(g, nf, t.copies, t.ncopies)) {
+      for (int d = 0; d < 3; ++d) cudaFree(t.copies[d]);
+      return rc;
+    }
+    it = g->staggered.emplace(key, t).first;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < nfields; ++i) {
+    cudaError_t e = enqueue_halo(it->second.copies, it->second.ncopies, nf, fields[i],
+                                 dtype_size(dt), s);
     if (e != cudaSuccess) return cuda_error(e, "halo launch");
   }
   return IGG_OK;

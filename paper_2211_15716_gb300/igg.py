@@ -58,6 +58,7 @@ def lib():
     L.igg_grid_shape.argtypes = [P, IP, IP, IP, IP, IP]
     L.igg_subdomain_info.argtypes = [P, I, IP, IP, IP, IP]
     L.igg_update_halo.argtypes = [P, ctypes.POINTER(P), I, I, P]
+    L.igg_update_halo_staggered.argtypes = [P, ctypes.POINTER(P), I, I, IP, P]
     L.igg_step.argtypes = [P, P, P, P, I, D, D, D, D, D, P]
     L.igg_step_hidden.argtypes = [P, IP, P, P, P, I, D, D, D, D, D, P]
     L.igg_run.argtypes = [P, I, IP, P, P, P, I, D, D, D, D, D, P]
@@ -65,7 +66,8 @@ def lib():
     L.igg_device_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint), I]
     L.igg_grid_set_option.argtypes = [P, I, I]
     for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
-                 "igg_grid_shape", "igg_subdomain_info", "igg_update_halo", "igg_step",
+                 "igg_grid_shape", "igg_subdomain_info", "igg_update_halo",
+                 "igg_update_halo_staggered", "igg_step",
                  "igg_step_hidden", "igg_run", "igg_reduce", "igg_device_status",
                  "igg_grid_set_option"):
         getattr(L, name).restype = I
@@ -207,6 +209,17 @@ class Grid:
         arr = (ctypes.c_void_p * len(fields))(*[_ptr(f, self.nsub * self.nloc, dt, "field").value
                                                 for f in fields])
         _check(lib().igg_update_halo(self._handle(), arr, len(fields), dtype_code(dt), _stream(stream)))
+
+    def update_halo_staggered(self, nf, *fields, stream=None):
+        """update_halo! on staggered fields of local size nf = (nx, ny, nz),
+        each within one point of the grid's size (igg_update_halo_staggered)."""
+        if not fields:
+            return
+        dt = fields[0].dtype
+        npts = self.nsub * int(nf[0]) * int(nf[1]) * int(nf[2])
+        arr = (ctypes.c_void_p * len(fields))(*[_ptr(f, npts, dt, "field").value for f in fields])
+        _check(lib().igg_update_halo_staggered(self._handle(), arr, len(fields), dtype_code(dt),
+                                               _ints(nf), _stream(stream)))
 
     def step(self, T2, T, Ci, lam, dt, dx, dy, dz, stream=None):
         """Fig. 1 step! on every subdomain (inner points of T2)."""

@@ -141,3 +141,55 @@ def test_planted_mistake_is_caught(monkeypatch):
     Tr = oracle.run(Tu, Ciu, 3, 1.0, dt, *dd)
     with pytest.raises(AssertionError):
         compare_to_undecomposed(Td, Tr, n, dims, o)
+
+
+STAGGERED = [
+    # n, dims, periods, overlap, delta (field size n + delta)
+    ((8, 7, 6), (2, 2, 2), (0, 0, 0), (2, 2, 2), (1, 0, 0)),
+    ((8, 7, 6), (2, 2, 2), (1, 1, 0), (2, 2, 2), (1, 1, 1)),
+    ((9, 8, 7), (3, 1, 2), (0, 1, 1), (3, 2, 3), (-1, 1, -1)),
+    ((7, 7, 7), (2, 2, 1), (1, 0, 1), (2, 2, 2), (-1, 0, 1)),   # overlap 1 in x: no x exchange
+    ((6, 6, 6), (1, 1, 1), (1, 1, 1), (2, 2, 2), (1, 1, 1)),    # its own neighbour
+]
+
+
+@pytest.mark.parametrize("n,dims,periods,overlap,delta", STAGGERED)
+def test_staggered_halo_restores_global_field(n, dims, periods, overlap, delta):
+    """A staggered field (local size n + delta, overlap o + delta) cut from one
+    global field (extent dims*(n-o) + o + delta, or dims*(n-o) periodic) with
+    every exchanged halo plane poisoned: after the halo update every point of
+    every subdomain equals the global field at its global index."""
+    nf = tuple(n[d] + delta[d] for d in range(3))
+    of = oracle.staggered_overlap(n, nf, overlap)
+    nsub = dims[0] * dims[1] * dims[2]
+    ng = tuple(dims[d] * (n[d] - overlap[d]) + (0 if periods[d] else overlap[d] + delta[d])
+               for d in range(3))
+    G = synth.uniform(21, 3, np.arange(ng[0] * ng[1] * ng[2], dtype=np.uint64)).reshape(ng[2], ng[1], ng[0])
+    left, right = oracle.neighbours(dims, periods)
+    F = np.empty((nsub, nf[2], nf[1], nf[0]))
+    idx = []
+    for s in range(nsub):
+        c = oracle.coords(s, dims)
+        ii = [(c[d] * (n[d] - overlap[d]) + np.arange(nf[d])) % ng[d] for d in range(3)]
+        idx.append(ii)
+        F[s] = G[np.ix_(ii[2], ii[1], ii[0])]
+        for d in range(3):
+            if of[d] < 2:
+                continue
+            sl = [slice(None)] * 3
+            if left[s][d] >= 0:
+                sl[2 - d] = 0
+                F[s][tuple(sl)] = np.nan
+            if right[s][d] >= 0:
+                sl[2 - d] = nf[d] - 1
+                F[s][tuple(sl)] = np.nan
+    oracle.update_halo_staggered(F, n, dims, periods, overlap)
+    for s in range(nsub):
+        ii = idx[s]
+        assert np.array_equal(F[s], G[np.ix_(ii[2], ii[1], ii[0])]), f"subdomain {s}"
+
+
+def test_staggered_overlap_rule():
+    assert oracle.staggered_overlap((8, 7, 6), (9, 6, 6), (2, 2, 2)) == (3, 1, 2)
+    with pytest.raises(ValueError):
+        oracle.update_halo_staggered(np.zeros((1, 6, 6, 10)), (8, 6, 6), (1, 1, 1), (0, 0, 0), (2, 2, 2))
