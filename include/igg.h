@@ -120,8 +120,8 @@ int igg_subdomain_info(const igg_grid *grid, int sub, int coords[3],
  * plane (index n-1) receives plane o-1 of its right neighbour. Whole planes
  * are copied, including points in other dimensions' halos, so edges and
  * corners end up exactly as after the sequential x, y, z exchange. The copy
- * is bit exact. Work is ordered on `stream` (the library's high-priority
- * stream runs it and `stream` waits for it).
+ * is bit exact. One launch per dimension serves all the fields. Work is
+ * ordered on `stream`.
  * ------------------------------------------------------------------------- */
 int igg_update_halo(igg_grid *grid, void *const fields[], int nfields,
                     igg_dtype dtype, void *stream);
@@ -139,6 +139,14 @@ int igg_update_halo(igg_grid *grid, void *const fields[], int nfields,
  * off by more than one or below 3, NULL or misaligned fields. */
 int igg_update_halo_staggered(igg_grid *grid, void *const fields[], int nfields,
                               igg_dtype dtype, const int nf[3], void *stream);
+
+/* update_halo!(A...) on fields of possibly different staggered sizes:
+ * sizes[3*i .. 3*i+2] is field i's local size (each within one point of the
+ * grid's, rules of igg_update_halo_staggered). One launch per dimension
+ * serves all fields (x, then y, then z), with the same result as updating
+ * the fields one by one. */
+int igg_update_halo_fields(igg_grid *grid, void *const fields[], const int *sizes,
+                           int nfields, igg_dtype dtype, void *stream);
 
 /* Device error word of the grid's pipelined kernels: bit 1 = a bounded
  * wait inside a kernel gave up (the kernel stopped early and its output is

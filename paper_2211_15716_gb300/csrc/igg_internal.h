@@ -163,6 +163,20 @@ cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, 
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.
+// The copies of one dimension of up to kMaxHaloJobs fields in one launch
+// (fields of different sizes: each job its own plane table and geometry as
+// for launch_halo; vec is set by the launch).
+constexpr int kMaxHaloJobs = 16;
+struct HaloJob {
+  const PlaneCopy *copies;
+  void *field;
+  long long sa, sb;
+  int ncopies, na, nb, vec;
+};
+struct HaloJobs {
+  HaloJob j[kMaxHaloJobs];
+};
+cudaError_t launch_halo_jobs(size_t elem_size, HaloJobs jobs, int njobs, cudaStream_t s);
 cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
                         void *field, int na, int nb, long long sa, long long sb,
                         cudaStream_t s);

@@ -608,6 +608,64 @@ cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
   return enqueue_halo(g->copies, g->ncopies, g->n, field, es, s);
 }
 
+// Plane tables for fields of local size nf: the grid's own, or a staggered
+// size's (built on first use).
+int halo_tables(igg_grid *g, const int nf[3], PlaneCopy *const **copies, const int **ncopies) {
+  if (nf[0] == g->n[0] && nf[1] == g->n[1] && nf[2] == g->n[2]) {
+    *copies = g->copies;
+    *ncopies = g->ncopies;
+    return IGG_OK;
+  }
+  const std::array<int, 3> key = {nf[0], nf[1], nf[2]};
+  auto it = g->staggered.find(key);
+  if (it == g->staggered.end()) {
+    igg_grid::Tables t;
+    if (int rc = build_halo_tables(g, nf, t.copies, t.ncopies)) {
+      for (int d = 0; d < 3; ++d) cudaFree(t.copies[d]);
+      return rc;
+    }
+    it = g->staggered.emplace(key, t).first;
+  }
+  *copies = it->second.copies;
+  *ncopies = it->second.ncopies;
+  return IGG_OK;
+}
+
+// Halo update of several fields (field i of local size nf[3i..3i+2]): per
+// dimension x, y, z one launch for all fields (chunks of kMaxHaloJobs).
+int enqueue_halo_fields(igg_grid *g, void *const fields[], const int *nf, int nfields, size_t es,
+                        cudaStream_t s) {
+  std::vector<PlaneCopy *const *> tc(nfields);
+  std::vector<const int *> tn(nfields);
+  for (int i = 0; i < nfields; ++i)
+    if (int rc = halo_tables(g, nf + 3 * i, &tc[i], &tn[i])) return rc;
+  for (int d = 0; d < 3; ++d) {
+    HaloJobs jobs;
+    int nj = 0;
+    for (int i = 0; i <= nfields; ++i) {
+      if (nj == kMaxHaloJobs || (i == nfields && nj > 0)) {
+        cudaError_t e = launch_halo_jobs(es, jobs, nj, s);
+        if (e != cudaSuccess) return cuda_error(e, "halo launch");
+        nj = 0;
+      }
+      if (i == nfields) break;
+      if (tn[i][d] == 0) continue;
+      const int *n = nf + 3 * i;
+      const long long sxy = (long long)n[0] * n[1];
+      HaloJob &j = jobs.j[nj++];
+      j.copies = tc[i][d];
+      j.ncopies = tn[i][d];
+      j.field = fields[i];
+      j.na = d == 0 ? n[1] : n[0];
+      j.nb = d == 2 ? n[1] : n[2];
+      j.sa = d == 0 ? n[0] : 1;
+      j.sb = d == 2 ? n[0] : sxy;
+      j.vec = 0;
+    }
+  }
+  return IGG_OK;
+}
+
 bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->ncopies[2] > 0; }
 
 // Whether hidden steps fuse the halo update into one TMA step launch: the
@@ -879,12 +937,10 @@ int igg_update_halo(igg_grid *g, void *const fields[], int nfields, igg_dtype dt
   for (int i = 0; i < nfields; ++i)
     if (int rc = check_field(g, fields[i], "field")) return rc;
   DeviceGuard dg(g->device);
-  cudaStream_t s = (cudaStream_t)stream;
-  for (int i = 0; i < nfields; ++i) {
-    cudaError_t e = enqueue_halo(g, fields[i], dtype_size(dt), s);
-    if (e != cudaSuccess) return cuda_error(e, "halo launch");
-  }
-  return IGG_OK;
+  std::vector<int> nf(3 * (size_t)nfields);
+  for (int i = 0; i < nfields; ++i)
+    for (int d = 0; d < 3; ++d) nf[3 * i + d] = g->n[d];
+  return enqueue_halo_fields(g, fields, nf.data(), nfields, dtype_size(dt), (cudaStream_t)stream);
 }
 
 int igg_update_halo_staggered(igg_grid *g, void *const fields[], int nfields, igg_dtype dt,
@@ -903,23 +959,30 @@ int igg_update_halo_staggered(igg_grid *g, void *const fields[], int nfields, ig
   for (int i = 0; i < nfields; ++i)
     if (int rc = check_field(g, fields[i], "field")) return rc;
   DeviceGuard dg(g->device);
-  const std::array<int, 3> key = {nf[0], nf[1], nf[2]};
-  auto it = g->staggered.find(key);
-  if (it == g->staggered.end()) {
-    igg_grid::Tables t;
-    if (int rc = build_halo_tables(g, nf, t.copies, t.ncopies)) {
-      for (int d = 0; d < 3; ++d) cudaFree(t.copies[d]);
-      return rc;
-    }
-    it = g->staggered.emplace(key, t).first;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> nfs(3 * (size_t)nfields);
+  for (int i = 0; i < nfields; ++i)
+    for (int d = 0; d < 3; ++d) nfs[3 * i + d] = nf[d];
+  return enqueue_halo_fields(g, fields, nfs.data(), nfields, dtype_size(dt), (cudaStream_t)stream);
+}
+
+int igg_update_halo_fields(igg_grid *g, void *const fields[], const int *sizes, int nfields,
+                           igg_dtype dt, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (int rc = check_dtype(dt)) return rc;
+  if (nfields < 0 || (nfields > 0 && (!fields || !sizes)))
+    return set_error(IGG_EINVAL, "bad field list");
   for (int i = 0; i < nfields; ++i) {
-    cudaError_t e = enqueue_halo(it->second.copies, it->second.ncopies, nf, fields[i],
-                                 dtype_size(dt), s);
-    if (e != cudaSuccess) return cuda_error(e, "halo launch");
+    for (int d = 0; d < 3; ++d) {
+      const int v = sizes[3 * i + d];
+      if (v < g->n[d] - 1 || v > g->n[d] + 1 || v < 3)
+        return set_error(IGG_EINVAL, "field %d: size %d in dimension %d not within one of %d (or < 3)",
+                         i, v, d, g->n[d]);
+    }
+    if (int rc = check_field(g, fields[i], "field")) return rc;
   }
-  return IGG_OK;
+  DeviceGuard dg(g->device);
+  return enqueue_halo_fields(g, fields, sizes, nfields, dtype_size(dt), (cudaStream_t)stream);
 }
 
 int igg_step(igg_grid *g, void *T2, const void *T, const void *Ci, igg_dtype dt, double lam,

@@ -59,6 +59,7 @@ def lib():
     L.igg_subdomain_info.argtypes = [P, I, IP, IP, IP, IP]
     L.igg_update_halo.argtypes = [P, ctypes.POINTER(P), I, I, P]
     L.igg_update_halo_staggered.argtypes = [P, ctypes.POINTER(P), I, I, IP, P]
+    L.igg_update_halo_fields.argtypes = [P, ctypes.POINTER(P), IP, I, I, P]
     L.igg_step.argtypes = [P, P, P, P, I, D, D, D, D, D, P]
     L.igg_step_hidden.argtypes = [P, IP, P, P, P, I, D, D, D, D, D, P]
     L.igg_run.argtypes = [P, I, IP, P, P, P, I, D, D, D, D, D, P]
@@ -67,7 +68,7 @@ def lib():
     L.igg_grid_set_option.argtypes = [P, I, I]
     for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
                  "igg_grid_shape", "igg_subdomain_info", "igg_update_halo",
-                 "igg_update_halo_staggered", "igg_step",
+                 "igg_update_halo_staggered", "igg_update_halo_fields", "igg_step",
                  "igg_step_hidden", "igg_run", "igg_reduce", "igg_device_status",
                  "igg_grid_set_option"):
         getattr(L, name).restype = I
@@ -220,6 +221,19 @@ class Grid:
         arr = (ctypes.c_void_p * len(fields))(*[_ptr(f, npts, dt, "field").value for f in fields])
         _check(lib().igg_update_halo_staggered(self._handle(), arr, len(fields), dtype_code(dt),
                                                _ints(nf), _stream(stream)))
+
+    def update_halo_fields(self, fields, sizes, stream=None):
+        """update_halo!(A...) on fields of possibly different staggered local
+        sizes (sizes[i] = (nx, ny, nz) of fields[i]), one launch per dimension."""
+        if not fields:
+            return
+        dt = fields[0].dtype
+        ptrs = [_ptr(f, self.nsub * int(s[0]) * int(s[1]) * int(s[2]), dt, "field").value
+                for f, s in zip(fields, sizes)]
+        arr = (ctypes.c_void_p * len(fields))(*ptrs)
+        flat = (ctypes.c_int * (3 * len(fields)))(*[int(v) for s in sizes for v in s])
+        _check(lib().igg_update_halo_fields(self._handle(), arr, flat, len(fields), dtype_code(dt),
+                                            _stream(stream)))
 
     def step(self, T2, T, Ci, lam, dt, dx, dy, dz, stream=None):
         """Fig. 1 step! on every subdomain (inner points of T2)."""

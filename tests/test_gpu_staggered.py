@@ -59,3 +59,26 @@ def test_staggered_sizes_rejected():
             t = torch.zeros(2 * nf[0] * nf[1] * nf[2], dtype=torch.float64, device="cuda")
             with pytest.raises(igg.IggError):
                 g.update_halo_staggered(nf, t)
+
+
+@pytest.mark.parametrize("n,dims,periods,overlap", [
+    ((8, 7, 6), (2, 2, 2), (0, 0, 0), (2, 2, 2)),
+    ((12, 9, 10), (2, 1, 3), (1, 1, 0), (2, 3, 2)),
+    ((6, 6, 6), (1, 1, 1), (1, 1, 1), (2, 2, 2)),
+])
+def test_fields_of_mixed_sizes_one_call(n, dims, periods, overlap):
+    """A staggered set (a cell field and the three face fields, sizes n and
+    n + e_d) updated in one call equals the oracle's update of each field."""
+    sizes = [tuple(n)] + [tuple(n[k] + (1 if k == d else 0) for k in range(3)) for d in range(3)]
+    nsub = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(5)
+    host = [rng.integers(0, 2**63, size=(nsub, s[2], s[1], s[0]), dtype=np.uint64) for s in sizes]
+    refs = [h.copy() for h in host]
+    for r in refs:
+        oracle.update_halo_staggered(r, n, dims, periods, overlap)
+    with igg.Grid(n, dims=dims, overlap=overlap, periods=periods) as g:
+        dev = [torch.from_numpy(h.view(np.int64)).cuda().view(torch.float64) for h in host]
+        g.update_halo_fields(dev, sizes)
+        torch.cuda.synchronize()
+        for d, r in zip(dev, refs):
+            assert np.array_equal(d.view(torch.int64).cpu().numpy().view(np.uint64), r)
