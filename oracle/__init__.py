@@ -85,6 +85,7 @@ def _load():
         lib.oracle_step_part.argtypes = [L, L, L, P, P, P, D, D, D, D, D, L, L, L, ctypes.c_int]
         lib.oracle_update_halo.argtypes = [ctypes.c_int, P, P, L, L, L, P, P, L]
         lib.oracle_adjoint_step.argtypes = [L, L, L, P, P, P, P, P, D, D, D, D, D]
+        lib.oracle_acoustic_step.argtypes = [L, L, L, P, P, P, P, D, D, D, D, D, D]
         lib.oracle_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -267,6 +268,44 @@ def update_halo_staggered(field: np.ndarray, n, dims, periods, overlap):
     if any(abs(nf[d] - int(n[d])) > 1 for d in range(3)):
         raise ValueError("a staggered field differs from the grid by at most one point")
     update_halo(field, dims, periods, staggered_overlap(n, nf, overlap))
+
+
+def acoustic_step(P, Vx, Vy, Vz, rho, K, dt, dx, dy, dz):
+    """One leapfrog step of staggered-grid acoustics on one array (see
+    oracle.c): P [nz][ny][nx], Vx [nz][ny][nx+1], Vy [nz][ny+1][nx],
+    Vz [nz+1][ny][nx], all updated in place."""
+    nz, ny, nx = P.shape
+    for a, shape in ((P, (nz, ny, nx)), (Vx, (nz, ny, nx + 1)), (Vy, (nz, ny + 1, nx)),
+                     (Vz, (nz + 1, ny, nx))):
+        _check3(a)
+        if a.shape != shape:
+            raise ValueError(f"field shape {a.shape}, expected {shape}")
+    _load().oracle_acoustic_step(nx, ny, nz, _ptr(P), _ptr(Vx), _ptr(Vy), _ptr(Vz), rho, K, dt,
+                                 dx, dy, dz)
+
+
+def acoustic_run_decomposed(P, Vx, Vy, Vz, nt, rho, K, dt, dx, dy, dz, n, dims, periods,
+                            overlap):
+    """nt acoustic steps on a decomposed grid (local cell size n, fields
+    [nsub][...] in place): every subdomain steps, then update_halo! of P, Vx,
+    Vy, Vz with their staggered overlaps."""
+    for _ in range(nt):
+        for s in range(P.shape[0]):
+            acoustic_step(P[s], Vx[s], Vy[s], Vz[s], rho, K, dt, dx, dy, dz)
+        for f in (P, Vx, Vy, Vz):
+            update_halo_staggered(f, n, dims, periods, overlap)
+
+
+def acoustic_energy(P_prev, P, Vx, Vy, Vz, rho, K, dx, dy, dz):
+    """Energy of the leapfrog scheme between two consecutive steps on one
+    array: (sum P_prev*P/(2K) + rho/2 sum |V|^2) * cell volume, with P_prev
+    the cell field before and P, V the fields after a step (fsum). With zero
+    velocities on the walls the discrete divergence is minus the transpose of
+    the discrete gradient, and this quantity is the same after every step."""
+    terms = [float(x) for x in (P_prev * P).ravel() / (2.0 * K)]
+    for v in (Vx, Vy, Vz):
+        terms += [float(x) for x in (0.5 * rho * v * v).ravel()]
+    return math.fsum(terms) * (dx * dy * dz)
 
 
 def adjoint_step(lam_out, lam_in, Tn, Ci, gCi, lam, dt, dx, dy, dz):

@@ -188,6 +188,58 @@ void oracle_adjoint_step(long nx, long ny, long nz, double *lam_out,
 }
 
 /* Number of OpenMP threads the loops above use (1 without OpenMP). */
+/* One leapfrog step of linear acoustics on a staggered grid: the multi-field
+ * staggered stencil that exercises update_halo! on fields of different sizes
+ * (the paper's grids are regular staggered grids, Sec. Approach; it prints no
+ * such solver, so the scheme is the textbook one, stated here).
+ * P is a cell field [nz][ny][nx]; the face fields are Vx [nz][ny][nx+1],
+ * Vy [nz][ny+1][nx], Vz [nz+1][ny][nx], face index i lying between cells i-1
+ * and i. With rho (density) and K (bulk modulus):
+ *   1. Vx[k][j][i] -= dt/rho*(P[k][j][i] - P[k][j][i-1])/dx for faces
+ *      i = 1..nx-1 and all j, k (likewise Vy over j = 1..ny-1, Vz over
+ *      k = 1..nz-1): the outermost faces (walls) are never written;
+ *   2. P[k][j][i] -= dt*K*((Vx[k][j][i+1] - Vx[k][j][i])/dx
+ *                         + (Vy[k][j+1][i] - Vy[k][j][i])/dy
+ *                         + (Vz[k+1][j][i] - Vz[k][j][i])/dz) on every cell,
+ * with the new velocities. Each expression is evaluated left to right. */
+void oracle_acoustic_step(long nx, long ny, long nz, double *P, double *Vx, double *Vy,
+                          double *Vz, double rho, double K, double dt, double dx, double dy,
+                          double dz) {
+#define PI(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+#define VXI(i, j, k) ((size_t)(i) + (size_t)(nx + 1) * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+#define VYI(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)(ny + 1) * (size_t)(k)))
+#define VZI(i, j, k) ((size_t)(i) + (size_t)nx * ((size_t)(j) + (size_t)ny * (size_t)(k)))
+  long i, j, k;
+#pragma omp parallel for private(i, j)
+  for (k = 0; k < nz; ++k)
+    for (j = 0; j < ny; ++j)
+      for (i = 1; i < nx; ++i)
+        Vx[VXI(i, j, k)] = Vx[VXI(i, j, k)] - dt / rho * (P[PI(i, j, k)] - P[PI(i - 1, j, k)]) / dx;
+#pragma omp parallel for private(i, j)
+  for (k = 0; k < nz; ++k)
+    for (j = 1; j < ny; ++j)
+      for (i = 0; i < nx; ++i)
+        Vy[VYI(i, j, k)] = Vy[VYI(i, j, k)] - dt / rho * (P[PI(i, j, k)] - P[PI(i, j - 1, k)]) / dy;
+#pragma omp parallel for private(i, j)
+  for (k = 1; k < nz; ++k)
+    for (j = 0; j < ny; ++j)
+      for (i = 0; i < nx; ++i)
+        Vz[VZI(i, j, k)] = Vz[VZI(i, j, k)] - dt / rho * (P[PI(i, j, k)] - P[PI(i, j, k - 1)]) / dz;
+#pragma omp parallel for private(i, j)
+  for (k = 0; k < nz; ++k)
+    for (j = 0; j < ny; ++j)
+      for (i = 0; i < nx; ++i)
+        P[PI(i, j, k)] = P[PI(i, j, k)] -
+                         dt * K *
+                             ((Vx[VXI(i + 1, j, k)] - Vx[VXI(i, j, k)]) / dx +
+                              (Vy[VYI(i, j + 1, k)] - Vy[VYI(i, j, k)]) / dy +
+                              (Vz[VZI(i, j, k + 1)] - Vz[VZI(i, j, k)]) / dz);
+#undef PI
+#undef VXI
+#undef VYI
+#undef VZI
+}
+
 int oracle_threads(void) {
 #ifdef _OPENMP
   int n = 1;
