@@ -225,6 +225,26 @@ int igg_run(igg_grid *grid, int nt, const int widths[3], void *T, void *T2,
             double dy, double dz, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Staggered-grid acoustics: a multi-field stencil on the grid's regular
+ * staggered layout (Sec. Approach), with fields of different sizes per
+ * subdomain: P at cells [nsub][nz][ny][nx], Vx at x faces
+ * [nsub][nz][ny][nx+1], Vy [nsub][nz][ny+1][nx], Vz [nsub][nz+1][ny][nx].
+ * One leapfrog step, in this order:
+ *   Vx[i] -= dt/rho*(P[i] - P[i-1])/dx on faces i = 1..nx-1 (all y, z), and
+ *   likewise Vy, Vz (the outermost faces are never written: walls, or halo
+ *   faces that the halo update fills);
+ *   P -= dt*K*((Vx[i+1]-Vx[i])/dx + (Vy[j+1]-Vy[j])/dy + (Vz[k+1]-Vz[k])/dz)
+ *   on every cell, with the new velocities;
+ * then, if with_halo, update_halo!(P, Vx, Vy, Vz) as igg_update_halo_fields
+ * (overlaps o for P and o+1 for each face field in its own dimension). dtype
+ * F64 or F32. Coefficients dt/(rho*dd) and dt*K/dd are formed in FP64; the
+ * kernels use FMAs (results within rounding of the left-to-right formula).
+ * ------------------------------------------------------------------------- */
+int igg_acoustic_step(igg_grid *grid, void *P, void *Vx, void *Vy, void *Vz,
+                      igg_dtype dtype, double rho, double K, double dt, double dx,
+                      double dy, double dz, int with_halo, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched form: nprob independent diffusion problems of uneven sizes (each
  * Fig. 1's step! on one array with fixed boundary values, its own lam, dt,
  * dx, dy, dz), advanced together by ONE persistent kernel launch per step.

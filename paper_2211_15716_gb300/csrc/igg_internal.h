@@ -161,6 +161,15 @@ cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, 
                                long long nzt, const Coef &c, unsigned *dev_err,
                                FixBuf fix, const HaloSend &send, cudaStream_t s);
 
+// Staggered-grid acoustics (acoustic.cu): coefficients dt/(rho dd) of the
+// velocity update and dt K/dd of the pressure update, formed on the host in
+// FP64; one step (velocities, then pressure) on every subdomain.
+struct AcCoef {
+  double ax, ay, az, bx, by, bz;
+};
+cudaError_t launch_acoustic(igg_dtype dt, int nsub, int nx, int ny, int nz, void *P, void *Vx,
+                            void *Vy, void *Vz, const AcCoef &c, cudaStream_t s);
+
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.
 // The copies of one dimension of up to kMaxHaloJobs fields in one launch

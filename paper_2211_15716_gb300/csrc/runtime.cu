@@ -985,6 +985,34 @@ int igg_update_halo_fields(igg_grid *g, void *const fields[], const int *sizes, 
   return enqueue_halo_fields(g, fields, sizes, nfields, dtype_size(dt), (cudaStream_t)stream);
 }
 
+int igg_acoustic_step(igg_grid *g, void *P, void *Vx, void *Vy, void *Vz, igg_dtype dt,
+                      double rho, double K, double dtime, double dx, double dy, double dz,
+                      int with_halo, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "acoustics: F64 or F32 only");
+  for (void *f : {P, Vx, Vy, Vz})
+    if (int rc = check_field(g, f, "field")) return rc;
+  if (!(rho > 0) || !(K > 0) || !(dx > 0) || !(dy > 0) || !(dz > 0) || !(dtime == dtime))
+    return set_error(IGG_EINVAL, "acoustics: rho, K and spacings must be positive, dt a number");
+  DeviceGuard dg(g->device);
+  AcCoef c;
+  c.ax = dtime / rho / dx;
+  c.ay = dtime / rho / dy;
+  c.az = dtime / rho / dz;
+  c.bx = dtime * K / dx;
+  c.by = dtime * K / dy;
+  c.bz = dtime * K / dz;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_acoustic(dt, g->nsub, g->n[0], g->n[1], g->n[2], P, Vx, Vy, Vz, c, s);
+  if (e != cudaSuccess) return cuda_error(e, "acoustic launch");
+  if (!with_halo) return IGG_OK;
+  void *const fields[4] = {P, Vx, Vy, Vz};
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const int sizes[12] = {nx, ny, nz, nx + 1, ny, nz, nx, ny + 1, nz, nx, ny, nz + 1};
+  return enqueue_halo_fields(g, fields, sizes, 4, dtype_size(dt), s);
+}
+
 int igg_step(igg_grid *g, void *T2, const void *T, const void *Ci, igg_dtype dt, double lam,
              double dtime, double dx, double dy, double dz, void *stream) {
   clear_error();

@@ -60,6 +60,7 @@ def lib():
     L.igg_update_halo.argtypes = [P, ctypes.POINTER(P), I, I, P]
     L.igg_update_halo_staggered.argtypes = [P, ctypes.POINTER(P), I, I, IP, P]
     L.igg_update_halo_fields.argtypes = [P, ctypes.POINTER(P), IP, I, I, P]
+    L.igg_acoustic_step.argtypes = [P, P, P, P, P, I, D, D, D, D, D, D, I, P]
     L.igg_step.argtypes = [P, P, P, P, I, D, D, D, D, D, P]
     L.igg_step_hidden.argtypes = [P, IP, P, P, P, I, D, D, D, D, D, P]
     L.igg_run.argtypes = [P, I, IP, P, P, P, I, D, D, D, D, D, P]
@@ -68,7 +69,8 @@ def lib():
     L.igg_grid_set_option.argtypes = [P, I, I]
     for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
                  "igg_grid_shape", "igg_subdomain_info", "igg_update_halo",
-                 "igg_update_halo_staggered", "igg_update_halo_fields", "igg_step",
+                 "igg_update_halo_staggered", "igg_update_halo_fields",
+                 "igg_acoustic_step", "igg_step",
                  "igg_step_hidden", "igg_run", "igg_reduce", "igg_device_status",
                  "igg_grid_set_option"):
         getattr(L, name).restype = I
@@ -234,6 +236,23 @@ class Grid:
         flat = (ctypes.c_int * (3 * len(fields)))(*[int(v) for s in sizes for v in s])
         _check(lib().igg_update_halo_fields(self._handle(), arr, flat, len(fields), dtype_code(dt),
                                             _stream(stream)))
+
+    def acoustic_fields(self, dtype=torch.float64):
+        """Zeroed P, Vx, Vy, Vz of the staggered acoustic layout."""
+        nx, ny, nz = self.n
+        shp = [(nz, ny, nx), (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)]
+        return [torch.zeros((self.nsub,) + s, dtype=dtype, device="cuda") for s in shp]
+
+    def acoustic_step(self, P, Vx, Vy, Vz, rho, K, dt, dx, dy, dz, halo=True, stream=None):
+        """One leapfrog step of staggered-grid acoustics (igg_acoustic_step)."""
+        nx, ny, nz = self.n
+        d = P.dtype
+        ptrs = [_ptr(f, self.nsub * a * b * c, d, name) for f, (a, b, c), name in
+                ((P, (nx, ny, nz), "P"), (Vx, (nx + 1, ny, nz), "Vx"), (Vy, (nx, ny + 1, nz), "Vy"),
+                 (Vz, (nx, ny, nz + 1), "Vz"))]
+        _check(lib().igg_acoustic_step(self._handle(), *ptrs, dtype_code(d), float(rho), float(K),
+                                       float(dt), float(dx), float(dy), float(dz), int(bool(halo)),
+                                       _stream(stream)))
 
     def step(self, T2, T, Ci, lam, dt, dx, dy, dz, stream=None):
         """Fig. 1 step! on every subdomain (inner points of T2)."""
