@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -280,8 +281,8 @@ def form_precision(steps):
 
 
 def form_batched(steps):
-    """256 independent FP32 problems, dims uniform on {32..192}: one
-    persistent launch per step, CUDA-graph loop, autotuned tiling."""
+    """256 independent FP32 problems, dims uniform on {32..192}: one launch
+    per step, CUDA-graph loop, autotuned kernel and tiling."""
     import oracle
     import synth
     import paper_2211_15716_gb300 as igg
@@ -370,12 +371,40 @@ def form_adjoint():
     return out
 
 
+def form_acoustic(steps):
+    """Staggered-grid acoustics on 2x2x2 subdomains of 256^3 cells (cell P,
+    three face fields one point longer), FP64 and FP32: ms per step with the
+    halo update of all four fields, and T_eff over the 12 field passes of a
+    step (velocities: read P, read and write Vx, Vy, Vz; pressure: read Vx,
+    Vy, Vz, read and write P)."""
+    import paper_2211_15716_gb300 as igg
+    n, dims = (256, 256, 256), (2, 2, 2)
+    rho, K, h = 1.0, 2.0, (1 / 511, 1 / 511, 1 / 511)
+    dt = 0.3 * h[0] / math.sqrt(K / rho)
+    out = {"form": "acoustic", "workload": "2x2x2 x 256^3 cells, staggered P, Vx, Vy, Vz, walls"}
+    with igg.Grid(n, dims=dims, overlap=(2, 2, 2)) as g:
+        cells = g.nsub * n[0] * n[1] * n[2]
+        for dtype, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+            P, Vx, Vy, Vz = g.acoustic_fields(dtype)
+            P.uniform_(-0.5, 0.5)
+            step = lambda: g.acoustic_step(P, Vx, Vy, Vz, rho, K, dt, *h)  # noqa: E731
+            for _ in range(3):
+                step()
+            ms = _timed(lambda: [step() for _ in range(steps)], 1) / steps
+            s = P.element_size()
+            out[name] = {"ms_per_step": round(ms, 4),
+                         "T_eff_GB_s": round(12 * cells * s / (ms * 1e-3) / 1e9, 1),
+                         "cell_updates_per_s": cells / (ms * 1e-3)}
+            del P, Vx, Vy, Vz
+    return out
+
+
 def run_forms(args):
     import paper_2211_15716_gb300  # noqa: F401
     from paper_2211_15716_gb300 import build as igg_build
     igg_build.build()
     for fn in (lambda: form_precision(max(20, args.steps // 5)), lambda: form_batched(max(20, args.steps)),
-               form_adjoint):
+               form_adjoint, lambda: form_acoustic(max(20, args.steps // 5))):
         print(json.dumps(fn()), flush=True)
         torch.cuda.empty_cache()
     return 0
