@@ -154,8 +154,14 @@ def dims_create(nsub: int, dims=(0, 0, 0)) -> tuple:
 def global_size(n, dims, overlap, periods) -> tuple:
     """n_g per dimension: dims*(n-o) + o for a non-periodic dimension and
     dims*(n-o) for a periodic one (reading of the implicit global grid: the
-    last o planes of a subdomain coincide with the first o of the next)."""
-    return tuple(dims[d] * (n[d] - overlap[d]) + (0 if periods[d] else overlap[d])
+    last o planes of a subdomain coincide with the first o of the next). A
+    dimension of size 1 is absent (2-D and 1-D grids): one subdomain, not
+    periodic, n_g = 1."""
+    for d in range(3):
+        if n[d] == 1 and (dims[d] != 1 or periods[d]):
+            raise ValueError("a dimension of size 1 needs dims 1 and no periodicity")
+    return tuple(1 if n[d] == 1 else
+                 dims[d] * (n[d] - overlap[d]) + (0 if periods[d] else overlap[d])
                  for d in range(3))
 
 
@@ -196,6 +202,8 @@ def global_indices(n, dims, overlap, periods, sub: int):
     out = []
     for d in range(3):
         g = c[d] * (n[d] - overlap[d]) + np.arange(n[d], dtype=np.int64)
+        if n[d] == 1:
+            g = np.zeros(1, dtype=np.int64)
         if periods[d]:
             g = g % ng[d]
         out.append(g)
@@ -206,12 +214,14 @@ def undecomposed_index(n, dims, overlap, sub: int):
     """Per axis, the index in the undecomposed array (extent n_g, or n_g + o
     for a periodic dimension) of each local point of subdomain `sub`."""
     c = coords(sub, dims)
-    return [c[d] * (n[d] - overlap[d]) + np.arange(n[d], dtype=np.int64) for d in range(3)]
+    return [np.zeros(1, dtype=np.int64) if n[d] == 1 else
+            c[d] * (n[d] - overlap[d]) + np.arange(n[d], dtype=np.int64) for d in range(3)]
 
 
 def spacing(l: float, n_g: int) -> float:
-    """Fig. 1: dx = lx/(nx_g()-1)."""
-    return l / (n_g - 1)
+    """Fig. 1: dx = lx/(nx_g()-1); +inf for an absent dimension (n_g = 1), whose
+    term d2/dd^2 is then 0."""
+    return math.inf if n_g == 1 else l / (n_g - 1)
 
 
 def cfl_dt(dx: float, dy: float, dz: float, lam: float, ci_max: float) -> float:

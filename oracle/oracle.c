@@ -51,6 +51,12 @@ static double lap_cell(const double *T, size_t p, size_t sx, size_t sy,
   return ((d2x / (dx * dx)) + (d2y / (dy * dy))) + (d2z / (dz * dz));
 }
 
+/* A dimension of size 1 is absent (a 2-D or 1-D grid): its only index counts
+ * as inner and its neighbour stride is 0, so its second difference is exactly
+ * 0 (with an infinite spacing its term d2/(dd*dd) is 0 as well). */
+#define LO(n) ((n) > 1 ? 1L : 0L)
+#define HI(n) ((n) > 1 ? (n) - 1 : 1L)
+
 /* Fig. 1 step! on one local array: every inner point (index 1..n-2 in each
  * dimension, 0-based) of T2 is written; points on the array boundary are not
  * touched (they keep whatever T2 holds, which is how Fig. 1's T2 = copy(T)
@@ -58,11 +64,12 @@ static double lap_cell(const double *T, size_t p, size_t sx, size_t sy,
 void oracle_step(long nx, long ny, long nz, double *T2, const double *T,
                  const double *Ci, double lam, double dt, double dx, double dy,
                  double dz) {
-  const size_t sx = 1, sy = (size_t)nx, sz = (size_t)nx * (size_t)ny;
+  const size_t sx = nx > 1 ? 1 : 0, sy = ny > 1 ? (size_t)nx : 0,
+               sz = nz > 1 ? (size_t)nx * (size_t)ny : 0;
 #pragma omp parallel for schedule(static)
-  for (long iz = 1; iz < nz - 1; ++iz)
-    for (long iy = 1; iy < ny - 1; ++iy)
-      for (long ix = 1; ix < nx - 1; ++ix) {
+  for (long iz = LO(nz); iz < HI(nz); ++iz)
+    for (long iy = LO(ny); iy < HI(ny); ++iy)
+      for (long ix = LO(nx); ix < HI(nx); ++ix) {
         size_t p = AT(ix, iy, iz);
         T2[p] = step_cell(T, Ci, p, sx, sy, sz, lam, dt, dx, dy, dz);
       }
@@ -76,19 +83,21 @@ void oracle_step(long nx, long ny, long nz, double *T2, const double *T,
  * i >= n - w + 1 in at least one dimension, w the width of that dimension.
  * Inner block: all other inner points. */
 static int in_boundary_set(long i, long n, long w) {
-  /* 0-based i; 1-based i+1 <= w  or  i+1 >= n-w+1 */
-  return (i + 1 <= w) || (i + 1 >= n - w + 1);
+  /* 0-based i; 1-based i+1 <= w  or  i+1 >= n-w+1; an absent dimension
+   * (n = 1) has no boundary slab */
+  return n > 1 && ((i + 1 <= w) || (i + 1 >= n - w + 1));
 }
 
 void oracle_step_part(long nx, long ny, long nz, double *T2, const double *T,
                       const double *Ci, double lam, double dt, double dx,
                       double dy, double dz, long bx, long by, long bz,
                       int select) {
-  const size_t sx = 1, sy = (size_t)nx, sz = (size_t)nx * (size_t)ny;
+  const size_t sx = nx > 1 ? 1 : 0, sy = ny > 1 ? (size_t)nx : 0,
+               sz = nz > 1 ? (size_t)nx * (size_t)ny : 0;
 #pragma omp parallel for schedule(static)
-  for (long iz = 1; iz < nz - 1; ++iz)
-    for (long iy = 1; iy < ny - 1; ++iy)
-      for (long ix = 1; ix < nx - 1; ++ix) {
+  for (long iz = LO(nz); iz < HI(nz); ++iz)
+    for (long iy = LO(ny); iy < HI(ny); ++iy)
+      for (long ix = LO(nx); ix < HI(nx); ++ix) {
         int b = in_boundary_set(ix, nx, bx) || in_boundary_set(iy, ny, by) ||
                 in_boundary_set(iz, nz, bz);
         if (b != select) continue;
@@ -119,7 +128,7 @@ void oracle_update_halo(int nsub, const int *left_nb, const int *right_nb,
   const size_t es = (size_t)elem_size;
   for (int d = 0; d < 3; ++d) {
     const long o = overlap[d];
-    if (o < 2) continue;
+    if (o < 2 || n[d] < 2) continue; /* staggered overlap 1, or an absent dimension */
     for (int s = 0; s < nsub; ++s) {
       for (int side = 0; side < 2; ++side) {
         int nb = side == 0 ? left_nb[3 * s + d] : right_nb[3 * s + d];

@@ -87,9 +87,11 @@ def global_linear_index(gx, gy, gz, n_g) -> np.ndarray:
 
 
 def _coords(gx, gy, gz, n_g, l):
-    x = np.asarray(gx, dtype=np.float64) * (l[0] / (n_g[0] - 1))
-    y = np.asarray(gy, dtype=np.float64) * (l[1] / (n_g[1] - 1))
-    z = np.asarray(gz, dtype=np.float64) * (l[2] / (n_g[2] - 1))
+    # an absent dimension (n_g = 1, 2-D and 1-D grids) sits at the centre
+    def c(g, n, ll):
+        g = np.asarray(g, dtype=np.float64)
+        return np.full(g.shape, 0.5 * ll) if n == 1 else g * (ll / (n - 1))
+    x, y, z = c(gx, n_g[0], l[0]), c(gy, n_g[1], l[1]), c(gz, n_g[2], l[2])
     return x[None, None, :], y[None, :, None], z[:, None, None]
 
 
