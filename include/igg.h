@@ -83,6 +83,13 @@ int igg_abi_version(void);
  * Global size per dimension: n_g = dims*(n - o) + o, or dims*(n - o) when
  * periodic. Requires n >= 3 and 2 <= o <= n - 1 per dimension, so that both
  * send planes (indices o-1 and n-o) are inner points.
+ * 2-D and 1-D grids: ny = 1 and/or nz = 1 makes that dimension absent (its
+ * dims entry 1 or free, not periodic, n_g = 1): its only index counts as
+ * inner, it has no neighbours, no halo and no second difference (pass an
+ * infinite spacing, whose weight dt*lam/dd^2 is then exactly 0). Steps on
+ * such grids run the vector or scalar kernels; the hidden step runs as the
+ * plain step followed by the halo update (same result). The adjoint and the
+ * acoustic step need a 3-D grid.
  * Creates the library's high- and low-priority streams and events.
  * On success *out owns the grid; release it with igg_finalize_global_grid.
  * ------------------------------------------------------------------------- */

@@ -396,7 +396,25 @@ int check_coef(double lam, double dt, double dx, double dy, double dz) {
 
 // The TMA kernel takes the regular boxes (full step, inner block) of grids
 // whose rows are 16-byte multiples, unless disabled on the grid.
-bool use_tma(const igg_grid *g, int V) { return V > 1 && g->tma_enabled && tma_available(); }
+// A dimension of size 1 is absent (2-D and 1-D grids): its only index is
+// inner, its neighbour stride 0 (zero second difference), its weight 0.
+bool low_dim(const igg_grid *g) { return g->n[1] == 1 || g->n[2] == 1; }
+int lo_in(int n) { return n > 1 ? 1 : 0; }
+int hi_in(int n) { return n > 1 ? n - 1 : 1; }
+
+// Zero neighbour strides of absent dimensions in vector tiles (rows along y
+// and march along z, or swapped).
+void zero_absent_strides(const igg_grid *g, std::vector<VTile> &v) {
+  for (VTile &t : v) {
+    const bool ya = g->n[1] == 1, za = g->n[2] == 1;
+    if (t.swap ? za : ya) t.sr = 0;
+    if (t.swap ? ya : za) t.sm = 0;
+  }
+}
+
+bool use_tma(const igg_grid *g, int V) {
+  return V > 1 && g->tma_enabled && tma_available() && !low_dim(g);
+}
 
 // Vector width used for dtype dt on this grid (1 = scalar kernel): the
 // 16-byte vector kernel needs rows of a multiple of V points.
@@ -413,8 +431,8 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
     return IGG_OK;
   }
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-  const long long xy = xy_tiles_of(1, nx - 1, 1, ny - 1) * g->nsub;
-  const int zb = choose_zb(xy, nz - 2);
+  const long long xy = xy_tiles_of(1, nx - 1, lo_in(ny), hi_in(ny)) * g->nsub;
+  const int zb = choose_zb(xy, hi_in(nz) - lo_in(nz));
   TileLists v;
   const bool tma = use_tma(g, V);
   const int Wt = tma ? tma_tile_width(dtype_of_vec(V), TMA_WIDE) : 0;
@@ -427,8 +445,10 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
       add_box_tma(v.tma, (long long)s * g->nloc, (long long)s * nz, 1, nx - 1, 1, ny - 1, 1, nz - 1,
                   zbt, V, Wt, Ht);
     else
-      add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, 1, ny - 1, 1, nz - 1, zb, 0);
+      add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, lo_in(ny), hi_in(ny), lo_in(nz),
+                hi_in(nz), zb, 0);
   }
+  zero_absent_strides(g, v.vec);
   TileSet ts;
   if (int rc = upload_tiles(v, V, &ts, tma ? TMA_WIDE : -1)) return rc;
   *out = &g->full.emplace(V, ts).first->second;
@@ -688,6 +708,9 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   Coef c = c0;
   c.f64_emu = g->f64_emu;
   const int V = grid_vec(g, dt);
+  // 2-D and 1-D grids: the hidden step runs as the plain step and the halo
+  // update (same result; no boundary/inner split of an absent dimension)
+  if (low_dim(g)) widths = nullptr;
   if (!widths) {
     TileSet *full = nullptr;
     if (int rc = build_full_tiles(g, V, &full)) return rc;
@@ -730,6 +753,7 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
 int check_widths(const igg_grid *g, const int *w) {
   if (!w) return IGG_OK;
   for (int d = 0; d < 3; ++d) {
+    if (g->n[d] == 1) continue;  // absent dimension
     if (w[d] < g->overlap[d])
       return set_error(IGG_EINVAL, "widths[%d]=%d is smaller than overlap %d", d, w[d],
                        g->overlap[d]);
@@ -785,6 +809,13 @@ int igg_init_global_grid(int nx, int ny, int nz, const int dims_in[3], int nsub,
   if (periods)
     for (int d = 0; d < 3; ++d) per[d] = periods[d] ? 1 : 0;
   for (int d = 0; d < 3; ++d) {
+    if (n[d] == 1 && d > 0) {
+      // an absent dimension (2-D and 1-D grids): one subdomain, not periodic
+      if (dims[d] > 1) return set_error(IGG_EINVAL, "dims[%d]=%d for a dimension of size 1", d, dims[d]);
+      if (per[d]) return set_error(IGG_EINVAL, "a dimension of size 1 cannot be periodic");
+      dims[d] = 1;
+      continue;
+    }
     if (n[d] < 3) return set_error(IGG_EINVAL, "local size n[%d]=%d < 3", d, n[d]);
     if (o[d] < 2 || o[d] > n[d] - 1)
       return set_error(IGG_EINVAL, "overlap[%d]=%d outside [2, n-1]", d, o[d]);
@@ -812,7 +843,7 @@ int igg_init_global_grid(int nx, int ny, int nz, const int dims_in[3], int nsub,
     g->dims[d] = dims[d];
     g->overlap[d] = o[d];
     g->periods[d] = per[d];
-    g->ng[d] = dims[d] * (n[d] - o[d]) + (per[d] ? 0 : o[d]);
+    g->ng[d] = n[d] == 1 ? 1 : dims[d] * (n[d] - o[d]) + (per[d] ? 0 : o[d]);
   }
   g->nsub = dims[0] * dims[1] * dims[2];
   g->nloc = nloc;
@@ -991,6 +1022,7 @@ int igg_acoustic_step(igg_grid *g, void *P, void *Vx, void *Vy, void *Vz, igg_dt
   clear_error();
   if (int rc = check_grid(g)) return rc;
   if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "acoustics: F64 or F32 only");
+  if (low_dim(g)) return set_error(IGG_EINVAL, "acoustics: needs a 3-D grid");
   for (void *f : {P, Vx, Vy, Vz})
     if (int rc = check_field(g, f, "field")) return rc;
   if (!(rho > 0) || !(K > 0) || !(dx > 0) || !(dy > 0) || !(dz > 0) || !(dtime == dtime))
@@ -1067,7 +1099,7 @@ int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const v
   if (nt >= 2) {
     // tile tables are allocated before the capture starts
     const int V = grid_vec(g, dt);
-    if (widths && !use_fused_halo(g, V)) {
+    if (widths && !use_fused_halo(g, V) && !low_dim(g)) {
       SplitTiles *st = nullptr;
       if (int rc = build_split_tiles(g, widths, V, &st)) return rc;
     } else {
@@ -1140,6 +1172,7 @@ int igg_reduce(int op, const void *a, const void *b, size_t n, igg_dtype dt, dou
 // grid; drivers with checkpoints every `every` steps.
 // ---------------------------------------------------------------------------
 static int check_adjoint_grid(const igg_grid *g, igg_dtype dt) {
+  if (low_dim(g)) return set_error(IGG_EINVAL, "the adjoint needs a 3-D grid");
   if (g->nsub != 1 || g->periods[0] || g->periods[1] || g->periods[2])
     return set_error(IGG_EINVAL, "the adjoint needs a single non-periodic subdomain");
   if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "adjoint dtype must be F64 or F32");

@@ -37,8 +37,10 @@ __device__ __forceinline__ void sweep_tile(const Tile &t, int tx, int ty, S *__r
   const int x = t.x0 + tx;
   const int y = t.y0 + ty;
   if (x >= t.xe || y >= t.ye) return;
-  const long long sy = t.nx;
-  const long long sz = (long long)t.nx * t.ny;
+  // absent dimensions (2-D and 1-D grids: ny = 1, or z range [0, 1)) have a
+  // zero neighbour stride
+  const long long sy = t.ny > 1 ? t.nx : 0;
+  const long long sz = t.z0 > 0 ? (long long)t.nx * t.ny : 0;
   long long p = t.base + x + sy * y + sz * (t.z0 - 1);
   C zm = N::ld(T + p);
   C zc = N::ld(T + p + sz);

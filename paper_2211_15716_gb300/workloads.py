@@ -24,8 +24,9 @@ from .igg import RED_MAX, Grid, reduce
 
 
 def spacing(l: float, n_g: int) -> float:
-    """Fig. 1: dx = lx/(nx_g()-1)."""
-    return l / (n_g - 1)
+    """Fig. 1: dx = lx/(nx_g()-1); +inf for an absent dimension (n_g = 1) of a
+    2-D or 1-D grid, whose weight dt*lam/dx^2 is then 0."""
+    return float("inf") if n_g == 1 else l / (n_g - 1)
 
 
 def cfl_dt(dx: float, dy: float, dz: float, lam: float, ci_max: float) -> float:
