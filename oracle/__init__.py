@@ -86,6 +86,7 @@ def _load():
         lib.oracle_update_halo.argtypes = [ctypes.c_int, P, P, L, L, L, P, P, L]
         lib.oracle_adjoint_step.argtypes = [L, L, L, P, P, P, P, P, D, D, D, D, D]
         lib.oracle_acoustic_step.argtypes = [L, L, L, P, P, P, P, D, D, D, D, D, D]
+        lib.oracle_gp_half.argtypes = [L, L, L, ctypes.c_int, P, P, P, D, D, D, D, D]
         lib.oracle_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -316,6 +317,39 @@ def acoustic_energy(P_prev, P, Vx, Vy, Vz, rho, K, dx, dy, dz):
     for v in (Vx, Vy, Vz):
         terms += [float(x) for x in (0.5 * rho * v * v).ravel()]
     return math.fsum(terms) * (dx * dy * dz)
+
+
+def gp_half(which, u, v, V, g, dt, dx, dy, dz):
+    """One half step of the Gross-Pitaevskii solver on one array (see
+    oracle.c): which 0 updates u from v, which 1 updates v from u."""
+    for a in (u, v, V):
+        _check3(a)
+    nz, ny, nx = u.shape
+    _load().oracle_gp_half(nx, ny, nz, int(which), _ptr(u), _ptr(v), _ptr(V), g, dt, dx, dy, dz)
+
+
+def gp_run(u, v, V, nt, g, dt, dx, dy, dz):
+    """nt steps (u half, then v half) on one array, in place."""
+    for _ in range(nt):
+        gp_half(0, u, v, V, g, dt, dx, dy, dz)
+        gp_half(1, u, v, V, g, dt, dx, dy, dz)
+
+
+def gp_run_decomposed(u, v, V, nt, g, dt, dx, dy, dz, dims, periods, overlap):
+    """nt steps on a decomposed grid ([nsub][nz][ny][nx] in place): every
+    subdomain's u half, update_halo!(u), every subdomain's v half,
+    update_halo!(v) (the v half reads the new u at halo points)."""
+    for _ in range(nt):
+        for which, f in ((0, u), (1, v)):
+            for s in range(u.shape[0]):
+                gp_half(which, u[s], v[s], V[s], g, dt, dx, dy, dz)
+            update_halo(f, dims, periods, overlap)
+
+
+def gp_invariant(u, v_prev, v):
+    """||u^n||^2 + <v^{n+1/2}, v^{n-1/2}> (fsum): with g = 0, zero boundary
+    values and a symmetric H, the same after every step."""
+    return math.fsum([float(x) for x in (u * u).ravel()] + [float(x) for x in (v * v_prev).ravel()])
 
 
 def adjoint_step(lam_out, lam_in, Tn, Ci, gCi, lam, dt, dx, dy, dz):

@@ -249,6 +249,41 @@ void oracle_acoustic_step(long nx, long ny, long nz, double *P, double *Vx, doub
 #undef VZI
 }
 
+/* Half steps of a Gross-Pitaevskii solver on one local array (a complex
+ * field psi = u + i v on the grid; the paper names a quantum-fluid solver of
+ * the nonlinear Gross-Pitaevskii equation as an application of the approach
+ * and prints no equations, so they are stated here):
+ *   i dpsi/dt = -1/2 lap(psi) + V psi + g |psi|^2 psi,
+ * i.e. du/dt = H v, dv/dt = -H u with H w = -1/2 lap(w) + (V + g (u^2 + v^2)) w.
+ * Staggered in time (u at whole steps, v at half steps):
+ *   which = 0:  u += dt * H(v)   with u^2 + v^2 from the current u and v,
+ *   which = 1:  v -= dt * H(u)   with the new u,
+ * on inner points only (psi fixed on the array boundary), lap the 7-point
+ * operator of step_cell. Each expression is evaluated left to right:
+ *   lap = ((d2x/(dx*dx) + d2y/(dy*dy)) + d2z/(dz*dz)),
+ *   h   = -0.5*lap + (V[p] + g*(u[p]*u[p] + v[p]*v[p]))*w[p],
+ *   out = out + dt*h  (which 0, out = u, w = v)  or  out - dt*h  (which 1,
+ *   out = v, w = u). */
+void oracle_gp_half(long nx, long ny, long nz, int which, double *u, double *v,
+                    const double *V, double g, double dt, double dx, double dy, double dz) {
+  const size_t sx = nx > 1 ? 1 : 0, sy = ny > 1 ? (size_t)nx : 0,
+               sz = nz > 1 ? (size_t)nx * (size_t)ny : 0;
+  double *out = which == 0 ? u : v;
+  const double *w = which == 0 ? v : u;
+#pragma omp parallel for schedule(static)
+  for (long iz = LO(nz); iz < HI(nz); ++iz)
+    for (long iy = LO(ny); iy < HI(ny); ++iy)
+      for (long ix = LO(nx); ix < HI(nx); ++ix) {
+        size_t p = AT(ix, iy, iz);
+        double d2x = (w[p + sx] - w[p]) - (w[p] - w[p - sx]);
+        double d2y = (w[p + sy] - w[p]) - (w[p] - w[p - sy]);
+        double d2z = (w[p + sz] - w[p]) - (w[p] - w[p - sz]);
+        double lap = ((d2x / (dx * dx)) + (d2y / (dy * dy))) + (d2z / (dz * dz));
+        double h = -0.5 * lap + (V[p] + g * (u[p] * u[p] + v[p] * v[p])) * w[p];
+        out[p] = which == 0 ? out[p] + dt * h : out[p] - dt * h;
+      }
+}
+
 int oracle_threads(void) {
 #ifdef _OPENMP
   int n = 1;
