@@ -252,6 +252,25 @@ int igg_acoustic_step(igg_grid *grid, void *P, void *Vx, void *Vy, void *Vz,
                       double dy, double dz, int with_halo, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Gross-Pitaevskii solver (the quantum-fluid application named in the
+ * paper's conclusion, which prints no equations; these are the library's):
+ *   i dpsi/dt = -1/2 lap(psi) + V psi + g |psi|^2 psi,  psi = u + i v,
+ * u and v real fields of the grid's layout (u at whole, v at half time
+ * steps), V a real potential of the same layout, psi fixed on each array's
+ * boundary. One step: u += dt*H(v) on inner points, update_halo!(u) if
+ * with_halo, v -= dt*H(u) with the new u, update_halo!(v) if with_halo,
+ * where H w = -1/2 lap(w) + (V + g*(u^2 + v^2)) w, the density taken from
+ * the values at hand (old u in the first half, new u in the second), lap the
+ * 7-point operator with spacings dx, dy, dz (+inf for an absent dimension).
+ * Stable for dt below 2 / (2 (1/dx^2 + 1/dy^2 + 1/dz^2) + max(V + g rho)).
+ * dtype F64 or F32; FMAs in the kernels (within rounding of the oracle's
+ * left-to-right evaluation).
+ * ------------------------------------------------------------------------- */
+int igg_gp_step(igg_grid *grid, void *u, void *v, const void *V, igg_dtype dtype,
+                double g, double dt, double dx, double dy, double dz, int with_halo,
+                void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched form: nprob independent diffusion problems of uneven sizes (each
  * Fig. 1's step! on one array with fixed boundary values, its own lam, dt,
  * dx, dy, dz), advanced together by ONE persistent kernel launch per step.

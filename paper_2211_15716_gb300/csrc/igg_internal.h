@@ -170,6 +170,14 @@ struct AcCoef {
 cudaError_t launch_acoustic(igg_dtype dt, int nsub, int nx, int ny, int nz, void *P, void *Vx,
                             void *Vy, void *Vz, const AcCoef &c, cudaStream_t s);
 
+// Gross-Pitaevskii half steps (gp.cu): kd = -dt/(2 dd^2) (0 for an absent
+// dimension), kc = -2 (kx + ky + kz), dt and g, formed on the host in FP64.
+struct GpCoef {
+  double kx, ky, kz, kc, dt, g;
+};
+cudaError_t launch_gp_half(igg_dtype dt, int which, int nsub, int nx, int ny, int nz, void *u,
+                           void *v, const void *V, const GpCoef &c, cudaStream_t s);
+
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.
 // The copies of one dimension of up to kMaxHaloJobs fields in one launch

@@ -1016,6 +1016,36 @@ int igg_update_halo_fields(igg_grid *g, void *const fields[], const int *sizes, 
   return enqueue_halo_fields(g, fields, sizes, nfields, dtype_size(dt), (cudaStream_t)stream);
 }
 
+int igg_gp_step(igg_grid *g, void *u, void *v, const void *V, igg_dtype dt, double gnl,
+                double dtime, double dx, double dy, double dz, int with_halo, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "Gross-Pitaevskii: F64 or F32 only");
+  for (const void *f : {(const void *)u, (const void *)v, V})
+    if (int rc = check_field(g, f, "field")) return rc;
+  if (u == v) return set_error(IGG_EINVAL, "u aliases v");
+  if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !(dtime == dtime) || !(gnl == gnl))
+    return set_error(IGG_EINVAL, "Gross-Pitaevskii: spacings must be positive, dt and g numbers");
+  DeviceGuard dg(g->device);
+  GpCoef c;
+  c.kx = -dtime / (2.0 * dx * dx);
+  c.ky = -dtime / (2.0 * dy * dy);
+  c.kz = -dtime / (2.0 * dz * dz);
+  c.kc = -2.0 * (c.kx + c.ky + c.kz);
+  c.dt = dtime;
+  c.g = gnl;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int which = 0; which < 2; ++which) {
+    cudaError_t e = launch_gp_half(dt, which, g->nsub, g->n[0], g->n[1], g->n[2], u, v, V, c, s);
+    if (e != cudaSuccess) return cuda_error(e, "Gross-Pitaevskii launch");
+    if (with_halo && any_halo(g)) {
+      e = enqueue_halo(g, which == 0 ? u : v, dtype_size(dt), s);
+      if (e != cudaSuccess) return cuda_error(e, "halo launch");
+    }
+  }
+  return IGG_OK;
+}
+
 int igg_acoustic_step(igg_grid *g, void *P, void *Vx, void *Vy, void *Vz, igg_dtype dt,
                       double rho, double K, double dtime, double dx, double dy, double dz,
                       int with_halo, void *stream) {

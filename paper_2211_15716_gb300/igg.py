@@ -61,6 +61,7 @@ def lib():
     L.igg_update_halo_staggered.argtypes = [P, ctypes.POINTER(P), I, I, IP, P]
     L.igg_update_halo_fields.argtypes = [P, ctypes.POINTER(P), IP, I, I, P]
     L.igg_acoustic_step.argtypes = [P, P, P, P, P, I, D, D, D, D, D, D, I, P]
+    L.igg_gp_step.argtypes = [P, P, P, P, I, D, D, D, D, D, I, P]
     L.igg_step.argtypes = [P, P, P, P, I, D, D, D, D, D, P]
     L.igg_step_hidden.argtypes = [P, IP, P, P, P, I, D, D, D, D, D, P]
     L.igg_run.argtypes = [P, I, IP, P, P, P, I, D, D, D, D, D, P]
@@ -70,7 +71,7 @@ def lib():
     for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
                  "igg_grid_shape", "igg_subdomain_info", "igg_update_halo",
                  "igg_update_halo_staggered", "igg_update_halo_fields",
-                 "igg_acoustic_step", "igg_step",
+                 "igg_acoustic_step", "igg_gp_step", "igg_step",
                  "igg_step_hidden", "igg_run", "igg_reduce", "igg_device_status",
                  "igg_grid_set_option"):
         getattr(L, name).restype = I
@@ -253,6 +254,14 @@ class Grid:
         _check(lib().igg_acoustic_step(self._handle(), *ptrs, dtype_code(d), float(rho), float(K),
                                        float(dt), float(dx), float(dy), float(dz), int(bool(halo)),
                                        _stream(stream)))
+
+    def gp_step(self, u, v, V, g, dt, dx, dy, dz, halo=True, stream=None):
+        """One Gross-Pitaevskii step (igg_gp_step): u half, halo, v half, halo."""
+        n = self.nsub * self.nloc
+        d = u.dtype
+        _check(lib().igg_gp_step(self._handle(), _ptr(u, n, d, "u"), _ptr(v, n, d, "v"),
+                                 _ptr(V, n, d, "V"), dtype_code(d), float(g), float(dt), float(dx),
+                                 float(dy), float(dz), int(bool(halo)), _stream(stream)))
 
     def step(self, T2, T, Ci, lam, dt, dx, dy, dz, stream=None):
         """Fig. 1 step! on every subdomain (inner points of T2)."""
