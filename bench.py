@@ -399,12 +399,42 @@ def form_acoustic(steps):
     return out
 
 
+def form_gp(steps):
+    """Gross-Pitaevskii on 2x2x2 subdomains of 256^3 points, FP64 and FP32:
+    ms per step (two half steps, each followed by the halo update of its
+    field) and T_eff over the 8 field passes of a step (each half: read u, v,
+    V, write the updated field)."""
+    import paper_2211_15716_gb300 as igg
+    n, dims = (256, 256, 256), (2, 2, 2)
+    h = 1.0 / 510
+    g = 1.0
+    dt = 0.3 / (2 * 3 / h ** 2 + 1.0 + 2 * g)
+    out = {"form": "gross_pitaevskii", "workload": "2x2x2 x 256^3, psi = u + i v, harmonic potential"}
+    with igg.Grid(n, dims=dims, overlap=(2, 2, 2)) as gr:
+        cells = gr.nsub * gr.nloc
+        for dtype, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+            u = torch.rand(gr.shape, dtype=dtype, device="cuda") - 0.5
+            v = torch.rand(gr.shape, dtype=dtype, device="cuda") - 0.5
+            P = torch.rand(gr.shape, dtype=dtype, device="cuda")
+            step = lambda: gr.gp_step(u, v, P, g, dt, h, h, h)  # noqa: E731
+            for _ in range(3):
+                step()
+            ms = _timed(lambda: [step() for _ in range(steps)], 1) / steps
+            s = u.element_size()
+            out[name] = {"ms_per_step": round(ms, 4),
+                         "T_eff_GB_s": round(8 * cells * s / (ms * 1e-3) / 1e9, 1),
+                         "cell_updates_per_s": cells / (ms * 1e-3)}
+            del u, v, P
+    return out
+
+
 def run_forms(args):
     import paper_2211_15716_gb300  # noqa: F401
     from paper_2211_15716_gb300 import build as igg_build
     igg_build.build()
     for fn in (lambda: form_precision(max(20, args.steps // 5)), lambda: form_batched(max(20, args.steps)),
-               form_adjoint, lambda: form_acoustic(max(20, args.steps // 5))):
+               form_adjoint, lambda: form_acoustic(max(20, args.steps // 5)),
+               lambda: form_gp(max(20, args.steps // 5))):
         print(json.dumps(fn()), flush=True)
         torch.cuda.empty_cache()
     return 0
