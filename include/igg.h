@@ -284,8 +284,8 @@ int igg_gp_step(igg_grid *grid, void *u, void *v, const void *V, igg_dtype dtype
  * the dtype. Row padding and gaps between problems are never written.
  * ------------------------------------------------------------------------- */
 
-/* sizes: nprob triples (nx, ny, nz), each >= 3. Creates the tile table with
- * the default tiling (32x8 tiles, 32-plane z depth, resident CTAs per SM). */
+/* sizes: nprob triples (nx, ny, nz), each >= 3. Creates the tile table of
+ * the default kernel (variant 4, else 3; z depth 32 planes). */
 int igg_batch_create(int nprob, const int *sizes, igg_dtype dtype,
                      igg_batch **out);
 
@@ -304,7 +304,11 @@ int igg_batch_pitches(const igg_batch *batch, int *pitches);
 int igg_batch_set_coefs(igg_batch *batch, const double *lam, const double *dt,
                         const double *dx, const double *dy, const double *dz);
 
-/* Kernel and tiling: variant 3 (the default) = the 16-byte vector kernel,
+/* Kernel and tiling: variant 4 = the TMA-pipelined kernel over every
+ * problem's tiles (per-problem tensor maps, encoded on the first step with a
+ * pair of field pointers and kept on the batch; ctas_per_sm must be 0;
+ * IGG_EINVAL without the driver's tensor-map encoder; the default where it
+ * is available); variant 3 = the 16-byte vector kernel,
  * one CTA per tile of 8 warps of row segments (ctas_per_sm must be 0);
  * variants 0, 1, 2 = the persistent scalar kernel with 32x8, 32x4, 64x4
  * columns per tile and ctas_per_sm CTAs per SM (0 = as many as are

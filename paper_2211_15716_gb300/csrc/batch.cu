@@ -10,14 +10,18 @@
 // offset aligned to 256 bytes. Each problem has its own lam, dt, dx, dy, dz
 // (coefficient table on the device).
 //
-// Kernels: variant 3 (default) launches the register-pipelined 16-byte
-// vector kernel, one CTA per tile of rows; variants 0-2 the persistent
-// scalar kernel with 32x8, 32x4 or 64x4 column tiles.
+// Kernels: variant 4 launches the TMA-pipelined kernel over every problem's
+// tiles (per-problem tensor maps in device memory; the default where the
+// driver's tensor-map encoder is available); variant 3 the register-pipelined
+// 16-byte vector kernel, one CTA per tile of rows;
+// variants 0-2 the persistent scalar kernel with 32x8, 32x4 or 64x4 column
+// tiles.
 #include <algorithm>
 #include <array>
 #include <cstring>
 #include <map>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "igg_internal.h"
@@ -26,8 +30,10 @@ using namespace igg;
 
 namespace {
 
-// the vector-kernel variant (one CTA per tile); below it the persistent ones
+// the vector-kernel variant (one CTA per tile), the TMA variant; below them
+// the persistent ones
 constexpr int kBatchVector = kPersistentVariants;
+constexpr int kBatchTma = kBatchVector + 1;
 
 // CTAs per SM of each persistent variant for this dtype (occupancy query).
 int max_ctas_per_sm(igg_dtype dt, int variant);
@@ -46,9 +52,15 @@ struct igg_batch {
   Coef *coef = nullptr;
   bool have_coef = false;
   int variant = kBatchVector, zb = 32, ctas_per_sm = 0;
-  Tile *tiles = nullptr;    // variants 0-2
-  VTile *vtiles = nullptr;  // variant 3
+  Tile *tiles = nullptr;      // variants 0-2
+  VTile *vtiles = nullptr;    // variant 3
+  TmaTile *ttiles = nullptr;  // variant 4
   int ntiles = 0;
+  // variant 4: tensor maps per (T, Ci) pointer pair, row pitch and ny per
+  // problem, device error word of the TMA kernel
+  std::map<std::pair<const void *, const void *>, TmaMapBytes *> maps;
+  int *geom = nullptr;
+  unsigned *dev_err = nullptr;
   cudaStream_t cap = nullptr;
   std::map<std::tuple<const void *, const void *, const void *>, cudaGraphExec_t> graphs;
 };
@@ -63,12 +75,29 @@ void drop_graphs(igg_batch *b) {
 int build_tiles(igg_batch *b) {
   cudaFree(b->tiles);
   cudaFree(b->vtiles);
+  cudaFree(b->ttiles);
   b->tiles = nullptr;
   b->vtiles = nullptr;
+  b->ttiles = nullptr;
   b->ntiles = 0;
   drop_graphs(b);
   cudaError_t e = cudaSuccess;
-  if (b->variant == kBatchVector) {
+  if (b->variant == kBatchTma) {
+    const int V = vec_width(b->dtype);
+    const int Wt = tma_tile_width(b->dtype, TMA_WIDE), Ht = tma_tile_rows(b->dtype, TMA_WIDE);
+    std::vector<TmaTile> v;
+    for (int p = 0; p < b->nprob; ++p) {
+      const int nx = b->sizes[p][0], ny = b->sizes[p][1], nz = b->sizes[p][2];
+      const size_t first = v.size();
+      add_box_tma(v, b->offsets[p], 0, 1, nx - 1, 1, ny - 1, 1, nz - 1,
+                  b->zb > 0 ? b->zb : nz - 2, V, Wt, Ht);
+      for (size_t k = first; k < v.size(); ++k) v[k].pad[0] = p;
+    }
+    b->ntiles = (int)v.size();
+    e = cudaMalloc(&b->ttiles, v.size() * sizeof(TmaTile));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->ttiles, v.data(), v.size() * sizeof(TmaTile), cudaMemcpyHostToDevice);
+  } else if (b->variant == kBatchVector) {
     const int V = vec_width(b->dtype);
     std::vector<VTile> v;
     for (int p = 0; p < b->nprob; ++p) {
@@ -124,9 +153,49 @@ int check_fields(const igg_batch *b, const void *T2, const void *T, const void *
   return IGG_OK;
 }
 
+// Tensor maps of (T, Ci) for the TMA variant, encoded and uploaded on first
+// use (before any capture: igg_batch_run prepares both pointer pairs).
+int batch_maps(igg_batch *b, const void *T, const void *Ci, const TmaMapBytes **out) {
+  const auto key = std::make_pair(T, Ci);
+  auto it = b->maps.find(key);
+  if (it != b->maps.end()) {
+    *out = it->second;
+    return IGG_OK;
+  }
+  std::vector<TmaMapBytes> h(2 * (size_t)b->nprob);
+  std::vector<int> sz(3 * (size_t)b->nprob);
+  for (int p = 0; p < b->nprob; ++p)
+    for (int d = 0; d < 3; ++d) sz[3 * p + d] = b->sizes[p][d];
+  if (!tma_batch_maps(b->dtype, T, Ci, b->nprob, b->offsets.data(), sz.data(), b->pitch.data(),
+                      h.data()))
+    return set_error(IGG_ECUDA, "tensor map encoding failed for the batch");
+  TmaMapBytes *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, h.size() * sizeof(TmaMapBytes));
+  if (e == cudaSuccess) e = cudaMemcpy(d, h.data(), h.size() * sizeof(TmaMapBytes), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_error(e, "batch tensor maps");
+  }
+  if (b->maps.size() >= 8) {  // keep a few pointer pairs
+    cudaFree(b->maps.begin()->second);
+    b->maps.erase(b->maps.begin());
+  }
+  b->maps.emplace(key, d);
+  *out = d;
+  return IGG_OK;
+}
+
 int enqueue(igg_batch *b, void *T2, const void *T, const void *Ci, cudaStream_t s) {
   cudaError_t e;
-  if (b->variant == kBatchVector) {
+  if (b->variant == kBatchTma) {
+    const TmaMapBytes *m = nullptr;
+    if (int rc = batch_maps(b, T, Ci, &m)) return rc;
+    TmaBatch tb;
+    tb.maps = m;
+    tb.geom = b->geom;
+    tb.coef = b->coef;
+    e = launch_stencil_tma_batch(b->dtype, b->ttiles, b->ntiles, T2, tb, b->dev_err, s);
+  } else if (b->variant == kBatchVector) {
     e = launch_stencil_vec(b->dtype, b->vtiles, b->ntiles, T2, T, Ci, Coef(), b->coef, s);
   } else {
     const int nctas = b->sm_count * b->ctas_per_sm;
@@ -189,6 +258,28 @@ int igg_batch_create(int nprob, const int *sizes, igg_dtype dt, igg_batch **out)
     return cuda_error(e, "batch set-up");
   }
   b->ctas_per_sm = 0;
+  b->variant = tma_available() ? kBatchTma : kBatchVector;
+  {
+    std::vector<int> geom(2 * (size_t)nprob);
+    for (int p = 0; p < nprob; ++p) {
+      geom[2 * p] = b->pitch[p];
+      geom[2 * p + 1] = b->sizes[p][1];
+    }
+    e = cudaMalloc(&b->geom, geom.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->geom, geom.data(), geom.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->dev_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess && tma_available()) e = tma_batch_prepare(dt);
+    if (e != cudaSuccess) {
+      cudaFree(b->geom);
+      cudaFree(b->dev_err);
+      cudaFree(b->coef);
+      cudaStreamDestroy(b->cap);
+      delete b;
+      return cuda_error(e, "batch set-up");
+    }
+  }
   if (int rc = build_tiles(b)) {
     cudaFree(b->coef);
     cudaStreamDestroy(b->cap);
@@ -207,6 +298,10 @@ int igg_batch_destroy(igg_batch *b) {
   drop_graphs(b);
   cudaFree(b->tiles);
   cudaFree(b->vtiles);
+  cudaFree(b->ttiles);
+  for (auto &kv : b->maps) cudaFree(kv.second);
+  cudaFree(b->geom);
+  cudaFree(b->dev_err);
   cudaFree(b->coef);
   cudaStreamDestroy(b->cap);
   delete b;
@@ -252,11 +347,13 @@ int igg_batch_set_coefs(igg_batch *b, const double *lam, const double *dt, const
 int igg_batch_configure(igg_batch *b, int variant, int zb, int ctas_per_sm) {
   clear_error();
   if (!b) return set_error(IGG_EINVAL, "batch is NULL");
-  if (variant < 0 || variant > kBatchVector)
-    return set_error(IGG_EINVAL, "variant %d outside [0, %d]", variant, kBatchVector);
+  if (variant < 0 || variant > kBatchTma)
+    return set_error(IGG_EINVAL, "variant %d outside [0, %d]", variant, kBatchTma);
+  if (variant == kBatchTma && !tma_available())
+    return set_error(IGG_EINVAL, "the TMA variant needs the driver's tensor-map encoder");
   if (zb < 0) return set_error(IGG_EINVAL, "zb < 0");
   DevGuard g(b->device);
-  if (variant == kBatchVector) {
+  if (variant >= kBatchVector) {
     if (ctas_per_sm != 0)
       return set_error(IGG_EINVAL, "ctas_per_sm must be 0 for the vector variant (one CTA per tile)");
   } else {
@@ -300,6 +397,11 @@ int igg_batch_run(igg_batch *b, int nt, void *T, void *T2, const void *Ci, void 
   if (T == Ci) return set_error(IGG_EINVAL, "T aliases Ci");
   DevGuard g(b->device);
   cudaStream_t s = (cudaStream_t)stream;
+  if (b->variant == kBatchTma) {  // tensor maps are built outside any capture
+    const TmaMapBytes *m = nullptr;
+    if (int rc = batch_maps(b, T, Ci, &m)) return rc;
+    if (int rc = batch_maps(b, T2, Ci, &m)) return rc;
+  }
   if (nt >= 2) {
     auto key = std::make_tuple((const void *)T, (const void *)T2, Ci);
     cudaGraphExec_t exec = nullptr;
@@ -352,9 +454,10 @@ int igg_batch_autotune(igg_batch *b, void *T2, const void *T, const void *Ci, in
   float best = 1e30f;
   int bv = b->variant, bz = b->zb, bc = b->ctas_per_sm;
   int rc = IGG_OK;
-  for (int v = 0; v <= kBatchVector && rc == IGG_OK; ++v) {
-    const bool vec = v == kBatchVector;
-    const int cmax = vec ? 0 : max_ctas_per_sm(b->dtype, v);
+  for (int v = 0; v <= kBatchTma && rc == IGG_OK; ++v) {
+    if (v == kBatchTma && !tma_available()) break;
+    const bool one_cta_per_tile = v >= kBatchVector;
+    const int cmax = one_cta_per_tile ? 0 : max_ctas_per_sm(b->dtype, v);
     const int cands[2] = {cmax, std::max(1, cmax / 2)};
     for (int zb : zbs) {
       for (int ci = 0; ci < (cmax > 1 ? 2 : 1); ++ci) {

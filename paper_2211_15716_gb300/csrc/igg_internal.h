@@ -125,6 +125,29 @@ struct TmaTile {
   int pad[2];
 };
 enum { TMA_WIDE = 0, TMA_WIDE_SWAP = 2 };
+// TMA tiles of the box [x0,x1) x rows [r0,r1) x march [m0,m1) (chunks of mb
+// planes) of one array at element offset base whose planes start at plane
+// zoff of the tensor map; tile width Wt, rows Ht, vector width V.
+void add_box_tma(std::vector<TmaTile> &v, long long base, long long zoff, int x0, int x1, int r0,
+                 int r1, int m0, int m1, int mb, int V, int Wt, int Ht);
+// Batched form on the TMA kernel: per problem two tensor maps (T, Ci) in
+// device memory, its row pitch and ny, its coefficients; a tile's problem
+// is its pad[0]. Maps are 128-byte opaque blocks here (CUtensorMap in tma.cu).
+struct alignas(64) TmaMapBytes {
+  unsigned char b[128];
+};
+struct TmaBatch {
+  const TmaMapBytes *maps;  // [2 * nprob]: T, Ci
+  const int *geom;          // [2 * nprob]: row pitch, ny
+  const Coef *coef;         // [nprob]
+};
+// Encodes the 2*nprob maps of fields T and Ci (problem b at element offset
+// off[b], size sizes[3b..3b+2], row pitch pitch[b]) into host memory out.
+bool tma_batch_maps(igg_dtype dt, const void *T, const void *Ci, int nprob,
+                    const long long *off, const int *sizes, const int *pitch, TmaMapBytes *out);
+cudaError_t tma_batch_prepare(igg_dtype dt);
+cudaError_t launch_stencil_tma_batch(igg_dtype dt, const TmaTile *tiles, int ntiles, void *T2,
+                                     const TmaBatch &b, unsigned *dev_err, cudaStream_t s);
 static_assert(sizeof(TmaTile) == 48, "TmaTile layout");
 // bits of the device error word: IGG_DEV_ERR_TIMEOUT, IGG_DEV_ERR_DRAIN (igg.h)
 int tma_tile_width(igg_dtype dt, int variant);

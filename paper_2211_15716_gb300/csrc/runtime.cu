@@ -258,6 +258,8 @@ long long tma_slots(int V, int variant = TMA_WIDE) {
   return (long long)per_sm * sms;
 }
 
+}  // namespace
+
 // Tiles of a TMA kernel variant for one box of the subdomain whose planes
 // start at zoff. Rows run over [r0, r1) in blocks of Ht, the march over
 // [m0, m1) in chunks of mb: rows y / march z, or (swapped variant) rows z /
@@ -282,6 +284,8 @@ void add_box_tma(std::vector<TmaTile> &v, long long base, long long zoff, int x0
         v.push_back(t);
       }
 }
+
+namespace {
 
 // Tiles of one box for the kernel of the set: scalar (V = 1), vector or TMA.
 struct TileLists {

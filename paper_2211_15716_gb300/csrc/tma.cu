@@ -22,6 +22,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "cell.cuh"
@@ -343,12 +344,16 @@ __device__ __forceinline__ void compute_vec<double, MODE_EMU + 2>(
 // rows along z, march along y (box {BW, 1, BH}), for boxes thin in y. The
 // cell arithmetic gets the y and z neighbour pairs in their own slots either
 // way, so both orientations give the same bits.
-template <class S, int LPR_, int H_, bool SWAP, int MODE, bool SEND>
+//
+// BATCH: independent problems of the batched form; a tile's problem (pad[0])
+// gives its tensor maps, row pitch, ny and coefficients (TmaBatch) in place
+// of mapT, mapC, nx, ny and c0.
+template <class S, int LPR_, int H_, bool SWAP, int MODE, bool SEND, bool BATCH = false>
 __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
                   unsigned *__restrict__ dev_err, void *__restrict__ fix, size_t fix_cap,
-                  const HaloSend send) {
+                  const HaloSend send, const TmaBatch batch = TmaBatch()) {
   using Sh = TmaShape<S, LPR_, H_>;
   using C = typename Num<S>::C;
   constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
@@ -361,6 +366,14 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 
   const TmaTile t = tiles[blockIdx.x];
   const int K = (t.m1 - t.m0) + 2;
+  const CUtensorMap *pmT = &mapT, *pmC = &mapC;
+  if constexpr (BATCH) {
+    pmT = reinterpret_cast<const CUtensorMap *>(batch.maps + 2 * t.pad[0]);
+    pmC = pmT + 1;
+    nx = batch.geom[2 * t.pad[0]];  // row pitch
+    ny = batch.geom[2 * t.pad[0] + 1];
+    c0 = batch.coef[t.pad[0]];
+  }
   // SEND: the subdomains reached by each combination of send options
   int *nbc = reinterpret_cast<int *>(smem + NS * Sh::STAGE + 2 * NS * 8 + 64);
   if (SEND && threadIdx.x < 27) {
@@ -399,11 +412,11 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
         mbar_expect_tx(bar, Sh::TB + Sh::CB);
         const int mT = t.m0 - 1 + k, mC = t.m0 - 2 + k;  // march index of the T / Ci plane
         if (!SWAP) {
-          tma_load_3d(dst, &mapT, t.x0 - V, t.r0 - 1, t.zoff + mT, bar);
-          tma_load_3d(dst + Sh::TBA, &mapC, t.x0, t.r0, t.zoff + mC, bar);
+          tma_load_3d(dst, pmT, t.x0 - V, t.r0 - 1, t.zoff + mT, bar);
+          tma_load_3d(dst + Sh::TBA, pmC, t.x0, t.r0, t.zoff + mC, bar);
         } else {
-          tma_load_3d(dst, &mapT, t.x0 - V, mT, t.zoff + t.r0 - 1, bar);
-          tma_load_3d(dst + Sh::TBA, &mapC, t.x0, mC, t.zoff + t.r0, bar);
+          tma_load_3d(dst, pmT, t.x0 - V, mT, t.zoff + t.r0 - 1, bar);
+          tma_load_3d(dst + Sh::TBA, pmC, t.x0, mC, t.zoff + t.r0, bar);
         }
       }
       flags[1] = k;
@@ -723,6 +736,62 @@ cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, co
   return cudaErrorInvalidValue;
 }
 
+// The batched form's launch: non-swapped wide tiles, the storage type's cell
+// (FP64 batches: the FP64 cell, no fix-up), maps from the TmaBatch table.
+template <class S>
+cudaError_t launch_batch_t(const TmaTile *tiles, int ntiles, void *T2, const TmaBatch &b,
+                           unsigned *dev_err, cudaStream_t s) {
+  using Shp = WideShape<S>;
+  using Sh = TmaShape<S, Shp::LPR, Shp::H>;
+  constexpr int MODE = sizeof(S) == 8 ? MODE_F64 : MODE_CELL;
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof none);
+  k_stencil_tma<S, Shp::LPR, Shp::H, false, MODE, false, true>
+      <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(none, none, tiles, (S *)T2, 0, 0,
+                                                          Coef(), dev_err, nullptr, 0,
+                                                          HaloSend(), b);
+  return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t prepare_batch_t() {
+  using Shp = WideShape<S>;
+  using Sh = TmaShape<S, Shp::LPR, Shp::H>;
+  constexpr int MODE = sizeof(S) == 8 ? MODE_F64 : MODE_CELL;
+  return cudaFuncSetAttribute(k_stencil_tma<S, Shp::LPR, Shp::H, false, MODE, false, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+}
+
+template <class S>
+bool batch_maps_t(const void *T, const void *Ci, int nprob, const long long *off, const int *sz,
+                  const int *pitch, TmaMapBytes *out) {
+  using Shp = WideShape<S>;
+  using Sh = TmaShape<S, Shp::LPR, Shp::H>;
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const CUtensorMapDataType t = sizeof(S) == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                : sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  for (int p = 0; p < nprob; ++p) {
+    const cuuint64_t dims[3] = {(cuuint64_t)sz[3 * p], (cuuint64_t)sz[3 * p + 1],
+                                (cuuint64_t)sz[3 * p + 2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch[p] * sizeof(S),
+                                   (cuuint64_t)pitch[p] * sz[3 * p + 1] * sizeof(S)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t boxT[3] = {(cuuint32_t)Sh::BW, (cuuint32_t)Sh::BH, 1};
+    const cuuint32_t boxC[3] = {(cuuint32_t)Sh::W, (cuuint32_t)Sh::H, 1};
+    const char *tb = static_cast<const char *>(T) + off[p] * (long long)sizeof(S);
+    const char *cb = static_cast<const char *>(Ci) + off[p] * (long long)sizeof(S);
+    for (int k = 0; k < 2; ++k)
+      if (fn(reinterpret_cast<CUtensorMap *>(&out[2 * p + k]), t, 3,
+             const_cast<char *>(k == 0 ? tb : cb), dims, strides, k == 0 ? boxT : boxC, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 int tma_tile_width(igg_dtype dt, int) {
@@ -744,6 +813,39 @@ int tma_tile_rows(igg_dtype dt, int) {
 }
 
 bool tma_available() { return encode_fn() != nullptr; }
+
+static_assert(sizeof(TmaMapBytes) == sizeof(CUtensorMap) && alignof(TmaMapBytes) >= 64,
+              "tensor map storage");
+
+bool tma_batch_maps(igg_dtype dt, const void *T, const void *Ci, int nprob, const long long *off,
+                    const int *sizes, const int *pitch, TmaMapBytes *out) {
+  switch (dt) {
+    case IGG_F64: return batch_maps_t<double>(T, Ci, nprob, off, sizes, pitch, out);
+    case IGG_F32: return batch_maps_t<float>(T, Ci, nprob, off, sizes, pitch, out);
+    case IGG_BF16: return batch_maps_t<__nv_bfloat16>(T, Ci, nprob, off, sizes, pitch, out);
+  }
+  return false;
+}
+
+cudaError_t tma_batch_prepare(igg_dtype dt) {
+  switch (dt) {
+    case IGG_F64: return prepare_batch_t<double>();
+    case IGG_F32: return prepare_batch_t<float>();
+    case IGG_BF16: return prepare_batch_t<__nv_bfloat16>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stencil_tma_batch(igg_dtype dt, const TmaTile *tiles, int ntiles, void *T2,
+                                     const TmaBatch &b, unsigned *dev_err, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (dt) {
+    case IGG_F64: return launch_batch_t<double>(tiles, ntiles, T2, b, dev_err, s);
+    case IGG_F32: return launch_batch_t<float>(tiles, ntiles, T2, b, dev_err, s);
+    case IGG_BF16: return launch_batch_t<__nv_bfloat16>(tiles, ntiles, T2, b, dev_err, s);
+  }
+  return cudaErrorInvalidValue;
+}
 
 size_t tma_fix_cap(const TmaTile *tiles, int ntiles) {
   size_t cap = 0;
