@@ -33,7 +33,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    hdrs = [os.path.join(CSRC, "*.h"), os.path.join(CSRC, "*.cuh"), os.path.join(INCLUDE, "*.h")]
+    return _sources() + [p for h in hdrs for p in glob.glob(h)]
 
 
 def up_to_date() -> bool:

@@ -1,136 +1,54 @@
 // Adjoint of Fig. 1's step! (the transposed stencil run backward in time) and
-// the checkpointed drivers that give gradients of a function of T_nt with
-// respect to Ci and the initial T.
-//
-// Forward step on inner points p:  T_{n+1}[p] = T_n[p] + Ci[p] * l(T_n)[p],
-// l(T)[p] = sum_d w_d (T[p-e_d] + T[p+e_d] - 2 T[p]),  w_d = dt*lam/dd^2,
-// identity on the array boundary. Given lam_in = dJ/dT_{n+1}:
-//   v[q]       = Ci[q]*lam_in[q] on inner q, 0 elsewhere,
-//   lam_out[q] = lam_in[q] + sum_d w_d (v[q-e_d] + v[q+e_d] - 2 v[q]),
-//                on every point q (neighbours outside the array are 0),
-//   gCi[p]    += lam_in[p] * l(T_n)[p] on inner p (accumulated in FP64).
-// FP64 fields form l(T_n) with the emulated cell's exact differences where the
-// stencil allows it (cell.cuh), else in FP64; the v sums are FP64 (lam_in
-// changes sign from point to point, which the emulation cannot take).
+// the checkpointed drivers' kernels: gradients of a function of T_nt with
+// respect to Ci and the initial T. The per-point arithmetic (adj_cell.cuh) is
+// shared with the TMA-pipelined adjoint kernel (adjoint_tma.cu); this file
+// holds the plain tiled kernel, used where the TMA kernel does not apply
+// (rows whose byte length is not a multiple of 16, unaligned fields, TMA
+// switched off), and the residual kernel.
 #include <algorithm>
 #include <cstring>
 
-#include "cell.cuh"
+#include "adj_cell.cuh"
 #include "igg_internal.h"
 
 namespace igg {
 namespace {
 
-template <class S>
-struct AdjNum;
-template <>
-struct AdjNum<double> {
-  using C = double;
-  static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
-  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  // l from the z-summed and neighbour values, forward-FP64 order
-  static __device__ __forceinline__ double lsum(double c, double xm, double xp, double ym,
-                                                double yp, double zm, double zp, double wx,
-                                                double wy, double wz, double wc) {
-    const double sx = __dadd_rn(xm, xp), sy = __dadd_rn(ym, yp), sz = __dadd_rn(zm, zp);
-    double l = __dmul_rn(wc, c);
-    l = __fma_rn(wx, sx, l);
-    l = __fma_rn(wy, sy, l);
-    return __fma_rn(wz, sz, l);
-  }
-  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double fma(double a, double b, double c) {
-    return __fma_rn(a, b, c);
-  }
-};
-template <>
-struct AdjNum<float> {
-  using C = float;
-  static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  // forward-FP32 order: differences first
-  static __device__ __forceinline__ float lsum(float c, float xm, float xp, float ym, float yp,
-                                               float zm, float zp, float wx, float wy, float wz,
-                                               float) {
-    const float ex = __fadd_rn(__fsub_rn(xp, c), __fsub_rn(xm, c));
-    const float ey = __fadd_rn(__fsub_rn(yp, c), __fsub_rn(ym, c));
-    const float ez = __fadd_rn(__fsub_rn(zp, c), __fsub_rn(zm, c));
-    float l = __fmul_rn(wx, ex);
-    l = __fmaf_rn(wy, ey, l);
-    return __fmaf_rn(wz, ez, l);
-  }
-  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float fma(float a, float b, float c) {
-    return __fmaf_rn(a, b, c);
-  }
-};
-
 constexpr int kAdjX = 32, kAdjY = 8, kAdjRing = 2 * (kAdjX + 2) + 2 * kAdjY;
 
-// l(T_n) * lam_in added to gCi on inner points: FP64 fields use the emulated
-// cell's exact second differences where the stencil shares sign and exponent
-// (T_n is a forward state, smooth), else the FP64 sum; FP32 fields their
-// FP32 sum. `inner` is the same for the whole warp's call; the FP64 sum is
-// reached only by warps with a point that needs it (a branch on a warp vote,
-// so that it is not evaluated, predicated off, on every point).
-__device__ __forceinline__ void gci_update(double *gp, bool inner, double la, double t, double xm,
-                                           double xp, double ym, double yp, double zm, double zp,
-                                           const W<double> &w) {
-  const double tn[6] = {xm, xp, ym, yp, zm, zp};
-  unsigned hn[6];
-  unsigned long long nb[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    hn[i] = dhi(tn[i]);
-    nb[i] = dbits(tn[i]);
-  }
-  const bool ok = emu_fast_ok(dhi(t), hn);
-  if (__all_sync(0xffffffffu, ok || !inner)) {
-    if (!inner) return;
-    const double g = *gp;
-    if (w.ng == 1) *gp = emu_apply(g, la, emu_lap<1>(t, nb, w));
-    else if (w.ng == 2) *gp = emu_apply(g, la, emu_lap<2>(t, nb, w));
-    else *gp = emu_apply(g, la, emu_lap<3>(t, nb, w));
-  } else if (inner) {
-    const double g = *gp;
-    if (ok) {
-      if (w.ng == 1) *gp = emu_apply(g, la, emu_lap<1>(t, nb, w));
-      else if (w.ng == 2) *gp = emu_apply(g, la, emu_lap<2>(t, nb, w));
-      else *gp = emu_apply(g, la, emu_lap<3>(t, nb, w));
-    } else {
-      *gp = __fma_rn(la, AdjNum<double>::lsum(t, xm, xp, ym, yp, zm, zp, w.wx, w.wy, w.wz, w.wc),
-                     g);
-    }
-  }
+__device__ __forceinline__ bool adj_inner(int x, int y, int z, int nx, int ny, int nz) {
+  return x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2;
 }
-__device__ __forceinline__ void gci_update(double *gp, bool inner, float la, float t, float xm,
-                                           float xp, float ym, float yp, float zm, float zp,
-                                           const W<float> &w) {
-  if (inner)
-    *gp = __fma_rn((double)la,
-                   (double)AdjNum<float>::lsum(t, xm, xp, ym, yp, zm, zp, w.wx, w.wy, w.wz, w.wc),
-                   *gp);
+
+// v at (x, y, z) in FP64 from global memory (the FP64 sum's inputs)
+__device__ __forceinline__ double v64_at(const double *__restrict__ lam_in,
+                                         const double *__restrict__ Ci, int x, int y, int z,
+                                         int nx, int ny, int nz) {
+  if (!adj_inner(x, y, z, nx, ny, nz)) return 0.0;
+  const long long p = x + (long long)nx * (y + (long long)ny * z);
+  return adj_v64(__ldg(lam_in + p), __ldg(Ci + p), true);
 }
 
 // One CTA per 32x8 block of (x, y) columns and a chunk of zb planes, every
-// point of the array. Per plane, v = Ci*lam_in and T_n of the block and of
-// the ring of one point around it go to shared memory (two buffers, one
-// barrier per plane); each v is formed once, by the thread of its point or
-// of its ring position. The column's planes z-1, z, z+1 stay in registers.
+// point of the array. Per plane, v and T_n of the block and of the ring of
+// one point around it go to shared memory (two buffers, one barrier per
+// plane); each v is formed once, by the thread of its point or of its ring
+// position. The column's planes z-1, z, z+1 stay in registers. Every thread
+// runs every plane (the warp votes inside need all lanes); stores are masked.
 template <class S>
 __global__ void __launch_bounds__(kAdjX *kAdjY)
     k_adjoint(int nx, int ny, int nz, int zb, S *__restrict__ lam_out,
               const S *__restrict__ lam_in, const S *__restrict__ Tn,
               const S *__restrict__ Ci, double *__restrict__ gCi, Coef c) {
-  using N = AdjNum<S>;
-  using C = typename N::C;
-  __shared__ C vs[2][kAdjY + 2][kAdjX + 2];
-  __shared__ C ts[2][kAdjY + 2][kAdjX + 2];
+  using Ops = AdjOps<S>;
+  using VT = typename Ops::VT;
+  __shared__ VT vs[2][kAdjY + 2][kAdjX + 2];
+  __shared__ S ts[2][kAdjY + 2][kAdjX + 2];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kAdjX + tx;
   const int x0 = blockIdx.x * kAdjX, y0 = blockIdx.y * kAdjY;
   const int x = x0 + tx, y = y0 + ty;
   const int z0 = blockIdx.z * zb, z1 = min(z0 + zb, nz);
-  const W<C> w = make_w(c, C(0));
+  const typename Ops::WT aw = Ops::weights(c);
   const long long sy = nx, sz = (long long)nx * ny;
   // ring position of this thread (tid < kAdjRing): rows y0-1 and y0+kAdjY
   // over x0-1 .. x0+kAdjX, then columns x0-1 and x0+kAdjX over y0 .. y0+kAdjY-1
@@ -152,19 +70,22 @@ __global__ void __launch_bounds__(kAdjX *kAdjY)
   const bool ring = tid < kAdjRing && rx >= 0 && rx < nx && ry >= 0 && ry < ny;
   const bool in_xy = x > 0 && x < nx - 1 && y > 0 && y < ny - 1;
   const bool rin_xy = rx > 0 && rx < nx - 1 && ry > 0 && ry < ny - 1;
+  const S zero = S(0);
   // v and T at (xx, yy, z): v = 0 off the inner points, T = 0 off the array
-  auto vload = [&](bool ok, bool inner, long long p, int z) -> C {
-    return (ok && inner && z > 0 && z < nz - 1) ? N::mul(N::ld(Ci + p), N::ld(lam_in + p)) : C(0);
+  auto vload = [&](bool ok, bool inner, long long p, int z) -> VT {
+    const bool in = ok && inner && z > 0 && z < nz - 1;
+    return Ops::v(Ops::lam(in ? __ldg(lam_in + p) : zero), in ? __ldg(Ci + p) : zero, in);
   };
-  auto tload = [&](bool ok, long long p, int z) -> C {
-    return (ok && z >= 0 && z < nz) ? N::ld(Tn + p) : C(0);
+  auto tload = [&](bool ok, long long p, int z) -> S {
+    return (ok && z >= 0 && z < nz) ? __ldg(Tn + p) : zero;
   };
   const long long pc = x + sy * y, pr = rx + sy * ry;
-  C vm = vload(own, in_xy, pc + sz * (z0 - 1), z0 - 1), vc = vload(own, in_xy, pc + sz * z0, z0);
-  C tm = tload(own, pc + sz * (z0 - 1), z0 - 1), tc = tload(own, pc + sz * z0, z0);
-  C la = own ? N::ld(lam_in + pc + sz * z0) : C(0);
+  VT vm = vload(own, in_xy, pc + sz * (z0 - 1), z0 - 1), vc = vload(own, in_xy, pc + sz * z0, z0);
+  S tm = tload(own, pc + sz * (z0 - 1), z0 - 1), tc = tload(own, pc + sz * z0, z0);
+  S la = own ? __ldg(lam_in + pc + sz * z0) : zero;
   // ring values of the current plane, loaded one plane ahead
-  C rv = vload(ring, rin_xy, pr + sz * z0, z0), rt = tload(ring, pr + sz * z0, z0);
+  VT rv = vload(ring, rin_xy, pr + sz * z0, z0);
+  S rt = tload(ring, pr + sz * z0, z0);
   for (int z = z0; z < z1; ++z) {
     const int b = z & 1;
     const long long p = pc + sz * z;
@@ -176,24 +97,32 @@ __global__ void __launch_bounds__(kAdjX *kAdjY)
       rv = vload(ring, rin_xy, pr + sz * (z + 1), z + 1);
       rt = tload(ring, pr + sz * (z + 1), z + 1);
     }
-    const C vp = vload(own, in_xy, p + sz, z + 1);
-    const C tp = tload(own, p + sz, z + 1);
-    const C lap = own && z + 1 < nz ? N::ld(lam_in + p + sz) : C(0);
+    const VT vp = vload(own, in_xy, p + sz, z + 1);
+    const S tp = tload(own, p + sz, z + 1);
+    const S lap = own && z + 1 < nz ? __ldg(lam_in + p + sz) : zero;
     __syncthreads();
-    if (own) {
-      const C vxm = vs[b][ty + 1][tx], vxp = vs[b][ty + 1][tx + 2];
-      const C vym = vs[b][ty][tx + 1], vyp = vs[b][ty + 2][tx + 1];
-      // lam_out = lam_in + wc v + sum_d w_d (v[-d] + v[+d])
-      C acc = N::fma(w.wc, vc, la);
-      acc = N::fma(w.wx, N::add(vxm, vxp), acc);
-      acc = N::fma(w.wy, N::add(vym, vyp), acc);
-      acc = N::fma(w.wz, N::add(vm, vp), acc);
-      lam_out[p] = (S)acc;
+    S out;
+    const bool ok = Ops::out(Ops::lam(la), vc, vs[b][ty + 1][tx], vs[b][ty + 1][tx + 2],
+                             vs[b][ty][tx + 1], vs[b][ty + 2][tx + 1], vm, vp, aw, out);
+    if constexpr (sizeof(S) == 8) {
+      // points outside the pair path's ranges: the FP64 sum
+      if (__any_sync(0xffffffffu, own && !ok)) {
+        if (own && !ok) {
+          const double *L = reinterpret_cast<const double *>(lam_in);
+          const double *C = reinterpret_cast<const double *>(Ci);
+          out = adj_out_f64(la, v64_at(L, C, x, y, z, nx, ny, nz), v64_at(L, C, x - 1, y, z, nx, ny, nz),
+                            v64_at(L, C, x + 1, y, z, nx, ny, nz), v64_at(L, C, x, y - 1, z, nx, ny, nz),
+                            v64_at(L, C, x, y + 1, z, nx, ny, nz), v64_at(L, C, x, y, z - 1, nx, ny, nz),
+                            v64_at(L, C, x, y, z + 1, nx, ny, nz), aw.w);
+        }
+      }
     }
-    // every thread of the warp takes part (warp vote inside)
-    gci_update(gCi + (own ? p : 0), own && in_xy && z > 0 && z < nz - 1, la, tc,
-               ts[b][ty + 1][tx], ts[b][ty + 1][tx + 2], ts[b][ty][tx + 1], ts[b][ty + 2][tx + 1],
-               tm, tp, w);
+    if (own) lam_out[p] = out;
+    const bool inner = own && in_xy && z > 0 && z < nz - 1;
+    const double g = inner ? gCi[p] : 0.0;
+    const double gn = gci_add(g, inner, la, tc, ts[b][ty + 1][tx], ts[b][ty + 1][tx + 2],
+                              ts[b][ty][tx + 1], ts[b][ty + 2][tx + 1], tm, tp, Ops::lapw(aw));
+    if (inner) gCi[p] = gn;
     vm = vc;
     vc = vp;
     tm = tc;
@@ -214,7 +143,9 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_adjoint(igg_dtype dt, int nx, int ny, int nz, void *lam_out,
                            const void *lam_in, const void *Tn, const void *Ci, double *gCi,
-                           const Coef &c, cudaStream_t s) {
+                           const Coef &c, bool tma, unsigned *dev_err, cudaStream_t s) {
+  if (tma && adjoint_tma_applies(dt, nx, lam_out, lam_in, Tn, Ci, gCi))
+    return launch_adjoint_tma(dt, nx, ny, nz, lam_out, lam_in, Tn, Ci, gCi, c, dev_err, s);
   const int zb = std::min(nz, 32);
   const dim3 grid((nx + kAdjX - 1) / kAdjX, (ny + kAdjY - 1) / kAdjY, (nz + zb - 1) / zb);
   const dim3 block(kAdjX, kAdjY);

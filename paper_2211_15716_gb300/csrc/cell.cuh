@@ -185,13 +185,12 @@ struct EmuLap {
   unsigned eoff, sign;
 };
 
+// The weighted sum of exact second differences D[3] (x, y, z; units
+// u = +-2^(E-1075), |D_d| < 2^53) with NG weight groups; `scale_hi` is the
+// high word of a double with u's sign and exponent field E.
 template <int NG>
-__device__ __forceinline__ EmuLap emu_lap(double tc, const unsigned long long *nb,
-                                          const W<double> &w) {
-  const unsigned long long c2 = dbits(tc) << 1;
-  long long D[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) D[d] = (long long)(nb[2 * d] + nb[2 * d + 1] - c2);
+__device__ __forceinline__ EmuLap emu_lap_d(const long long *D, unsigned scale_hi,
+                                            const W<double> &w) {
   long long G[NG];
   if constexpr (NG == 1) {
     G[0] = D[0] + D[1] + D[2];
@@ -231,12 +230,21 @@ __device__ __forceinline__ EmuLap emu_lap(double tc, const unsigned long long *n
     L.C = __fadd_rn(__fadd_rn(__fadd_rn(X[0], X[1]), __fadd_rn(X[2], e1)),
                     __fadd_rn(__fadd_rn(R[0], R[1]), __fadd_rn(R[2], e2)));
   }
-  const unsigned hc = dhi(tc);
-  L.eoff = (hc & 0x7FF00000u) - (179u << 20);
+  L.eoff = (scale_hi & 0x7FF00000u) - (179u << 20);
   // the bit differences of negative values carry the opposite sign of the
   // value differences
-  L.sign = hc & 0x80000000u;
+  L.sign = scale_hi & 0x80000000u;
   return L;
+}
+
+template <int NG>
+__device__ __forceinline__ EmuLap emu_lap(double tc, const unsigned long long *nb,
+                                          const W<double> &w) {
+  const unsigned long long c2 = dbits(tc) << 1;
+  long long D[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) D[d] = (long long)(nb[2 * d] + nb[2 * d + 1] - c2);
+  return emu_lap_d<NG>(D, dhi(tc), w);
 }
 
 // base + m * l for an emulated Laplacian l, with two FP64 FMAs (the sign of

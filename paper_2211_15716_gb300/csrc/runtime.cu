@@ -1231,7 +1231,8 @@ int igg_adjoint_step(igg_grid *g, void *lam_out, const void *lam_in, const void 
   if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
   DeviceGuard dg(g->device);
   cudaError_t e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], lam_out, lam_in, Tn, Ci, gCi,
-                                 make_coef(lam, dtime, dx, dy, dz), (cudaStream_t)stream);
+                                 make_coef(lam, dtime, dx, dy, dz), g->tma_enabled, g->dev_err,
+                                 (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
   return IGG_OK;
 }
@@ -1319,7 +1320,8 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
         return rc;
     for (int j = len - 1; j >= 0; --j) {
       char *nxt = cur == LA ? LB : LA;
-      e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], nxt, cur, state(j), Ci, gCi, c, s);
+      e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], nxt, cur, state(j), Ci, gCi, c,
+                         g->tma_enabled, g->dev_err, s);
       if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
       cur = nxt;
     }
