@@ -240,42 +240,6 @@ __device__ __forceinline__ float adj_lap32(float c, float xm, float xp, float ym
   return __fmaf_rn(w.wz, ez, l);
 }
 
-// Exact second differences of a stencil whose seven values share the sign
-// and whose exponent fields take at most two neighbouring values
-// {Emin, Emin + 1} (a smooth field crossing a power of two): each magnitude's
-// significand, leading bit included, shifted left by E - Emin is an integer
-// of at most 54 bits in units of 2^(Emin - 1075), so the differences are
-// exact 64-bit sums. True, with D[3] and the scale's high word (sign,
-// exponent field Emin), when the stencil qualifies, Emin lies in
-// [949, 1138] and every |D_d| < 2^53 (the range emu_lap_d takes).
-__device__ __forceinline__ bool emu_spread_d(double tc, const unsigned long long *nb, long long *D,
-                                             unsigned &scale_hi) {
-  const unsigned long long cb = dbits(tc);
-  const unsigned hc = (unsigned)(cb >> 32);
-  unsigned emin = (hc >> 20) & 0x7FFu, emax = emin, sdiff = 0u;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const unsigned h = (unsigned)(nb[i] >> 32);
-    const unsigned e = (h >> 20) & 0x7FFu;
-    emin = min(emin, e);
-    emax = max(emax, e);
-    sdiff |= (h ^ hc) & 0x80000000u;
-  }
-  auto mag = [&](unsigned long long b) -> long long {
-    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
-    return (long long)(((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << ((e - emin) & 1u));
-  };
-  const long long c2 = 2 * mag(cb);
-  bool ok = sdiff == 0u && emax - emin <= 1u && emin - 949u <= 189u;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    D[d] = mag(nb[2 * d]) + mag(nb[2 * d + 1]) - c2;
-    ok = ok && (unsigned long long)(D[d] + (1ll << 53)) < (1ull << 54);
-  }
-  scale_hi = (hc & 0x80000000u) | (emin << 20);
-  return ok;
-}
-
 // g + lam_in * l(T_n) for an inner point, g elsewhere. FP64 fields form l
 // with the emulated cell's exact differences: where the stencil shares sign
 // and exponent (T_n is a forward state, smooth) from the bit patterns, where

@@ -128,10 +128,12 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // in FP64, S*u and C*u widened to FP64 exactly by bit manipulation (the
 // scaling by u is an exponent offset folded into the widening).
 //
-// Stencils with mixed signs or exponents (the shells where a smooth field
-// crosses a power of two) or with E outside [949, 1139] take cell_f64. The
-// choice depends only on the point's inputs, so every kernel makes the same
-// choice and produces the same bits.
+// Stencils whose exponents take two neighbouring values (the shells where a
+// smooth field crosses a power of two) get the same weighted sum from exact
+// differences of the significands shifted to the smaller exponent's scale
+// (emu_spread_d). Stencils with mixed signs, a wider exponent spread or E
+// outside the ranges take cell_f64. The choice depends only on the point's
+// inputs, so every kernel makes the same choice and produces the same bits.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double v) {
   return (unsigned long long)__double_as_longlong(v);
@@ -255,6 +257,42 @@ __device__ __forceinline__ double emu_apply(double base, double m, const EmuLap 
   return __fma_rn(sm, f2d_scaled(L.S, L.eoff), __fma_rn(sm, f2d_scaled(L.C, L.eoff), base));
 }
 
+// Exact second differences of a stencil whose seven values share the sign
+// and whose exponent fields take at most two neighbouring values
+// {Emin, Emin + 1} (a smooth field crossing a power of two): each magnitude's
+// significand, leading bit included, shifted left by E - Emin is an integer
+// of at most 54 bits in units of 2^(Emin - 1075), so the differences are
+// exact 64-bit sums. True, with D[3] and the scale's high word (sign,
+// exponent field Emin), when the stencil qualifies, Emin lies in
+// [949, 1138] and every |D_d| < 2^53 (the range emu_lap_d takes).
+__device__ __forceinline__ bool emu_spread_d(double tc, const unsigned long long *nb, long long *D,
+                                             unsigned &scale_hi) {
+  const unsigned long long cb = dbits(tc);
+  const unsigned hc = (unsigned)(cb >> 32);
+  unsigned emin = (hc >> 20) & 0x7FFu, emax = emin, sdiff = 0u;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const unsigned h = (unsigned)(nb[i] >> 32);
+    const unsigned e = (h >> 20) & 0x7FFu;
+    emin = min(emin, e);
+    emax = max(emax, e);
+    sdiff |= (h ^ hc) & 0x80000000u;
+  }
+  auto mag = [&](unsigned long long b) -> long long {
+    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+    return (long long)(((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << ((e - emin) & 1u));
+  };
+  const long long c2 = 2 * mag(cb);
+  bool ok = sdiff == 0u && emax - emin <= 1u && emin - 949u <= 189u;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    D[d] = mag(nb[2 * d]) + mag(nb[2 * d + 1]) - c2;
+    ok = ok && (unsigned long long)(D[d] + (1ll << 53)) < (1ull << 54);
+  }
+  scale_hi = (hc & 0x80000000u) | (emin << 20);
+  return ok;
+}
+
 // The emulated update of a fast-path point: tc + ci * l(T).
 template <int NG>
 __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
@@ -269,7 +307,18 @@ __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long l
   return cell_emu_fast<3>(tc, nb, ci, w);
 }
 
-// One point: the emulated cell where its fast path applies, else cell_f64.
+// The emulated update of a stencil crossing one power of two (emu_spread_d
+// holds): tc + ci * l(T) from the shifted significands' differences.
+__device__ __forceinline__ double cell_emu_spread(double tc, const long long *D, unsigned sh,
+                                                  double ci, const W<double> &w) {
+  if (w.ng == 1) return emu_apply(tc, ci, emu_lap_d<1>(D, sh, w));
+  if (w.ng == 2) return emu_apply(tc, ci, emu_lap_d<2>(D, sh, w));
+  return emu_apply(tc, ci, emu_lap_d<3>(D, sh, w));
+}
+
+// One point: the emulated cell where its fast path applies, else where the
+// stencil crosses one power of two the emulated cell from shifted
+// significands, else cell_f64.
 __device__ __forceinline__ double cell_emu(double tc, const double *tn, double ci,
                                            const W<double> &w) {
   unsigned hn[6];
@@ -279,8 +328,11 @@ __device__ __forceinline__ double cell_emu(double tc, const double *tn, double c
     hn[i] = dhi(tn[i]);
     nb[i] = dbits(tn[i]);
   }
-  if (!emu_fast_ok(dhi(tc), hn)) return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
-  return cell_emu_fast(tc, nb, ci, w);
+  if (emu_fast_ok(dhi(tc), hn)) return cell_emu_fast(tc, nb, ci, w);
+  long long D[3];
+  unsigned sh;
+  if (emu_spread_d(tc, nb, D, sh)) return cell_emu_spread(tc, D, sh, ci, w);
+  return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
 }
 
 // The FP64 update used by every kernel: the emulated cell or the FP64 cell.

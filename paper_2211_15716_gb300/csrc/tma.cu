@@ -86,7 +86,7 @@ __device__ __forceinline__ FixList fix_list(void *fix, size_t cap) {
   unsigned *c = reinterpret_cast<unsigned *>(e + cap);
   return {e, c, c + 1};
 }
-constexpr int kFixupBlocks = 8 * 152;
+constexpr int kFixupBlocks = 2 * 152;
 
 // Halo update fused into the step (HaloSend). A point's send option in
 // dimension d: 0 = none, 1 = to plane n - 1 of the left neighbour
@@ -243,7 +243,8 @@ __device__ __forceinline__ void compute_vec<double, MODE_F64>(
 
 // Emulated fast path for both points, computed unconditionally (no branch
 // in the common case); ok marks the points whose fast path applies, the
-// others are left to the fix-up.
+// others are left to the fix-up (which applies cell(): the shifted-
+// significand form across one power of two, else the FP64 cell).
 template <int NG>
 __device__ __forceinline__ void compute_vec_emu(
     const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
@@ -496,9 +497,10 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
   }
 }
 
-// Fix-up of an emulated-cell launch: the points left by the kernel get the
-// FP64 cell (the same choice and the same arithmetic as cell() everywhere
-// else). The kernel listed every 32-point row segment with such points; the
+// Fix-up of an emulated-cell launch: the points left by the kernel get
+// cell() (the same choice and arithmetic as every kernel: the shifted-
+// significand form where the stencil crosses one power of two, else the
+// FP64 cell). The kernel listed every 32-point row segment with such points; the
 // fix-up's warps take the entries in turn, lane l updating point p + l when
 // bit l is set. The last block to finish resets the list.
 __global__ void __launch_bounds__(256)
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(256)
     const double tc = __ldg(T + p);
     const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
                           __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-    const double v = cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+    const double v = cell(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
     T2[p] = v;
     if (send.nbr) {
       const int sub = (int)(p / send.nloc);
