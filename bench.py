@@ -196,6 +196,27 @@ def run_reference(args, ws, rank):
 # --forms: the reduced-precision, batched and adjoint forms, each against the
 # FP64 form on the same GPU, one JSON line each (not the headline line)
 # ---------------------------------------------------------------------------
+def step_samples(fn, n, stream, steps_per_call):
+    """n timed calls of fn (each steps_per_call steps) back to back: the
+    median ms per step and the 95 % confidence interval of the median from
+    the order statistics at ranks n/2 -+ 1.96 sqrt(n)/2."""
+    import torch as _t
+    evs = [(_t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    _t.cuda.synchronize()
+    t = sorted(a.elapsed_time(b) / steps_per_call for a, b in evs)
+    half = 1.959964 * math.sqrt(n) / 2
+    lo = max(0, int(math.floor(n / 2 - half)) - 1)
+    hi = min(n - 1, int(math.ceil(n / 2 + half)) - 1)
+    med = 0.5 * (t[(n - 1) // 2] + t[n // 2])
+    return {"n": n, "steps_per_sample": steps_per_call, "median_ms_per_step": round(med, 4),
+            "ci95_ms_per_step": [round(t[lo], 4), round(t[hi], 4)],
+            "min_ms_per_step": round(t[0], 4), "max_ms_per_step": round(t[-1], 4)}
+
+
 def _timed(fn, reps):
     import torch as _t
     fn()
@@ -536,6 +557,11 @@ def main():
     clocks = sampler.stop()
     k_ms = k0.elapsed_time(k1) / kreps
 
+    # ---- per-sample step times (outside the timed region): median and a
+    # 95 % confidence interval of the median from order statistics ---------
+    samples = step_samples(lambda: grid.run(2, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths),
+                           40, stream, 2)
+
     # ---- variants (outside the timed region): plain step, FP64 cell -------
     variants = {}
     vsteps = max(10, args.steps // 4)
@@ -623,6 +649,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "variants": variants,
+        "step_samples": samples,
         "device_status": status,
     }
     if tdtype == torch.float64:

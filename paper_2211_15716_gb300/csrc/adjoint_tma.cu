@@ -70,47 +70,6 @@ struct AdjShape {
   static_assert(NS >= 4, "issue rule needs two loads ahead");
 };
 
-constexpr int kAdjZc = 32;  // z chunk of the work order
-
-// Barrier of all warps (named barrier 1) that returns, to every thread,
-// whether any thread passed true.
-__device__ __forceinline__ bool all_any(bool pred, unsigned nthreads) {
-  unsigned r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
-      " selp.u32 %0, 1, 0, q;\n}"
-      : "=r"(r)
-      : "r"((unsigned)pred), "r"(nthreads)
-      : "memory");
-  return r != 0;
-}
-
-// One segment of a CTA's share: planes [m0, m1) of column col.
-struct Seg {
-  int col, m0, m1;
-};
-
-// The share [u, u1) of the work order (z chunk, column, plane in chunk),
-// walked one segment at a time.
-struct Share {
-  long long u, u1;
-  int nz, ncol;
-  __device__ bool next(Seg &s) {
-    if (u >= u1) return false;
-    const long long per = (long long)ncol * kAdjZc;   // positions of a full chunk
-    const int c = (int)(u / per);
-    const int zc = min(kAdjZc, nz - c * kAdjZc);      // planes per column in chunk c
-    const long long w = u - (long long)c * per;
-    s.col = (int)(w / zc);
-    const int zi = (int)(w - (long long)s.col * zc);
-    const int len = (int)min((long long)(zc - zi), u1 - u);
-    s.m0 = c * kAdjZc + zi;
-    s.m1 = s.m0 + len;
-    u += len;
-    return true;
-  }
-};
-
 template <class S>
 __device__ __forceinline__ void lds16(const void *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);

@@ -198,8 +198,10 @@ cudaError_t launch_acoustic(igg_dtype dt, int nsub, int nx, int ny, int nz, void
 struct GpCoef {
   double kx, ky, kz, kc, dt, g;
 };
+// With `tma`, 3-D grids whose rows allow it take the TMA-pipelined kernel.
 cudaError_t launch_gp_half(igg_dtype dt, int which, int nsub, int nx, int ny, int nz, void *u,
-                           void *v, const void *V, const GpCoef &c, cudaStream_t s);
+                           void *v, const void *V, const GpCoef &c, bool tma, unsigned *dev_err,
+                           cudaStream_t s);
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.

@@ -1040,7 +1040,8 @@ int igg_gp_step(igg_grid *g, void *u, void *v, const void *V, igg_dtype dt, doub
   c.g = gnl;
   cudaStream_t s = (cudaStream_t)stream;
   for (int which = 0; which < 2; ++which) {
-    cudaError_t e = launch_gp_half(dt, which, g->nsub, g->n[0], g->n[1], g->n[2], u, v, V, c, s);
+    cudaError_t e = launch_gp_half(dt, which, g->nsub, g->n[0], g->n[1], g->n[2], u, v, V, c,
+                                   g->tma_enabled && !low_dim(g), g->dev_err, s);
     if (e != cudaSuccess) return cuda_error(e, "Gross-Pitaevskii launch");
     if (with_halo && any_halo(g)) {
       e = enqueue_halo(g, which == 0 ? u : v, dtype_size(dt), s);

@@ -1,7 +1,8 @@
 // TMA and mbarrier helpers shared by the TMA-pipelined kernels: shared
 // memory addresses, bounded mbarrier waits (about 2 s of globaltimer, false on
-// timeout), 3-D tiled bulk tensor loads, and the host-side tensor map encoder
-// reached through the runtime's driver entry point.
+// timeout), 3-D tiled bulk tensor loads, the host-side tensor map encoder
+// reached through the runtime's driver entry point, and the work order and
+// barrier reduction of the persistent column kernels.
 #pragma once
 
 #include <cuda.h>
@@ -101,6 +102,49 @@ bool encode(CUtensorMap *m, const void *base, int nx, int ny, long long nzt, int
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+constexpr int kShareZc = 32;  // z chunk of the work order of Share
+
+// Barrier of all warps (named barrier 1) that returns, to every thread,
+// whether any thread passed true.
+__device__ __forceinline__ bool all_any(bool pred, unsigned nthreads) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((unsigned)pred), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+
+// One segment of a CTA's share: planes [m0, m1) of column col.
+struct Seg {
+  int col, m0, m1;
+};
+
+// The share [u, u1) of a persistent CTA in the work order (z chunk, column,
+// plane in chunk) of ncol columns of nz planes each, walked one segment at a
+// time; CTA b of G takes [U b / G, U (b + 1) / G), U = ncol nz, so every CTA
+// gets the same number of planes (within one).
+struct Share {
+  long long u, u1;
+  int nz, ncol;
+  __device__ bool next(Seg &s) {
+    if (u >= u1) return false;
+    const long long per = (long long)ncol * kShareZc;   // positions of a full chunk
+    const int c = (int)(u / per);
+    const int zc = min(kShareZc, nz - c * kShareZc);      // planes per column in chunk c
+    const long long w = u - (long long)c * per;
+    s.col = (int)(w / zc);
+    const int zi = (int)(w - (long long)s.col * zc);
+    const int len = (int)min((long long)(zc - zi), u1 - u);
+    s.m0 = c * kShareZc + zi;
+    s.m1 = s.m0 + len;
+    u += len;
+    return true;
+  }
+};
 
 }  // namespace
 }  // namespace igg

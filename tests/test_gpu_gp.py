@@ -90,3 +90,50 @@ def test_gp_linear_invariant_gpu():
             vals.append(oracle.gp_invariant(u.cpu().numpy()[0], vprev, vn))
             vprev = vn
     assert np.abs(np.array(vals) - vals[0]).max() <= 1e-11 * vals[0]
+
+
+def _gp_run(n, dims, periods, U, Vv, Pot, g, dt, dd, nt, dtype, tma):
+    o = (2, 2, 2)
+    with igg.Grid(n, dims=dims, overlap=o, periods=periods) as gr:
+        gr.set_option(igg.Grid.OPT_TMA, 1 if tma else 0)
+        u, v, P = (torch.from_numpy(a).to(dtype).cuda() for a in (U, Vv, Pot))
+        for _ in range(nt):
+            gr.gp_step(u, v, P, g, dt, *dd)
+        torch.cuda.synchronize()
+        assert gr.device_status() == 0
+        return u.double().cpu().numpy(), v.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_gp_tma_and_tiled_kernels_same_bits(dtype):
+    """The TMA kernel (several x tiles with a ragged one, two subdomains) and
+    the tiled kernel share the per-point arithmetic: identical bits."""
+    n, dims, periods = (132, 37, 29), (2, 1, 1), (1, 0, 0)
+    g, nt = 0.9, 4
+    dd = (0.1, 0.12, 0.09)
+    dt = 0.3 / (2 * sum(1 / h ** 2 for h in dd) + 1.0 + 2 * g)
+    U, Vv, Pot = inputs(n, dims, periods, (2, 2, 2), 11)
+    a = _gp_run(n, dims, periods, U, Vv, Pot, g, dt, dd, nt, dtype, True)
+    b = _gp_run(n, dims, periods, U, Vv, Pot, g, dt, dd, nt, dtype, False)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("tma", [True, False])
+def test_gp_fp64_values_outside_pair_ranges(tma):
+    """Fields holding tiny, huge and zero values (FP64 sum at those points)
+    still meet the oracle within 1e-12 of the largest value."""
+    n, dims, periods = (66, 21, 19), (1, 1, 1), (0, 0, 0)
+    g, nt = 0.9, 3
+    dd = (0.1, 0.12, 0.09)
+    dt = 0.3 / (2 * sum(1 / h ** 2 for h in dd) + 1.0 + 2 * g)
+    U, Vv, Pot = inputs(n, dims, periods, (2, 2, 2), 12)
+    rng = np.random.default_rng(3)
+    pick = rng.random(U.shape)
+    U = np.where(pick < 0.03, U * 1e-20, U)
+    U = np.where((pick >= 0.03) & (pick < 0.05), 0.0, U)
+    Vv = np.where(pick > 0.98, Vv * 1e-30, Vv)
+    ru, rv = U.copy(), Vv.copy()
+    oracle.gp_run_decomposed(ru, rv, Pot, nt, g, dt, *dd, dims, periods, (2, 2, 2))
+    gu, gv = _gp_run(n, dims, periods, U, Vv, Pot, g, dt, dd, nt, torch.float64, tma)
+    for a, r in ((gu, ru), (gv, rv)):
+        assert np.abs(a - r).max() <= 1e-12 * np.abs(r).max()
