@@ -107,7 +107,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = ("tma.cu", "cell.cuh", "igg_internal.h")
+KERNEL_SOURCES = ("tma.cu", "tma_util.cuh", "cell.cuh", "igg_internal.h")
 
 
 def kernel_source_sha256() -> str:

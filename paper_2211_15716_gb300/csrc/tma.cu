@@ -86,7 +86,7 @@ __device__ __forceinline__ FixList fix_list(void *fix, size_t cap) {
   unsigned *c = reinterpret_cast<unsigned *>(e + cap);
   return {e, c, c + 1};
 }
-constexpr int kFixupBlocks = 2 * 152;
+constexpr int kFixupBlocks = 8 * 152;
 
 // Halo update fused into the step (HaloSend). A point's send option in
 // dimension d: 0 = none, 1 = to plane n - 1 of the left neighbour
