@@ -460,6 +460,52 @@ def form_gp(steps):
     return out
 
 
+def profile_case(which):
+    """Short fixed workloads for ncu captures of one kernel (not bench lines):
+    'adjoint': 13 adjoint steps at 256^3 on FP64 fields (T_n the Gaussian bump,
+    sigma 0.15), then 13 on FP32 fields; 'gp': three Gross-Pitaevskii steps on
+    2x2x2 x 128^3, FP64 then FP32. Prints each case's ms per launch."""
+    import synth
+    import paper_2211_15716_gb300 as igg
+    from paper_2211_15716_gb300 import autograd as ag
+    from paper_2211_15716_gb300 import workloads as wl
+
+    if which == "adjoint":
+        n = 256
+        g = igg.Grid((n, n, n))
+        gi = [np.arange(n)] * 3
+        gauss = np.ascontiguousarray(np.broadcast_to(synth.gaussian_bump(*gi, (n, n, n), sigma=0.15),
+                                                     (n, n, n)))
+        dd = [wl.spacing(1.0, n)] * 3
+        dt = wl.cfl_dt(*dd, 1.0, 0.67)
+        for tdt in (torch.float64, torch.float32):
+            gen = torch.Generator(device="cuda").manual_seed(0)
+            lam_in = torch.randn(g.shape, dtype=torch.float64, device="cuda", generator=gen).to(tdt)
+            Tn = torch.from_numpy(gauss).to(tdt).cuda().view(g.shape).contiguous()
+            C = torch.full(g.shape, 0.53, dtype=tdt, device="cuda")
+            out = torch.empty_like(lam_in)
+            gci = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+            ms = _timed(lambda: ag.adjoint_step(g, out, lam_in, Tn, C, gci, 1.0, dt, *dd), 12)
+            print(json.dumps({"profile": "adjoint", "dtype": str(tdt), "ms_per_launch": round(ms, 4),
+                              "device_status": g.device_status()}))
+        g.finalize()
+    elif which == "gp":
+        n = 128
+        h = 1.0 / (2 * n - 2)
+        gnl = 1.0
+        dt = 0.3 / (2 * 3 / h ** 2 + 1.0 + 2 * gnl)
+        with igg.Grid((n, n, n), dims=(2, 2, 2), overlap=(2, 2, 2)) as gr:
+            for tdt in (torch.float64, torch.float32):
+                gen = torch.Generator(device="cuda").manual_seed(0)
+                u = torch.rand(gr.shape, dtype=tdt, device="cuda", generator=gen) - 0.5
+                v = torch.rand(gr.shape, dtype=tdt, device="cuda", generator=gen) - 0.5
+                P = torch.rand(gr.shape, dtype=tdt, device="cuda", generator=gen)
+                ms = _timed(lambda: gr.gp_step(u, v, P, gnl, dt, h, h, h), 2)
+                print(json.dumps({"profile": "gp", "dtype": str(tdt), "ms_per_step": round(ms, 4),
+                                  "device_status": gr.device_status()}))
+    return 0
+
+
 def run_forms(args):
     import paper_2211_15716_gb300  # noqa: F401
     from paper_2211_15716_gb300 import build as igg_build
@@ -484,12 +530,19 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--forms", action="store_true",
                     help="measure the precision, batched and adjoint forms (extra JSON lines)")
+    ap.add_argument("--profile", choices=["adjoint", "gp"],
+                    help="run a short fixed workload of one kernel for an ncu capture")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.forms:
         return run_forms(args)
+    if args.profile:
+        import paper_2211_15716_gb300  # noqa: F401
+        from paper_2211_15716_gb300 import build as igg_build
+        igg_build.build()
+        return profile_case(args.profile)
     if args.warmup < 3:
         args.warmup = 3
 
