@@ -263,8 +263,15 @@ int igg_acoustic_step(igg_grid *grid, void *P, void *Vx, void *Vy, void *Vz,
  * the values at hand (old u in the first half, new u in the second), lap the
  * 7-point operator with spacings dx, dy, dz (+inf for an absent dimension).
  * Stable for dt below 2 / (2 (1/dx^2 + 1/dy^2 + 1/dz^2) + max(V + g rho)).
- * dtype F64 or F32; FMAs in the kernels (within rounding of the oracle's
- * left-to-right evaluation).
+ * dtype F64 or F32. F32 fields: FMAs (within rounding of the oracle's
+ * left-to-right evaluation). F64 fields: each half-step update (q =
+ * dt (V + g rho) and the seven terms) is formed in float pairs (~48-bit
+ * significands) and rounded once to FP64, within about 2^-45 of |u or v| plus
+ * the magnitudes of the terms; points whose values leave the pair ranges
+ * (|u|, |v|, |V| outside [2^-40, 2^41), |q| outside [2^-36, 2^37), zero
+ * allowed) use the FP64 formula. 3-D grids whose rows are a multiple of 16
+ * bytes (and 16-byte aligned fields) run a TMA-pipelined kernel unless
+ * IGG_OPT_TMA is 0; other grids a column kernel with the same bits.
  * ------------------------------------------------------------------------- */
 int igg_gp_step(igg_grid *grid, void *u, void *v, const void *V, igg_dtype dtype,
                 double g, double dt, double dx, double dy, double dz, int with_halo,
@@ -348,6 +355,18 @@ int igg_batch_autotune(igg_batch *batch, void *T2, const void *T,
  * Forward step on inner points p: T_{n+1}[p] = T_n[p] + Ci[p]*l(T_n)[p],
  * l(T)[p] = sum_d w_d (T[p-e_d] + T[p+e_d] - 2 T[p]), w_d = dt*lam/dd^2;
  * boundary points are unchanged.
+ *
+ * Arithmetic of a step: F32 fields in F32 with FMAs, the gCi increment in
+ * FP64 from the two F32 factors. F64 fields: lam_out is formed in float pairs
+ * (~48-bit significands) as a compensated dot product and rounded once to
+ * FP64, within about 2^-45 of |lam_in| + sum |w v| (points whose stencil
+ * holds |lam| outside [2^-40, 2^41) or Ci outside [2^-20, 2^21), zero
+ * allowed, or with weights outside [2^-18, 2^18], use the FP64 sum); l(T_n)
+ * for gCi from exact integer second differences where the stencil shares
+ * sign and crosses at most one power of two, else in FP64. Rows of a
+ * multiple of 16 bytes with 16-byte aligned fields run a TMA-pipelined
+ * kernel unless IGG_OPT_TMA is 0; other rows a tiled kernel with the same
+ * bits.
  * ------------------------------------------------------------------------- */
 
 /* One backward step. lam_in = dJ/dT_{n+1}; writes lam_out = dJ/dT_n on
