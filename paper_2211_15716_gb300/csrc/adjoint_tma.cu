@@ -4,10 +4,10 @@
 //
 // Tiles are W x H (x, y) columns (W = 32 lanes x one 16-byte vector: 64
 // FP64 or 128 FP32 points; H = 8 FP64 / 16 FP32 rows, one warp per row)
-// marching along z. A
-// persistent grid (all CTAs resident) takes equal shares of the work order
-// (z chunk, column, plane), so every CTA handles the same number of planes;
-// a share splits into segments (runs of planes of one column).
+// marching along z. A persistent grid (all CTAs resident) takes equal shares
+// of the work order (z chunk, column, plane), so every CTA handles the same
+// number of planes; a share splits into segments (runs of planes of one
+// column).
 //
 // Per plane p, cp.async.bulk.tensor (TMA) loads into a ring of NS shared-
 // memory stages the (W + 2V) x (H + 2) boxes of lam_in, Ci and T_n around the
