@@ -163,6 +163,16 @@ int igg_update_halo_fields(igg_grid *grid, void *const fields[], const int *size
 #define IGG_DEV_ERR_DRAIN 2u
 int igg_device_status(igg_grid *grid, unsigned *status, int clear);
 
+/* Self-test of that failure detection, without a GPU fault: on the current
+ * device, one kernel whose warps wait on two mbarriers with the pipelined
+ * kernels' bounded wait (about 2 s); the phase of one completes, nothing
+ * ever arrives on the other. The warps agree on stopping through the barrier
+ * reduction of the persistent kernels, so none is left waiting, and the
+ * kernel records IGG_DEV_ERR_TIMEOUT. *status (host) receives the recorded
+ * bits: IGG_DEV_ERR_TIMEOUT when the detection works. Synchronises the
+ * device; takes about 2 s. */
+int igg_selftest_bounded_wait(unsigned *status);
+
 /* Grid options (wait for the grid's streams; cached CUDA graphs are
  * rebuilt):
  *   IGG_OPT_TMA (default 1): run the regular boxes of the step with the

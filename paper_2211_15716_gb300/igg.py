@@ -292,6 +292,18 @@ class Grid:
         return T if nt % 2 == 0 else T2
 
 
+def selftest_bounded_wait() -> int:
+    """igg_selftest_bounded_wait: the device error bits recorded by a kernel
+    whose bounded wait on an mbarrier that never completes runs out (expected
+    DEV_ERR_TIMEOUT); about 2 s."""
+    fn = lib().igg_selftest_bounded_wait
+    fn.argtypes = [ctypes.POINTER(ctypes.c_uint)]
+    fn.restype = ctypes.c_int
+    st = ctypes.c_uint(0)
+    _check(fn(ctypes.byref(st)))
+    return int(st.value)
+
+
 def reduce(op: int, a: torch.Tensor, b: torch.Tensor | None = None, out: torch.Tensor | None = None,
            stream=None):
     """FP64 reduction over all elements (RED_MAX, RED_SUM, RED_SUM_DIV,
