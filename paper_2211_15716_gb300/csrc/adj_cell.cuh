@@ -49,11 +49,17 @@ __device__ __forceinline__ FF pair_lam(double lam) {
   return q;
 }
 
-// v of one point for FP64 fields as a normalised pair from the pair of lam
-// (pair_lam) and Ci; (0, 0) off the inner points; NaN in h when lam or Ci
-// lies outside the pair range.
-__device__ __forceinline__ FF adj_v_pair(const FF &a, double ci, bool inner) {
-  const FF b = pair_split(ci);
+// Ci as a pair, NaN in h outside the pair range
+__device__ __forceinline__ FF pair_ci(double ci) {
+  FF b = pair_split(ci);
+  b.h = pair_ok(ci, kPairCiE) ? b.h : __int_as_float(0x7FC00000);
+  return b;
+}
+
+// v of one point for FP64 fields as a normalised pair from the pairs of lam
+// (pair_lam) and Ci (pair_ci); (0, 0) off the inner points; NaN in h when
+// either pair holds one (a value outside the pair range).
+__device__ __forceinline__ FF adj_v_pairs(const FF &a, const FF &b, bool inner) {
   const float p = __fmul_rn(a.h, b.h);
   float e = __fmaf_rn(a.h, b.h, -p);
   e = __fmaf_rn(a.h, b.l, e);
@@ -63,10 +69,13 @@ __device__ __forceinline__ FF adj_v_pair(const FF &a, double ci, bool inner) {
   float q;
   v.h = fast_two_sum(p, e, q);
   v.l = q;
-  v.h = pair_ok(ci, kPairCiE) ? v.h : __int_as_float(0x7FC00000);
   v.h = inner ? v.h : 0.f;
   v.l = inner ? v.l : 0.f;
   return v;
+}
+
+__device__ __forceinline__ FF adj_v_pair(const FF &a, double ci, bool inner) {
+  return adj_v_pairs(a, pair_ci(ci), inner);
 }
 
 // v of one point for FP64 fields in FP64 (the FP64 sum's input)

@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(256)
 
 cudaError_t launch_adjoint(igg_dtype dt, int nx, int ny, int nz, void *lam_out,
                            const void *lam_in, const void *Tn, const void *Ci, double *gCi,
-                           const Coef &c, bool tma, unsigned *dev_err, cudaStream_t s) {
+                           const Coef &c, bool tma, unsigned *dev_err, cudaStream_t s,
+                           const void *ci_pairs) {
   if (tma && adjoint_tma_applies(dt, nx, lam_out, lam_in, Tn, Ci, gCi))
-    return launch_adjoint_tma(dt, nx, ny, nz, lam_out, lam_in, Tn, Ci, gCi, c, dev_err, s);
+    return launch_adjoint_tma(dt, nx, ny, nz, lam_out, lam_in, Tn, Ci, gCi, c, dev_err, s,
+                              dt == IGG_F64 ? ci_pairs : nullptr);
   const int zb = std::min(nz, 32);
   const dim3 grid((nx + kAdjX - 1) / kAdjX, (ny + kAdjY - 1) / kAdjY, (nz + zb - 1) / zb);
   const dim3 block(kAdjX, kAdjY);

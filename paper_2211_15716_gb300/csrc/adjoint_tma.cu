@@ -73,7 +73,10 @@ __device__ __forceinline__ void lds16(const void *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);
 }
 
-template <class S>
+// CIP (FP64 fields): the Ci box holds Ci as pairs (pair_ci, formed once per
+// run by k_pair_ci) instead of the FP64 values; the FP64 sum then reads Ci
+// from memory.
+template <class S, bool CIP>
 __global__ void __launch_bounds__(32 * AdjShape<S>::WARPS, AdjShape<S>::MINB)
     k_adjoint_tma(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mC,
                   const __grid_constant__ CUtensorMap mT, const __grid_constant__ CUtensorMap mG,
@@ -193,7 +196,13 @@ __global__ void __launch_bounds__(32 * AdjShape<S>::WARPS, AdjShape<S>::MINB)
         if (l) l[i] = a.v[i];
         if (lq) lq[i] = qq;
         t[i] = d.v[i];
-        v[i] = Ops::v(qq, b.v[i], xyin[i] && zi);
+        if constexpr (CIP) {
+          FF cp;
+          memcpy(&cp, &b.v[i], 8);
+          v[i] = adj_v_pairs(qq, cp, xyin[i] && zi);
+        } else {
+          v[i] = Ops::v(qq, b.v[i], xyin[i] && zi);
+        }
       }
     };
     // the v plane of plane p from load kk: own values v, the ring from the boxes
@@ -205,8 +214,15 @@ __global__ void __launch_bounds__(32 * AdjShape<S>::WARPS, AdjShape<S>::MINB)
       const S *L = box(kk, 0), *C = box(kk, 1);
       const bool zi = zin(p);
 #pragma unroll
-      for (int j = 0; j < Sh::RPT; ++j)
-        if (rb[j] >= 0) vb[rb[j]] = Ops::v(Ops::lam(L[rb[j]]), C[rb[j]], rxy[j] && zi);
+      for (int j = 0; j < Sh::RPT; ++j) {
+        if (rb[j] < 0) continue;
+        if constexpr (CIP) {
+          vb[rb[j]] = adj_v_pairs(Ops::lam(L[rb[j]]), reinterpret_cast<const FF *>(C)[rb[j]],
+                                  rxy[j] && zi);
+        } else {
+          vb[rb[j]] = Ops::v(Ops::lam(L[rb[j]]), C[rb[j]], rxy[j] && zi);
+        }
+      }
     };
     // load of plane m0 - 1 (own values), then of plane m0 (own values, v plane)
     bool good = wait_full(k);
@@ -274,15 +290,23 @@ __global__ void __launch_bounds__(32 * AdjShape<S>::WARPS, AdjShape<S>::MINB)
                 return xx >= 1 && xx <= nx - 2 && yy >= 1 && yy <= ny - 2 && zz >= 1 &&
                        zz <= nz - 2;
               };
-              auto v64 = [&](int bb, int xx, int yy) {
-                return adj_v64(L[bb], C[bb], in3(xx, yy, m));
+              // Ci of an inner point: from the box, or (pairs in the box)
+              // from memory
+              auto ci_at = [&](const S *Cb, int bb, int xx, int yy, int zz) -> double {
+                if constexpr (CIP) return Ci[xx + (long long)nx * yy + sz * zz];
+                else return Cb[bb];
               };
-              const bool inm = in3(x, y, m - 1);
+              auto v64 = [&](int bb, int xx, int yy) {
+                const bool in = in3(xx, yy, m);
+                return in ? adj_v64(L[bb], ci_at(C, bb, xx, yy, m), true) : 0.0;
+              };
+              const bool inm = in3(x, y, m - 1), inp = in3(x, y, m + 1);
               const long long pm = x + (long long)nx * y + sz * (m - 1);
               out[i] = adj_out_f64(lc[i], v64(b, x, y), v64(b - 1, x - 1, y), v64(b + 1, x + 1, y),
                                    v64(b - BW, x, y - 1), v64(b + BW, x, y + 1),
                                    adj_v64(inm ? lam_in[pm] : 0.0, inm ? Ci[pm] : 0.0, inm),
-                                   adj_v64(Ln[b], Cn[b], in3(x, y, m + 1)), aw.w);
+                                   inp ? adj_v64(Ln[b], ci_at(Cn, b, x, y, m + 1), true) : 0.0,
+                                   aw.w);
             }
           }
         }
@@ -357,33 +381,34 @@ __global__ void __launch_bounds__(32 * AdjShape<S>::WARPS, AdjShape<S>::MINB)
   }
 }
 
-template <class S>
+template <class S, bool CIP>
 cudaError_t prepare_adj_t(int *ctas_per_sm) {
   using Sh = AdjShape<S>;
   static cudaError_t done = cudaErrorNotReady;
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
   if (done == cudaErrorNotReady)
-    done = cudaFuncSetAttribute(k_adjoint_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Sh::SMEM);
+    done = cudaFuncSetAttribute(k_adjoint_tma<S, CIP>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   if (done != cudaSuccess) return done;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_adjoint_tma<S>,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_adjoint_tma<S, CIP>,
                                                        32 * Sh::WARPS, Sh::SMEM);
 }
 
-template <class S>
+template <class S, bool CIP>
 cudaError_t launch_adj_t(int nx, int ny, int nz, void *lam_out, const void *lam_in, const void *Tn,
-                         const void *Ci, double *gCi, const Coef &c, unsigned *dev_err,
-                         cudaStream_t s) {
+                         const void *Ci, const void *ci_box, double *gCi, const Coef &c,
+                         unsigned *dev_err, cudaStream_t s) {
   using Sh = AdjShape<S>;
   CUtensorMap mL, mC, mT, mG;
+  // the Ci box: FP64 values, or their pairs (8 bytes each, the same box)
   if (!encode<S>(&mL, lam_in, nx, ny, nz, Sh::BW, Sh::BH, 1) ||
-      !encode<S>(&mC, Ci, nx, ny, nz, Sh::BW, Sh::BH, 1) ||
+      !encode<S>(&mC, ci_box, nx, ny, nz, Sh::BW, Sh::BH, 1) ||
       !encode<S>(&mT, Tn, nx, ny, nz, Sh::BW, Sh::BH, 1) ||
       !encode<double>(&mG, gCi, nx, ny, nz, Sh::W, Sh::H, 1))
     return cudaErrorInvalidValue;
   int per_sm = 0, dev = 0, sms = 0;
-  cudaError_t e = prepare_adj_t<S>(&per_sm);
+  cudaError_t e = prepare_adj_t<S, CIP>(&per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -392,10 +417,18 @@ cudaError_t launch_adj_t(int nx, int ny, int nz, void *lam_out, const void *lam_
   const long long U = (long long)ncx * ncy * nz;
   // every CTA gets at least a few planes; at most the resident CTAs
   const long long G = std::min<long long>((long long)per_sm * sms, std::max<long long>(1, U / 4));
-  k_adjoint_tma<S><<<(unsigned)G, 32 * Sh::WARPS, Sh::SMEM, s>>>(
+  k_adjoint_tma<S, CIP><<<(unsigned)G, 32 * Sh::WARPS, Sh::SMEM, s>>>(
       mL, mC, mT, mG, nx, ny, nz, ncx, ncx * ncy, (S *)lam_out, (const S *)lam_in,
       (const S *)Ci, gCi, c, dev_err);
   return cudaGetLastError();
+}
+
+// Ci as pairs (pair_ci), once per checkpointed run
+__global__ void __launch_bounds__(256) k_pair_ci(const double *__restrict__ Ci, FF *__restrict__ out,
+                                                 long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = pair_ci(__ldg(Ci + i));
 }
 
 }  // namespace
@@ -415,15 +448,29 @@ bool adjoint_tma_applies(igg_dtype dt, int nx, const void *lam_out, const void *
 
 cudaError_t launch_adjoint_tma(igg_dtype dt, int nx, int ny, int nz, void *lam_out,
                                const void *lam_in, const void *Tn, const void *Ci, double *gCi,
-                               const Coef &c, unsigned *dev_err, cudaStream_t s) {
+                               const Coef &c, unsigned *dev_err, cudaStream_t s,
+                               const void *ci_pairs) {
   switch (dt) {
     case IGG_F64:
-      return launch_adj_t<double>(nx, ny, nz, lam_out, lam_in, Tn, Ci, gCi, c, dev_err, s);
+      if (ci_pairs)
+        return launch_adj_t<double, true>(nx, ny, nz, lam_out, lam_in, Tn, Ci, ci_pairs, gCi, c,
+                                          dev_err, s);
+      return launch_adj_t<double, false>(nx, ny, nz, lam_out, lam_in, Tn, Ci, Ci, gCi, c,
+                                         dev_err, s);
     case IGG_F32:
-      return launch_adj_t<float>(nx, ny, nz, lam_out, lam_in, Tn, Ci, gCi, c, dev_err, s);
+      return launch_adj_t<float, false>(nx, ny, nz, lam_out, lam_in, Tn, Ci, Ci, gCi, c,
+                                        dev_err, s);
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_pair_ci(const void *Ci, void *pairs, long long n, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 8 * 152) blocks = 8 * 152;
+  if (blocks < 1) blocks = 1;
+  k_pair_ci<<<(unsigned)blocks, 256, 0, s>>>((const double *)Ci, (FF *)pairs, n);
+  return cudaGetLastError();
 }
 
 }  // namespace igg

@@ -224,17 +224,23 @@ cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
                         cudaStream_t s);
 
 // Adjoint step over every point of one array, and out = a - b elementwise.
-// With `tma`, fields that allow it take the TMA-pipelined kernel.
+// With `tma`, fields that allow it take the TMA-pipelined kernel; FP64 fields
+// with `ci_pairs` (Ci as pairs from launch_pair_ci, n elements of 8 bytes)
+// load those instead of splitting Ci (same results).
 cudaError_t launch_adjoint(igg_dtype dt, int nx, int ny, int nz, void *lam_out,
                            const void *lam_in, const void *Tn, const void *Ci, double *gCi,
-                           const Coef &c, bool tma, unsigned *dev_err, cudaStream_t s);
+                           const Coef &c, bool tma, unsigned *dev_err, cudaStream_t s,
+                           const void *ci_pairs = nullptr);
 // TMA adjoint kernel: applies to F64/F32 rows of a multiple of 16 bytes and
 // 16-byte aligned fields (and a driver with tensor maps).
 bool adjoint_tma_applies(igg_dtype dt, int nx, const void *lam_out, const void *lam_in,
                          const void *Tn, const void *Ci, const double *gCi);
 cudaError_t launch_adjoint_tma(igg_dtype dt, int nx, int ny, int nz, void *lam_out,
                                const void *lam_in, const void *Tn, const void *Ci, double *gCi,
-                               const Coef &c, unsigned *dev_err, cudaStream_t s);
+                               const Coef &c, unsigned *dev_err, cudaStream_t s,
+                               const void *ci_pairs = nullptr);
+// FP64 Ci (n values) as pairs for the adjoint kernel (8 bytes each)
+cudaError_t launch_pair_ci(const void *Ci, void *pairs, long long n, cudaStream_t s);
 cudaError_t launch_sub(igg_dtype dt, long long n, void *out, const void *a, const void *b,
                        cudaStream_t s);
 

@@ -1304,6 +1304,22 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
   const char *K = (const char *)ckpt;
   char *S = (char *)seg, *LA = (char *)work, *LB = (char *)work + bytes;
   const Coef c = make_coef(lam, dtime, dx, dy, dz);
+  // FP64 fields on the TMA kernel: Ci split into pairs once for the run
+  // (stream-ordered scratch, freed on every exit)
+  struct Scratch {
+    void *p = nullptr;
+    cudaStream_t s;
+    ~Scratch() {
+      if (p) cudaFreeAsync(p, s);
+    }
+  } ci_pairs;
+  ci_pairs.s = s;
+  if (dt == IGG_F64 && g->tma_enabled &&
+      adjoint_tma_applies(dt, g->n[0], work, lam_nt, ckpt, Ci, gCi)) {
+    cudaError_t ea = cudaMallocAsync(&ci_pairs.p, (size_t)g->nloc * 8, s);
+    if (ea == cudaSuccess) ea = launch_pair_ci(Ci, ci_pairs.p, g->nloc, s);
+    if (ea != cudaSuccess) return cuda_error(ea, "Ci pairs");
+  }
   cudaError_t e = cudaMemcpyAsync(LA, lam_nt, bytes, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(gCi, 0, (size_t)g->nloc * sizeof(double), s);
   // segment buffers carry the fixed boundary values of T0 (steps write inner points only)
@@ -1322,7 +1338,7 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
     for (int j = len - 1; j >= 0; --j) {
       char *nxt = cur == LA ? LB : LA;
       e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], nxt, cur, state(j), Ci, gCi, c,
-                         g->tma_enabled, g->dev_err, s);
+                         g->tma_enabled, g->dev_err, s, ci_pairs.p);
       if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
       cur = nxt;
     }

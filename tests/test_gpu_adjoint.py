@@ -289,3 +289,30 @@ def test_adjoint_gci_paths_crossing_powers_of_two_and_zero(tma):
     assert status == 0
     assert np.abs(gg - ref_g).max() <= 1e-12 * np.abs(ref_g).max()
     assert np.abs(o - ref_out).max() <= 1e-12 * np.abs(ref_out).max()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_checkpointed_gradient_tma_and_tiled_same_bits(dtype):
+    """The checkpointed run on the TMA kernel (FP64: Ci split into pairs once
+    per run) and on the tiled kernel give the same bits; some Ci lie outside
+    the pair range (their points take the FP64 sum, Ci read from memory)."""
+    n = (66, 17, 12)
+    nt, every = 9, 4
+    T0, Ci, Ci_star, dd, dt = case(n)
+    Cm = np.where(np.random.default_rng(5).random(Ci.shape) < 0.05, 1e-9, Ci)
+    T_obs = oracle.forward_states(T0, Ci_star, nt, 1.0, dt, *dd)[-1]
+    res = []
+    for tma in (True, False):
+        with igg.Grid(n) as g:
+            g.set_option(igg.Grid.OPT_TMA, 1 if tma else 0)
+            T0d, Cd, Od = (dev(a, dtype) for a in (T0, Cm, T_obs))
+            T_nt, ckpt = ag.forward_checkpointed(g, nt, every, T0d, Cd, 1.0, dt, *dd)
+            gT, gC = ag.adjoint_checkpointed(g, nt, every, ckpt, Cd, ag.residual(T_nt, Od), 1.0, dt, *dd)
+            torch.cuda.synchronize()
+            assert g.device_status() == 0
+            res.append((gT.double().cpu().numpy(), gC.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    if dtype == torch.float64:
+        J, gT0, gCi = oracle.gradient(T0, np.ascontiguousarray(Cm), T_obs, nt, 1.0, dt, *dd)
+        assert np.linalg.norm(res[0][0][0] - gT0) <= 1e-10 * np.linalg.norm(gT0)
+        assert np.linalg.norm(res[0][1][0] - gCi) <= 1e-10 * np.linalg.norm(gCi)
