@@ -410,7 +410,9 @@ int igg_forward_checkpointed(igg_grid *grid, int nt, int every, const void *T0,
  * its checkpoint (into `seg`, every-1 fields; unused when every == 1) and
  * runs the adjoint steps backward in time. Writes gT0 = dJ/dT_0 (dtype
  * field) and gCi = dJ/dCi (FP64 field, overwritten). `work` holds two fields.
- * Memory: (ceil(nt/every) + every + 3) fields instead of nt + 1. */
+ * Memory: (ceil(nt/every) + every + 3) fields instead of nt + 1; F64 fields
+ * on the TMA kernel also take, for the run, a scratch of 8 bytes per point
+ * (Ci as float pairs) from the stream-ordered allocator on `stream`. */
 int igg_adjoint_checkpointed(igg_grid *grid, int nt, int every,
                              const void *ckpt, const void *Ci,
                              const void *lam_nt, igg_dtype dtype, double lam,
