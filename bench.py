@@ -207,14 +207,24 @@ def step_samples(fn, n, stream, steps_per_call):
         fn()
         b.record(stream)
     _t.cuda.synchronize()
-    t = sorted(a.elapsed_time(b) / steps_per_call for a, b in evs)
+    t = [a.elapsed_time(b) / steps_per_call for a, b in evs]
+    med, lo, hi = median_ci95(t)
+    return {"n": n, "steps_per_sample": steps_per_call, "median_ms_per_step": round(med, 4),
+            "ci95_ms_per_step": [round(lo, 4), round(hi, 4)],
+            "min_ms_per_step": round(min(t), 4), "max_ms_per_step": round(max(t), 4)}
+
+
+def median_ci95(samples):
+    """Median of the samples and the distribution-free 95 % confidence
+    interval of the median: the order statistics at ranks n/2 -+ 1.96 sqrt(n)/2
+    (1-based, rounded outward, clamped to the sample)."""
+    t = sorted(samples)
+    n = len(t)
     half = 1.959964 * math.sqrt(n) / 2
     lo = max(0, int(math.floor(n / 2 - half)) - 1)
     hi = min(n - 1, int(math.ceil(n / 2 + half)) - 1)
     med = 0.5 * (t[(n - 1) // 2] + t[n // 2])
-    return {"n": n, "steps_per_sample": steps_per_call, "median_ms_per_step": round(med, 4),
-            "ci95_ms_per_step": [round(t[lo], 4), round(t[hi], 4)],
-            "min_ms_per_step": round(t[0], 4), "max_ms_per_step": round(t[-1], 4)}
+    return med, t[lo], t[hi]
 
 
 def _timed(fn, reps):

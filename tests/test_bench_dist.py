@@ -66,3 +66,23 @@ def test_reference_arm_two_ranks():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_median_ci95_order_statistics():
+    """The step-sample interval: median of the samples and the order
+    statistics at ranks n/2 -+ 1.96 sqrt(n)/2; for 40 samples ranks 13 and 27
+    (1-based). Coverage of the true median checked on seeded samples."""
+    import random
+    sys.path.insert(0, ROOT)
+    import bench
+    med, lo, hi = bench.median_ci95(list(range(40, 0, -1)))  # 1..40 reversed
+    assert med == 20.5 and lo == 13 and hi == 27
+    med, lo, hi = bench.median_ci95([5.0])
+    assert med == lo == hi == 5.0
+    rng = random.Random(3)
+    hits = 0
+    for _ in range(2000):
+        xs = [rng.expovariate(1.0) for _ in range(40)]
+        _, a, b = bench.median_ci95(xs)
+        hits += a <= 0.6931471805599453 <= b  # median of Exp(1) = ln 2
+    assert 0.93 <= hits / 2000 <= 0.99
