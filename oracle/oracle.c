@@ -137,16 +137,17 @@ void oracle_update_halo(int nsub, const int *left_nb, const int *right_nb,
         long src_plane = side == 0 ? n[d] - o : o - 1;
         unsigned char *dst = base + (size_t)s * nloc * es;
         const unsigned char *src = base + (size_t)nb * nloc * es;
-        for (long iz = 0; iz < nz; ++iz)
-          for (long iy = 0; iy < ny; ++iy)
-            for (long ix = 0; ix < nx; ++ix) {
-              long c[3] = {ix, iy, iz};
-              if (c[d] != dst_plane) continue;
-              long cs[3] = {ix, iy, iz};
-              cs[d] = src_plane;
-              memcpy(dst + AT(c[0], c[1], c[2]) * es,
-                     src + AT(cs[0], cs[1], cs[2]) * es, es);
-            }
+        /* every point of the plane: the two other dimensions a, b, all indices */
+        const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+        for (long ib = 0; ib < n[db]; ++ib)
+          for (long ia = 0; ia < n[da]; ++ia) {
+            long c[3], cs[3];
+            c[d] = dst_plane;
+            cs[d] = src_plane;
+            c[da] = cs[da] = ia;
+            c[db] = cs[db] = ib;
+            memcpy(dst + AT(c[0], c[1], c[2]) * es, src + AT(cs[0], cs[1], cs[2]) * es, es);
+          }
       }
     }
   }
