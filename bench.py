@@ -170,7 +170,7 @@ def grid_launches_per_hidden_step(grid, w, dtype="f64", f64_emu=True, fused=True
     Split: the two boundary launches (z slabs with the x ends, y slabs), the
     halo copies of each dimension with neighbours, and the inner block.  With
     the emulated FP64 cell every stencil launch is followed by its fix-up."""
-    per_stencil = 2 if (dtype == "f64" and f64_emu) else 1
+    per_stencil = 1
     if fused:
         return per_stencil
     dims, periods = grid.dims, grid.periods

@@ -121,14 +121,17 @@ int igg_subdomain_info(const igg_grid *grid, int sub, int coords[3],
 /* ---------------------------------------------------------------------------
  * Halo update (update_halo!, Sec. Approach; Fig. 1 update_halo!(T2)).
  *
- * For each of the nfields fields (device pointers of `dtype`, layout above)
- * and for the dimensions in the order x, y, z: every subdomain's first
- * plane (index 0) receives plane n-o of its left neighbour, and its last
- * plane (index n-1) receives plane o-1 of its right neighbour. Whole planes
- * are copied, including points in other dimensions' halos, so edges and
- * corners end up exactly as after the sequential x, y, z exchange. The copy
- * is bit exact. One launch per dimension serves all the fields. Work is
- * ordered on `stream`.
+ * For each of the nfields fields (device pointers of `dtype`, layout above),
+ * the result of this exchange for the dimensions in the order x, y, z:
+ * every subdomain's first plane (index 0) receives plane n-o of its left
+ * neighbour, and its last plane (index n-1) receives plane o-1 of its right
+ * neighbour. Whole planes, including points in other dimensions' halos, so
+ * edges and corners end up exactly as after the sequential x, y, z exchange.
+ * The copy is bit exact. On 3-D grids each field takes one launch that
+ * gathers every halo cell's value directly from the point the sequential
+ * copies would bring to it (following them back: z, then y, then x); 2-D and
+ * 1-D grids take one plane-copy launch per dimension for all the fields.
+ * Work is ordered on `stream`.
  * ------------------------------------------------------------------------- */
 int igg_update_halo(igg_grid *grid, void *const fields[], int nfields,
                     igg_dtype dtype, void *stream);
@@ -180,20 +183,19 @@ int igg_selftest_bounded_wait(unsigned *status);
  *     selects the register-pipelined vector kernel. Bit-identical results.
  *   IGG_OPT_F64_EMU (default 1): F64 fields use the emulated FP64 cell: for
  *     points whose 7 stencil values share sign and exponent, the second
- *     differences are formed exactly in integers, weighted in float-float
- *     and applied with two FP64 FMAs (per-step error about 2^-44 of
- *     sum_d |w_d D_d| plus two FP64 roundings of T2); other points, and all
- *     points with 0, use the FP64 cell (8 FP64 instructions per point).
+ *     differences are formed exactly from the bit patterns as integers,
+ *     weighted in float-float pairs and applied with one FP64 FMA and an
+ *     integer ulp correction (per-step error within about one ulp of T2 plus
+ *     2^-44 of Ci sum_d |w_d D_d|); stencils across one power of two take
+ *     the same sums from shifted significands and two FP64 FMAs; other
+ *     points, and all points with 0 (or weights above 2^40), use the FP64
+ *     cell (8 FP64 instructions per point).
  *   IGG_OPT_FUSED_HALO (default 1): igg_step_hidden (and igg_run with
- *     widths) on TMA kernels with n[d] >= 2*overlap[d] in every dimension fuse
- *     the halo update into the step instead of splitting it: one launch
- *     computes every inner point and also stores each point of a sent plane
- *     into the halo cells that the plane copies would give it (all subdomains
- *     being in the device's memory, nothing is left to overlap); 0 selects
- *     the boundary/inner split described at igg_step_hidden. Bit-identical
- *     results for fields whose halo cells at the global boundary agree
- *     between neighbouring subdomains (as when every subdomain is set from
- *     one global field). */
+ *     widths) run as the full step launch followed by the one-launch halo
+ *     update (all subdomains being in the device's memory, no transfer is
+ *     left to overlap, and the split's extra launches cost more than they
+ *     hide); 0 selects the boundary/inner split described at
+ *     igg_step_hidden. Bit-identical results either way. */
 #define IGG_OPT_TMA 1
 #define IGG_OPT_F64_EMU 2
 #define IGG_OPT_FUSED_HALO 3
@@ -215,7 +217,9 @@ int igg_step(igg_grid *grid, void *T2, const void *T, const void *Ci,
              double dz, void *stream);
 
 /* Fig. 1 @hide_communication widths begin step!(T2,T,...); update_halo!(T2)
- * end: the step on the boundary set of every subdomain (inner points whose
+ * end. By default (IGG_OPT_FUSED_HALO = 1) this is the full step launch
+ * followed by the one-launch halo update of T2, on `stream`. With the option
+ * 0 it is the paper's split: the step on the boundary set of every subdomain (inner points whose
  * 1-based index i has i <= w or i >= n - w + 1 in some dimension, w =
  * widths[d]) runs first on the library's high-priority stream, followed
  * there by the halo update of T2; the inner block runs concurrently on the
@@ -240,6 +244,22 @@ int igg_step_hidden(igg_grid *grid, const int widths[3], void *T2,
 int igg_run(igg_grid *grid, int nt, const int widths[3], void *T, void *T2,
             const void *Ci, igg_dtype dtype, double lam, double dt, double dx,
             double dy, double dz, void *stream);
+
+/* Fig. 1's solver end to end for callers whose fields live in host memory:
+ * on `stream`, copy T0 from T_host into the device buffer T and Ci from
+ * Ci_host into Ci, set T2 = copy(T) on the device (Fig. 1), run igg_run's
+ * nt steps (widths as there), and copy the newest state back into T_host.
+ * T_host and Ci_host hold nsub*nloc elements each in the fields' layout
+ * [nsub][nz][ny][nx]; page-locked host memory keeps the copies asynchronous
+ * (pageable memory works, but its copies block the calling thread). T, T2
+ * and Ci are the caller's device buffers (16-byte aligned, overwritten).
+ * The call only enqueues: synchronise `stream` before reading T_host.
+ * Errors: IGG_EINVAL for NULL host pointers and igg_run's conditions;
+ * IGG_ECUDA if a copy cannot be enqueued. */
+int igg_run_host(igg_grid *grid, int nt, const int widths[3], void *T_host,
+                 const void *Ci_host, void *T, void *T2, void *Ci, igg_dtype dtype,
+                 double lam, double dt, double dx, double dy, double dz,
+                 void *stream);
 
 /* ---------------------------------------------------------------------------
  * Staggered-grid acoustics: a multi-field stencil on the grid's regular

@@ -56,11 +56,13 @@ struct W {
 };
 
 // FP64 weights: the doubles, the same weights as float pairs wh + wl for the
-// emulated FP64 cell, and which cell to use.
+// emulated FP64 cell (and scaled copies of them for its fast path: ah, al =
+// 2^23 wh, 2^23 wl), and which cell to use.
 template <>
 struct W<double> {
   double wx, wy, wz, wc;
   float wh[3], wl[3];
+  float ah[3], al[3];
   bool emu;
   int ng;  // weight groups (weight_groups)
 };
@@ -76,6 +78,8 @@ __device__ __forceinline__ W<double> make_w(const Coef &c, double) {
   for (int i = 0; i < 3; ++i) {
     w.wh[i] = __double2float_rn(d[i]);
     w.wl[i] = __double2float_rn(__dsub_rn(d[i], (double)w.wh[i]));
+    w.ah[i] = __fmul_rn(w.wh[i], 8388608.0f);
+    w.al[i] = __fmul_rn(w.wl[i], 8388608.0f);
   }
   w.emu = c.f64_emu != 0;
   w.ng = weight_groups(c.wx, c.wy, c.wz);
@@ -293,20 +297,6 @@ __device__ __forceinline__ bool emu_spread_d(double tc, const unsigned long long
   return ok;
 }
 
-// The emulated update of a fast-path point: tc + ci * l(T).
-template <int NG>
-__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
-                                                double ci, const W<double> &w) {
-  return emu_apply(tc, ci, emu_lap<NG>(tc, nb, w));
-}
-
-__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
-                                                double ci, const W<double> &w) {
-  if (w.ng == 1) return cell_emu_fast<1>(tc, nb, ci, w);
-  if (w.ng == 2) return cell_emu_fast<2>(tc, nb, ci, w);
-  return cell_emu_fast<3>(tc, nb, ci, w);
-}
-
 // The emulated update of a stencil crossing one power of two (emu_spread_d
 // holds): tc + ci * l(T) from the shifted significands' differences.
 __device__ __forceinline__ double cell_emu_spread(double tc, const long long *D, unsigned sh,
@@ -316,19 +306,203 @@ __device__ __forceinline__ double cell_emu_spread(double tc, const long long *D,
   return emu_apply(tc, ci, emu_lap_d<3>(D, sh, w));
 }
 
-// One point: the emulated cell where its fast path applies, else where the
-// stencil crosses one power of two the emulated cell from shifted
+// ---------------------------------------------------------------------------
+// Fast path of the emulated FP64 cell: one FP64 FMA per point.
+//
+// In units of u = ulp(T) = 2^(E-1075) the update of a stencil whose seven
+// values share sign and exponent field E is an update of the bit pattern:
+// with the exact integer group sums G_g of the bit-pattern second
+// differences (as above, negated differences for negative values included),
+//   bits(T2) = bits(T) + Ci * sum_g w_g G_g
+// for as long as T2 stays in T's binade. Each G_g is split exactly into
+// G_g = Gh 2^23 + Gl with |Gl| <= 2^22 (Gh = (G_g + 2^22) >> 23; the fast
+// path requires |Gh| < 2^24, i.e. |G_g| < 2^47, so that both halves are
+// FP32 numbers; Gl is read off its bits as 2^23 + 2^22 + Gl, an FP32 number
+// with exponent 23, minus 1.5 2^23). With the weights as float pairs,
+// S + C = sum_g w_g G_g is formed from error-free FMA products (2^23 wh) Gh,
+// the small terms (2^23 wl) Gh and wh Gl, and a two-sum of the leading
+// products, to about 2^-46 of sum_g |w_g G_g|. Then
+//   T2 = fma(+-Ci, |S| u, T)   (the only FP64 instruction; |S| u widened
+//                              to FP64 by moving the FP32 fields),
+//   bits(T2) += rint(Ci_f C)   (Ci_f: Ci truncated to 24 bits; rint by
+//                              an FP32 FMA adding 1.5 2^23),
+// within about one ulp of T2 plus 2^-44 of Ci sum_g |w_g G_g| of the exact
+// update. The FP32 arithmetic of the sums runs on pairs of points (float2
+// instructions) in the TMA kernel and on single points elsewhere, with the
+// same per-point roundings, so both give the same bits.
+//
+// The fast path applies when the seven values share sign and exponent field
+// E in [180, 2008], every |Gh| < 2^24, Ci is positive with its exponent in
+// the FP32 range, |Ci_f C| < 2^22 and T2 (after the correction) keeps T's
+// sign and exponent. With |w| <= 2^40 (the host's condition for the emulated
+// cell) |S| < 2^90, so |S| u is a normal double for every such E. E, and the
+// sign, enter only through the centre; when a point's stencil passes, its
+// row neighbour shares them, so the TMA kernel's pairs of points take both
+// from the first point of the pair.
+// ---------------------------------------------------------------------------
+// Pairs of FP32 numbers use the packed instructions. The sums below are
+// written so that no product feeds an addition (products are FMAs with a
+// zero addend, or folded into the FMA that uses them): the compiler may fuse
+// a packed multiply into a following packed addition, which would change the
+// rounding against the scalar form.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vset(float w, float) { return w; }
+__device__ __forceinline__ float2 vset(float w, float2) { return make_float2(w, w); }
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+
+// error-free sum a + b = s + e (Knuth's two-sum), per lane
+template <class V>
+__device__ __forceinline__ V vtwo_sum(V a, V b, V &e) {
+  const V s = vadd(a, b);
+  const V bb = vadd(s, vneg(a));
+  e = vadd(vadd(a, vneg(vadd(s, vneg(bb)))), vadd(b, vneg(bb)));
+  return s;
+}
+
+// The centre's part of the fast-path test: sign and exponent field E in
+// [180, 2008] (hc: the centre's high word).
+__device__ __forceinline__ bool emu2_centre_ok(unsigned hc) {
+  return (hc & 0x7FF00000u) - (180u << 20) < (1829u << 20);
+}
+
+// Integer part of the fast path for one point: the group sums of the bit-
+// pattern second differences, split into Gh (exact FP32 for |Gh| < 2^24)
+// and the bits gm of the FP32 number 1.5 2^23 + Gl. True when the seven
+// values share sign and exponent and every |Gh| < 2^24 (the centre's own
+// test is emu2_centre_ok). nb: x-, x+, y-, y+, z-, z+.
+template <int NG>
+__device__ __forceinline__ bool emu2_int(unsigned long long bc, const unsigned long long *nb,
+                                         int *gh, unsigned *gm) {
+  const unsigned hc = (unsigned)(bc >> 32);
+  unsigned o = 0u;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) o |= (unsigned)(nb[i] >> 32) ^ hc;
+  const unsigned long long c2 = bc << 1, B = 1ull << 22;
+  unsigned long long G[NG];  // G_g + 2^22 (mod 2^64)
+  if constexpr (NG == 1) {
+    G[0] = (nb[0] + nb[1] - c2) + (nb[2] + nb[3] - c2) + (nb[4] + nb[5] - c2) + B;
+  } else if constexpr (NG == 2) {
+    G[0] = nb[0] + nb[1] - c2 + B;
+    G[1] = (nb[2] + nb[3] - c2) + (nb[4] + nb[5] - c2) + B;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) G[d] = nb[2 * d] + nb[2 * d + 1] - c2 + B;
+  }
+  unsigned r = 0u;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const unsigned lo = (unsigned)G[g];
+    gh[g] = (int)__funnelshift_r(lo, (unsigned)(G[g] >> 32), 23);
+    gm[g] = (lo & 0x7FFFFFu) | 0x4B000000u;
+    r |= (unsigned)gh[g] + (1u << 24);
+  }
+  return o < (1u << 20) && r < (1u << 25);
+}
+
+// S + C = sum_g w_g G_g from the FP32 halves (per lane: one point or two);
+// gl holds the FP32 numbers 1.5 2^23 + Gl.
+template <int NG, class V>
+__device__ __forceinline__ void emu2_sum(const V *gh, const V *gl, const W<double> &w, V &S,
+                                         V &C) {
+  V P[NG], E[NG], L[NG];
+  const V zero = vset(0.0f, V());
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const V a = vset(w.ah[g], V());
+    P[g] = vfma(a, gh[g], zero);  // the rounded product
+    E[g] = vfma(a, gh[g], vneg(P[g]));
+    L[g] = vadd(gl[g], vset(-kMagic, V()));  // Gl, exact
+  }
+  V R = vfma(vset(w.wh[0], V()), L[0], zero);
+#pragma unroll
+  for (int g = 1; g < NG; ++g) R = vfma(vset(w.wh[g], V()), L[g], R);
+#pragma unroll
+  for (int g = 0; g < NG; ++g) R = vfma(vset(w.al[g], V()), gh[g], R);
+  if constexpr (NG == 1) {
+    S = P[0];
+    C = vadd(E[0], R);
+  } else if constexpr (NG == 2) {
+    V e;
+    S = vtwo_sum(P[0], P[1], e);
+    C = vadd(vadd(E[0], E[1]), vadd(e, R));
+  } else {
+    V e1, e2;
+    S = vtwo_sum(vtwo_sum(P[0], P[1], e1), P[2], e2);
+    C = vadd(vadd(vadd(E[0], E[1]), vadd(E[2], e1)), vadd(e2, R));
+  }
+}
+
+// Ci truncated to an FP32 number (meaningful when emu2_apply's Ci condition
+// holds: Ci positive with its exponent field in [897, 1150]).
+__device__ __forceinline__ float emu2_cif(double ci) {
+  return __uint_as_float(__funnelshift_l((unsigned)__double2loint(ci),
+                                         (unsigned)__double2hiint(ci) - (896u << 20), 3));
+}
+
+// T2 of a fast-path point from S and Kr = fma(Ci_f, C, 1.5 2^23) (one
+// rounding: the nearest integer to Ci_f C is bits(Kr) - 0x4B400000 when
+// |Ci_f C| < 2^22);
+// hc: the high word that gives the point's sign and exponent (see above);
+// ok is cleared where the remaining conditions fail.
+__device__ __forceinline__ double emu2_apply(unsigned long long bc, unsigned hc, double ci,
+                                             float S, float Kr, bool &ok) {
+  const unsigned sb = __float_as_uint(S);
+  const unsigned eoff = (hc & 0x7FF00000u) - (179u << 20);
+  const double sd = __hiloint2double((int)(((sb << 1) >> 4) + eoff), (int)(sb << 29));
+  const unsigned cih = (unsigned)__double2hiint(ci);
+  const double sci = __hiloint2double((int)(cih ^ ((hc ^ sb) & 0x80000000u)), __double2loint(ci));
+  const double t2 = __fma_rn(sci, sd, __longlong_as_double((long long)bc));
+  const unsigned long long r =
+      dbits(t2) + (unsigned long long)__float_as_uint(Kr) - 0x4B400000ull;
+  ok = ok && cih - (897u << 20) < (254u << 20) && fabsf(Kr - kMagic) < 4194304.0f &&
+       (((unsigned)(r >> 32) ^ (unsigned)(bc >> 32)) & 0xFFF00000u) == 0u;
+  return __longlong_as_double((long long)r);
+}
+
+// The fast path for one point; ok tells whether it applies.
+template <int NG>
+__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
+                                                double ci, const W<double> &w, bool &ok) {
+  const unsigned long long bc = dbits(tc);
+  int gh[NG];
+  unsigned gm[NG];
+  ok = emu2_int<NG>(bc, nb, gh, gm) && emu2_centre_ok((unsigned)(bc >> 32));
+  float fh[NG], fl[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    fh[g] = __int2float_rn(gh[g]);
+    fl[g] = __uint_as_float(gm[g]);
+  }
+  float S, C;
+  emu2_sum<NG>(fh, fl, w, S, C);
+  const float Kr = __fmaf_rn(emu2_cif(ci), C, kMagic);
+  return emu2_apply(bc, (unsigned)(bc >> 32), ci, S, Kr, ok);
+}
+
+__device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
+                                                double ci, const W<double> &w, bool &ok) {
+  if (w.ng == 1) return cell_emu_fast<1>(tc, nb, ci, w, ok);
+  if (w.ng == 2) return cell_emu_fast<2>(tc, nb, ci, w, ok);
+  return cell_emu_fast<3>(tc, nb, ci, w, ok);
+}
+
+// One point: the emulated cell's fast path where it applies, else where the
+// stencil crosses at most one power of two the emulated cell from shifted
 // significands, else cell_f64.
 __device__ __forceinline__ double cell_emu(double tc, const double *tn, double ci,
                                            const W<double> &w) {
-  unsigned hn[6];
   unsigned long long nb[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    hn[i] = dhi(tn[i]);
-    nb[i] = dbits(tn[i]);
-  }
-  if (emu_fast_ok(dhi(tc), hn)) return cell_emu_fast(tc, nb, ci, w);
+  for (int i = 0; i < 6; ++i) nb[i] = dbits(tn[i]);
+  bool ok;
+  const double r = cell_emu_fast(tc, nb, ci, w, ok);
+  if (ok) return r;
   long long D[3];
   unsigned sh;
   if (emu_spread_d(tc, nb, D, sh)) return cell_emu_spread(tc, D, sh, ci, w);

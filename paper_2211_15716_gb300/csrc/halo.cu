@@ -1,10 +1,11 @@
-// Halo update kernel (update_halo!, Sec. Approach): on one GPU every
+// Halo update kernels (update_halo!, Sec. Approach): on one GPU every
 // neighbour lives in the same device memory, so packing, sending and
-// unpacking a face collapse into one device-to-device copy of the face plane
-// from the sending subdomain's array into the receiving subdomain's halo
-// plane. One launch copies all face planes of one dimension of one field;
-// the host issues the dimensions in the order x, y, z on one stream, which
-// gives edges and corners the values of the sequential exchange.
+// unpacking a face collapse into device-to-device copies. Fields of the
+// grid's own size take one gather launch (k_halo_gather, below); staggered
+// sizes take the plane copies: one launch copies all face planes of one
+// dimension of one field, the host issuing the dimensions in the order x, y,
+// z on one stream, which gives edges and corners the values of the
+// sequential exchange.
 #include <algorithm>
 
 #include "igg_internal.h"
@@ -64,6 +65,86 @@ __global__ void __launch_bounds__(256) k_halo_jobs(const HaloJobs jobs) {
   }
 }
 
+// The halo update of a field of the grid's own size in one launch (the
+// gather form of update_halo!): every halo cell receives the value that the
+// plane copies in the order x, y, z would leave in it. Following the copies
+// backwards from the cell (z, then y, then x), wherever its coordinate in
+// dimension d is 0 (n_d - 1) and its current subdomain has a left (right)
+// neighbour in d, the value comes from that neighbour's cell with coordinate
+// n_d - o_d (o_d - 1). The chain ends at a cell that no copy writes (an inner
+// point, or a boundary cell without neighbour), so the launch never reads a
+// cell it writes, and one launch gives the sequential result.
+//
+// One block per row of the subdomain's boundary shell: rows of the z faces
+// (2 ny per subdomain, x from 0 to nx - 1), of the y faces with z inner
+// (2 (nz - 2)), and the x face columns with y, z inner (2 (nz - 2), y along
+// the row). A face row's z and y steps are the same for every x: it is copied
+// as a whole from its source row, then its two end cells take their x step.
+__device__ __forceinline__ void gather_step(const HaloGather &h, int d, int &s, int &c,
+                                            bool &moved) {
+  const int side = c == 0 ? 0 : (c == h.n[d] - 1 ? 1 : -1);
+  if (side < 0) return;
+  const int nb = h.nbr[6 * s + 2 * d + side];
+  if (nb < 0) return;
+  s = nb;
+  c = side ? h.o[d] - 1 : h.n[d] - h.o[d];
+  moved = true;
+}
+
+template <class E, bool VEC>
+__global__ void __launch_bounds__(256) k_halo_gather(E *__restrict__ f, const HaloGather h) {
+  const int nx = h.n[0], ny = h.n[1], nz = h.n[2];
+  const int rows = 2 * ny + 4 * (nz - 2);
+  const int s0 = (int)(blockIdx.x / rows);
+  int row = (int)(blockIdx.x % rows);
+  const long long sy = nx, sz = (long long)nx * ny;
+  if (row < 2 * ny + 2 * (nz - 2)) {
+    int y, z;
+    if (row < 2 * ny) {
+      y = row % ny;
+      z = row < ny ? 0 : nz - 1;
+    } else {
+      row -= 2 * ny;
+      z = 1 + row % (nz - 2);
+      y = row < nz - 2 ? 0 : ny - 1;
+    }
+    int s = s0, cy = y, cz = z;
+    bool moved = false;
+    gather_step(h, 2, s, cz, moved);
+    gather_step(h, 1, s, cy, moved);
+    E *dst = f + (long long)s0 * h.nloc + sy * y + sz * z;
+    const E *src = f + (long long)s * h.nloc + sy * cy + sz * cz;
+    if (moved) {
+      if (VEC) {
+        const int nv = nx * (int)sizeof(E) / 16;
+        for (int i = threadIdx.x; i < nv; i += blockDim.x)
+          reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+      } else {
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) dst[x] = src[x];
+      }
+    }
+    __syncthreads();  // the row's end cells after its whole-row copy
+    if (threadIdx.x < 2) {
+      const int x = threadIdx.x ? nx - 1 : 0;
+      int ss = s, cx = x;
+      bool mx = false;
+      gather_step(h, 0, ss, cx, mx);
+      if (mx) dst[x] = f[(long long)ss * h.nloc + cx + sy * cy + sz * cz];
+    }
+  } else {
+    // an x face column: x = 0 or nx - 1, z inner, y = 1 .. ny - 2
+    row -= 2 * ny + 2 * (nz - 2);
+    const int z = 1 + row % (nz - 2), x = row < nz - 2 ? 0 : nx - 1;
+    int s = s0, cx = x;
+    bool moved = false;
+    gather_step(h, 0, s, cx, moved);
+    if (!moved) return;
+    E *dst = f + (long long)s0 * h.nloc + x + sz * z;
+    const E *src = f + (long long)s * h.nloc + cx + sz * z;
+    for (int y = 1 + threadIdx.x; y <= ny - 2; y += blockDim.x) dst[sy * y] = src[sy * y];
+  }
+}
+
 bool vec_rows(size_t elem_size, int na, long long sa, long long sb, const void *field) {
   return sa == 1 && ((long long)na * (long long)elem_size) % 16 == 0 && sb % na == 0 &&
          reinterpret_cast<uintptr_t>(field) % 16 == 0;
@@ -107,6 +188,34 @@ cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
     case 2: return launch_e<unsigned short>(copies, ncopies, field, na, nb, sa, sb, vec, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_halo_gather(size_t elem_size, void *field, const HaloGather &h,
+                               cudaStream_t s) {
+  if (h.n[0] < 3 || h.n[1] < 3 || h.n[2] < 3) return cudaErrorInvalidValue;
+  const long long blocks = (long long)h.nsub * (2 * h.n[1] + 4 * (h.n[2] - 2));
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks >= (1ll << 31)) return cudaErrorInvalidValue;
+  const bool vec = ((long long)h.n[0] * (long long)elem_size) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(field) % 16 == 0;
+  const unsigned b = (unsigned)blocks;
+  switch (elem_size) {
+    case 8:
+      if (vec) k_halo_gather<unsigned long long, true><<<b, 256, 0, s>>>((unsigned long long *)field, h);
+      else k_halo_gather<unsigned long long, false><<<b, 256, 0, s>>>((unsigned long long *)field, h);
+      break;
+    case 4:
+      if (vec) k_halo_gather<unsigned, true><<<b, 256, 0, s>>>((unsigned *)field, h);
+      else k_halo_gather<unsigned, false><<<b, 256, 0, s>>>((unsigned *)field, h);
+      break;
+    case 2:
+      if (vec) k_halo_gather<unsigned short, true><<<b, 256, 0, s>>>((unsigned short *)field, h);
+      else k_halo_gather<unsigned short, false><<<b, 256, 0, s>>>((unsigned short *)field, h);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace igg

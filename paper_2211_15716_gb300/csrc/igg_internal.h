@@ -51,6 +51,13 @@ __host__ __device__ inline int weight_groups(double wx, double wy, double wz) {
   return (wx == wy && wy == wz) ? 1 : (wy == wz ? 2 : 3);
 }
 
+// The emulated FP64 cell takes weights of magnitude at most 2^40 (its fast
+// path's FP32 products then stay finite); other weights use the FP64 cell.
+inline bool emu_weights_ok(const Coef &c) {
+  const double lim = 1099511627776.0;  // 2^40
+  return fabs(c.wx) <= lim && fabs(c.wy) <= lim && fabs(c.wz) <= lim;
+}
+
 // One face-plane copy of the halo update: the plane whose point with both
 // in-plane indices 0 is at element offset `src` is copied onto the plane at
 // `dst` (same in-plane geometry).
@@ -158,9 +165,9 @@ bool tma_available();
 cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
 // Fix-up buffer of an FP64 tile set of the TMA kernel (emulated cell): room
 // for cap entries of 16 bytes (one per 32-point row segment with points left
-// to the FP64 cell, so cap = the set's computed points / 32 suffices), then
-// the entry count and a block counter, both zero on entry. The kernel fills
-// it; the fix-up launch that follows on the same stream updates the listed
+// to the fix-up, so cap = the set's computed points / 32 suffices), then the
+// entry count and a block counter, both zero on entry. The kernel fills it;
+// the fix-up launch that follows on the same stream updates the listed
 // points and resets the count and the counter.
 struct FixBuf {
   void *p = nullptr;
@@ -168,21 +175,10 @@ struct FixBuf {
 };
 size_t tma_fix_cap(const TmaTile *tiles, int ntiles);
 inline size_t tma_fix_bytes(size_t cap) { return cap * 16 + 2 * sizeof(unsigned); }
-// x faces of the halo update fused into the boundary launches of the hidden
-// step (all subdomains share the device's memory): every computed point with
-// x = o_x - 1 (x = n_x - o_x) is also stored into plane n_x - 1 (plane 0) of
-// its left (right) x neighbour, where the x plane copy of Fig. 1's
-// update_halo! would put it; the y and z plane copies follow on the same
-// stream. nbr = NULL: no sends.
-struct HaloSend {
-  const int *nbr = nullptr;  // [nsub][3][2]: left, right neighbour per dimension, -1 none
-  int n[3] = {0, 0, 0}, o[3] = {0, 0, 0};
-  long long nloc = 0;
-};
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               FixBuf fix, const HaloSend &send, cudaStream_t s);
+                               FixBuf fix, cudaStream_t s);
 
 // Staggered-grid acoustics (acoustic.cu): coefficients dt/(rho dd) of the
 // velocity update and dt K/dd of the pressure update, formed on the host in
@@ -222,6 +218,17 @@ cudaError_t launch_halo_jobs(size_t elem_size, HaloJobs jobs, int njobs, cudaStr
 cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
                         void *field, int na, int nb, long long sa, long long sb,
                         cudaStream_t s);
+// The halo update of a field of the grid's own size (3-D grids) in one
+// launch (the gather form, halo.cu): nbr[6 sub + 2 d + side] is the left
+// (side 0) or right (side 1) neighbour in dimension d, -1 none.
+struct HaloGather {
+  const int *nbr = nullptr;
+  int n[3] = {0, 0, 0}, o[3] = {0, 0, 0};
+  long long nloc = 0;
+  int nsub = 0;
+};
+cudaError_t launch_halo_gather(size_t elem_size, void *field, const HaloGather &h,
+                               cudaStream_t s);
 
 // Adjoint step over every point of one array, and out = a - b elementwise.
 // With `tma`, fields that allow it take the TMA-pipelined kernel; FP64 fields

@@ -444,11 +444,26 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
   const int zbt = tma ? choose_zb_tma(tma_xy_tiles(1, nx - 1, 1, ny - 1, V, Wt, Ht) * g->nsub,
                                       nz - 2, tma_slots(V))
                       : 0;
-  for (int s = 0; s < g->nsub; ++s) {
-    if (tma)
-      add_box_tma(v.tma, (long long)s * g->nloc, (long long)s * nz, 1, nx - 1, 1, ny - 1, 1, nz - 1,
-                  zbt, V, Wt, Ht);
-    else
+  if (tma) {
+    // Tile order: for each (z chunk, row block) the tiles of the subdomains
+    // that are neighbours in x side by side, so that the halo cells a tile
+    // stores into its x neighbour share their 32-byte sectors with points
+    // that the neighbour's tiles store at about the same time (the L2 then
+    // merges the partial writes instead of reading the sectors back).
+    std::vector<std::vector<TmaTile>> per(g->nsub);
+    for (int s = 0; s < g->nsub; ++s)
+      add_box_tma(per[s], (long long)s * g->nloc, (long long)s * nz, 1, nx - 1, 1, ny - 1, 1,
+                  nz - 1, zbt, V, Wt, Ht);
+    const int nrow = (int)((nx - 1 + Wt - 1) / Wt);  // tiles per row block (x0 = 0 .. nx - 2)
+    const int dx = g->dims[0];
+    for (int syz = 0; syz < g->nsub / dx; ++syz)
+      for (size_t b = 0; b < per[syz * dx].size(); b += nrow)
+        for (int sx = 0; sx < dx; ++sx) {
+          const std::vector<TmaTile> &p = per[sx + dx * syz];
+          v.tma.insert(v.tma.end(), p.begin() + b, p.begin() + std::min(p.size(), b + nrow));
+        }
+  } else {
+    for (int s = 0; s < g->nsub; ++s)
       add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, lo_in(ny), hi_in(ny), lo_in(nz),
                 hi_in(nz), zb, 0);
   }
@@ -562,25 +577,11 @@ int build_split_tiles(igg_grid *g, const int w[3], int V, SplitTiles **out) {
   return IGG_OK;
 }
 
-// The fused halo sends of a grid (HaloSend).
-HaloSend halo_send(const igg_grid *g) {
-  HaloSend h;
-  h.nbr = g->nbr;
-  for (int d = 0; d < 3; ++d) {
-    h.n[d] = g->n[d];
-    h.o[d] = g->overlap[d];
-  }
-  h.nloc = g->nloc;
-  return h;
-}
-
 cudaError_t launch_tiles(const igg_grid *g, int V, igg_dtype dt, const TileSet &ts, void *T2,
-                         const void *T, const void *Ci, const Coef &c, cudaStream_t s,
-                         const HaloSend &send = HaloSend()) {
+                         const void *T, const void *Ci, const Coef &c, cudaStream_t s) {
   if (ts.tma >= 0)
     return launch_stencil_tma(dt, ts.tma, (const TmaTile *)ts.dev, ts.n, T2, T, Ci, g->n[0],
-                              g->n[1], (long long)g->nsub * g->n[2], c, g->dev_err, ts.fix, send,
-                              s);
+                              g->n[1], (long long)g->nsub * g->n[2], c, g->dev_err, ts.fix, s);
   if (V > 1) return launch_stencil_vec(dt, (const VTile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
   return launch_stencil(dt, (const Tile *)ts.dev, ts.n, T2, T, Ci, c, nullptr, s);
 }
@@ -628,7 +629,20 @@ cudaError_t enqueue_halo(PlaneCopy *const copies[3], const int ncopies[3], const
   return e;
 }
 
+// The halo update of a field of the grid's own size: on 3-D grids one
+// gather launch, else the plane copies dimension by dimension.
 cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
+  if (g->n[0] > 1 && g->n[1] > 1 && g->n[2] > 1) {
+    HaloGather h;
+    h.nbr = g->nbr;
+    for (int d = 0; d < 3; ++d) {
+      h.n[d] = g->n[d];
+      h.o[d] = g->overlap[d];
+    }
+    h.nloc = g->nloc;
+    h.nsub = g->nsub;
+    return launch_halo_gather(es, field, h, s);
+  }
   return enqueue_halo(g->copies, g->ncopies, g->n, field, es, s);
 }
 
@@ -692,16 +706,9 @@ int enqueue_halo_fields(igg_grid *g, void *const fields[], const int *nf, int nf
 
 bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->ncopies[2] > 0; }
 
-// Whether hidden steps fuse the halo update into one TMA step launch: the
-// option, TMA tiles, some halo, and n >= 2 o (a point is sent at most one way
-// per dimension).
-bool use_fused_halo(const igg_grid *g, int V) {
-  if (!g->fused_halo || !use_tma(g, V) || !any_halo(g)) return false;
-  for (int d = 0; d < 3; ++d)
-    if (g->n[d] < 2 * g->overlap[d]) return false;
-  return true;
-}
-
+// Whether hidden steps run as the full step launch followed by the halo
+// update (the option; the alternative is the boundary/inner split).
+bool use_fused_halo(const igg_grid *g) { return g->fused_halo; }
 
 // One step of Fig. 1's loop, queued on s: plain (full step, then halo update
 // of T2 on s) or hidden (boundary set + halo on the high-priority stream,
@@ -710,11 +717,15 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
                  igg_dtype dt, const Coef &c0, bool with_halo, cudaStream_t s) {
   cudaError_t e;
   Coef c = c0;
-  c.f64_emu = g->f64_emu;
+  c.f64_emu = g->f64_emu && emu_weights_ok(c);
   const int V = grid_vec(g, dt);
   // 2-D and 1-D grids: the hidden step runs as the plain step and the halo
-  // update (same result; no boundary/inner split of an absent dimension)
-  if (low_dim(g)) widths = nullptr;
+  // update (same result; no boundary/inner split of an absent dimension);
+  // by default (the grid's option) every hidden step does: with all
+  // subdomains in one device's memory there is no transfer to overlap, and
+  // the full step launch followed by the one-launch halo update is faster
+  // than the split's extra launches
+  if (low_dim(g) || use_fused_halo(g)) widths = nullptr;
   if (!widths) {
     TileSet *full = nullptr;
     if (int rc = build_full_tiles(g, V, &full)) return rc;
@@ -724,14 +735,6 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
       e = enqueue_halo(g, T2, dtype_size(dt), s);
       if (e != cudaSuccess) return cuda_error(e, "halo launch");
     }
-    return IGG_OK;
-  }
-  if (with_halo && use_fused_halo(g, V)) {
-    // the hidden step as one launch with the halo update fused into it
-    TileSet *full = nullptr;
-    if (int rc = build_full_tiles(g, V, &full)) return rc;
-    e = launch_tiles(g, V, dt, *full, T2, T, Ci, c, s, halo_send(g));
-    if (e != cudaSuccess) return cuda_error(e, "fused step launch");
     return IGG_OK;
   }
   SplitTiles *st = nullptr;
@@ -972,6 +975,14 @@ int igg_update_halo(igg_grid *g, void *const fields[], int nfields, igg_dtype dt
   for (int i = 0; i < nfields; ++i)
     if (int rc = check_field(g, fields[i], "field")) return rc;
   DeviceGuard dg(g->device);
+  if (g->n[0] > 1 && g->n[1] > 1 && g->n[2] > 1) {  // 3-D: one gather launch per field
+    if (!any_halo(g)) return IGG_OK;
+    for (int i = 0; i < nfields; ++i) {
+      cudaError_t e = enqueue_halo(g, fields[i], dtype_size(dt), (cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_error(e, "halo launch");
+    }
+    return IGG_OK;
+  }
   std::vector<int> nf(3 * (size_t)nfields);
   for (int i = 0; i < nfields; ++i)
     for (int d = 0; d < 3; ++d) nf[3 * i + d] = g->n[d];
@@ -1134,7 +1145,7 @@ int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const v
   if (nt >= 2) {
     // tile tables are allocated before the capture starts
     const int V = grid_vec(g, dt);
-    if (widths && !use_fused_halo(g, V) && !low_dim(g)) {
+    if (widths && !use_fused_halo(g) && !low_dim(g)) {
       SplitTiles *st = nullptr;
       if (int rc = build_split_tiles(g, widths, V, &st)) return rc;
     } else {
@@ -1173,6 +1184,32 @@ int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const v
     }
   }
   if (nt % 2) return enqueue_step(g, widths, T2, T, Ci, dt, c, true, s);
+  return IGG_OK;
+}
+
+int igg_run_host(igg_grid *g, int nt, const int widths[3], void *T_host, const void *Ci_host,
+                 void *T, void *T2, void *Ci, igg_dtype dt, double lam, double dtime, double dx,
+                 double dy, double dz, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (!T_host || !Ci_host) return set_error(IGG_EINVAL, "T_host or Ci_host is NULL");
+  if (int rc = check_dtype(dt)) return rc;
+  if (nt < 0) return set_error(IGG_EINVAL, "nt < 0");
+  if (int rc = check_field(g, T, "T")) return rc;
+  if (int rc = check_field(g, T2, "T2")) return rc;
+  if (int rc = check_field(g, Ci, "Ci")) return rc;
+  if (T2 == T || T2 == Ci || T == Ci) return set_error(IGG_EINVAL, "T, T2, Ci alias");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)g->nsub * (size_t)g->nloc * dtype_size(dt);
+  cudaError_t e = cudaMemcpyAsync(T, T_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Ci, Ci_host, bytes, cudaMemcpyHostToDevice, s);
+  // Fig. 1: T2 = copy(T) (the boundary values stay fixed in both buffers)
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T2, T, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(inputs)");
+  if (int rc = igg_run(g, nt, widths, T, T2, Ci, dt, lam, dtime, dx, dy, dz, stream)) return rc;
+  e = cudaMemcpyAsync(T_host, nt % 2 ? T2 : T, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(result)");
   return IGG_OK;
 }
 

@@ -60,7 +60,7 @@ struct TmaShape {
   static constexpr int TBA = (TB + 127) / 128 * 128;
   static constexpr int CB = W * H * (int)sizeof(S);     // Ci box bytes
   static constexpr int STAGE = (TBA + CB + 127) / 128 * 128;
-  static constexpr int SMEM = NS * STAGE + 2 * NS * 8 + 64 + 128;  // + flags, send table
+  static constexpr int SMEM = NS * STAGE + 2 * NS * 8 + 64;  // + flags
   static_assert(H % ROWS_PER_PASS == 0, "rows per tile");
   static_assert(BW <= 256 && BH <= 256, "TMA box dims");
 };
@@ -88,106 +88,6 @@ __device__ __forceinline__ FixList fix_list(void *fix, size_t cap) {
 }
 constexpr int kFixupBlocks = 8 * 152;
 
-// Halo update fused into the step (HaloSend). A point's send option in
-// dimension d: 0 = none, 1 = to plane n - 1 of the left neighbour
-// (coordinate o - 1), 2 = to plane 0 of the right neighbour (coordinate
-// n - o); fused steps need n >= 2 o, so that at most one option applies.
-__device__ __forceinline__ int send_opt(const HaloSend &h, int d, int c) {
-  return c == h.o[d] - 1 ? 1 : (c == h.n[d] - h.o[d] ? 2 : 0);
-}
-
-// Subdomain reached from sub by the options (ix, iy, iz) taken in the order
-// x, y, z, as the plane copies go; -1 where a neighbour is missing.
-__device__ __forceinline__ int send_sub(const HaloSend &h, int sub, int ix, int iy, int iz) {
-  if (ix && sub >= 0) sub = h.nbr[6 * sub + 0 + ix - 1];
-  if (iy && sub >= 0) sub = h.nbr[6 * sub + 2 + iy - 1];
-  if (iz && sub >= 0) sub = h.nbr[6 * sub + 4 + iz - 1];
-  return sub;
-}
-
-// Stores v, the new value of point (x, y, z) with options (ox, oy, oz), into
-// every halo cell that the plane copies in the order x, y, z give it: for
-// each nonempty subset of its send dimensions, the cell of the subdomain
-// reached through those neighbours with those coordinates replaced.
-// nbc(k): the subdomain reached by the options of index k = ix + 3 iy + 9 iz.
-template <class S, class NB>
-__device__ __forceinline__ void send_value(const HaloSend &h, const NB &nbc, S *T2, int x, int y,
-                                           int z, int ox, int oy, int oz,
-                                           typename Num<S>::C v) {
-  const int x2 = ox == 1 ? h.n[0] - 1 : 0, y2 = oy == 1 ? h.n[1] - 1 : 0,
-            z2 = oz == 1 ? h.n[2] - 1 : 0;
-  const long long sx = 1, sy = h.n[0], sz = (long long)h.n[0] * h.n[1];
-  // a point on one sent plane only (all but the edges and corners): one cell
-  if ((ox != 0) + (oy != 0) + (oz != 0) == 1) {
-    const int sd = nbc(ox + 3 * oy + 9 * oz);
-    if (sd >= 0)
-      Num<S>::st(T2 + (long long)sd * h.nloc + sx * (ox ? x2 : x) + sy * (oy ? y2 : y) +
-                     sz * (oz ? z2 : z),
-                 v);
-    return;
-  }
-#pragma unroll
-  for (int k = 1; k < 8; ++k) {
-    if (((k & 1) && !ox) || ((k & 2) && !oy) || ((k & 4) && !oz)) continue;
-    const int sd = nbc(((k & 1) ? ox : 0) + 3 * ((k & 2) ? oy : 0) + 9 * ((k & 4) ? oz : 0));
-    if (sd < 0) continue;
-    Num<S>::st(T2 + (long long)sd * h.nloc + sx * ((k & 1) ? x2 : x) + sy * ((k & 2) ? y2 : y) +
-                   sz * ((k & 4) ? z2 : z),
-               v);
-  }
-}
-
-// The halo sends of one tile, after its points are stored (the block's
-// stores are visible to it after a barrier): its points on sent planes are
-// read back from T2 and stored to their halo cells. Points left to the
-// fix-up send stale values here; the fix-up sends them again afterwards.
-// Three disjoint groups: points on a sent march plane, the other points on
-// a sent row, the other points on a sent x column.
-template <class S, bool SWAP>
-__device__ __noinline__ void send_tile(const HaloSend &h, const int *nbc, const TmaTile &t,
-                                       S *T2) {
-  const int dr = SWAP ? 2 : 1, dm = SWAP ? 1 : 2;  // dimensions of rows and march
-  const long long sx = 1, sy = h.n[0], sz = (long long)h.n[0] * h.n[1];
-  const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
-  const int nxr = t.xe - t.xb, nr = t.re - t.r0;
-  const auto nb = [nbc](int k) { return nbc[k]; };
-  auto one = [&](int x, int r, int m) {
-    const int y = SWAP ? m : r, z = SWAP ? r : m;
-    const int ox = send_opt(h, 0, x), oy = send_opt(h, 1, y), oz = send_opt(h, 2, z);
-    const S *p = T2 + t.base + sx * x + sy * y + sz * z;
-    send_value<S>(h, nb, T2, x, y, z, ox, oy, oz, Num<S>::cv(*(volatile const S *)p));
-  };
-  const int mp[2] = {h.o[dm] - 1, h.n[dm] - h.o[dm]};  // sent march planes
-  const int rp[2] = {h.o[dr] - 1, h.n[dr] - h.o[dr]};  // sent rows
-  const int xp[2] = {h.o[0] - 1, h.n[0] - h.o[0]};     // sent x columns
-  for (int q = 0; q < 2; ++q) {
-    const int m = mp[q];
-    if (m < t.m0 || m >= t.m1) continue;
-    for (int i = threadIdx.x; i < nxr * nr; i += blockDim.x) one(t.xb + i % nxr, t.r0 + i / nxr, m);
-  }
-  const int nm = t.m1 - t.m0;
-  for (int q = 0; q < 2; ++q) {
-    const int r = rp[q];
-    if (r < t.r0 || r >= t.re) continue;
-    for (int i = threadIdx.x; i < nxr * nm; i += blockDim.x) {
-      const int m = t.m0 + i / nxr;
-      if (m == mp[0] || m == mp[1]) continue;
-      one(t.xb + i % nxr, r, m);
-    }
-  }
-  for (int q = 0; q < 2; ++q) {
-    const int x = xp[q];
-    if (x < t.xb || x >= t.xe) continue;
-    for (int i = threadIdx.x; i < nr * nm; i += blockDim.x) {
-      const int r = t.r0 + i % nr, m = t.m0 + i / nr;
-      if (m == mp[0] || m == mp[1] || r == rp[0] || r == rp[1]) continue;
-      one(x, r, m);
-    }
-  }
-  (void)srow;
-  (void)smarch;
-}
-
 // bit i of x (i < 16) to bit 2i
 __device__ __forceinline__ unsigned spread16(unsigned x) {
   x = (x | (x << 8)) & 0x00FF00FFu;
@@ -195,13 +95,13 @@ __device__ __forceinline__ unsigned spread16(unsigned x) {
   x = (x | (x << 2)) & 0x33333333u;
   x = (x | (x << 1)) & 0x55555555u;
   return x;
-}  // one resident wave of 256-thread blocks
+}
 
 // How a TMA kernel computes its points: MODE_CELL = the shared cell() of the
 // storage type (FP32, BF16); for FP64 fields, MODE_F64 = the FP64 cell and
 // MODE_EMU + (3 - NG) = the emulated cell's fast path with NG weight groups
-// (the grid's weight_groups), leaving the points it hands to the
-// FP64 cell unwritten and flagging their tile for k_fixup_f64.
+// (the grid's weight_groups); the points its fast path does not take are
+// listed for the fix-up launch (k_fixup_f64), which applies cell().
 enum { MODE_CELL = 0, MODE_F64 = 1, MODE_EMU = 2, MODE_EMU_LAST = 4 };
 __host__ __device__ constexpr bool is_emu(int mode) {
   return mode >= MODE_EMU && mode <= MODE_EMU_LAST;
@@ -243,26 +143,40 @@ __device__ __forceinline__ void compute_vec<double, MODE_F64>(
 
 // Emulated fast path for both points, computed unconditionally (no branch
 // in the common case); ok marks the points whose fast path applies, the
-// others are left to the fix-up (which applies cell(): the shifted-
-// significand form across one power of two, else the FP64 cell).
+// others are listed for the fix-up launch (cell(): the shifted-significand
+// form across one power of two, else the FP64 cell).
 template <int NG>
 __device__ __forceinline__ void compute_vec_emu(
     const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
     const Vec<double> &zm, const Vec<double> &zp, const Vec<double> &ci, const W<double> &w,
     Vec<double> &out, unsigned &ok) {
-  const unsigned long long nb0[6] = {dbits(left),     dbits(c.v[1]),  dbits(ym.v[0]),
+  const unsigned long long b0 = dbits(c.v[0]), b1 = dbits(c.v[1]);
+  const unsigned long long nb0[6] = {dbits(left),     b1,             dbits(ym.v[0]),
                                      dbits(yp.v[0]),  dbits(zm.v[0]), dbits(zp.v[0])};
-  const unsigned long long nb1[6] = {dbits(c.v[0]),   dbits(right),   dbits(ym.v[1]),
+  const unsigned long long nb1[6] = {b0,              dbits(right),   dbits(ym.v[1]),
                                      dbits(yp.v[1]),  dbits(zm.v[1]), dbits(zp.v[1])};
-  unsigned hn0[6], hn1[6];
+  int gh0[NG], gh1[NG];
+  unsigned gm0[NG], gm1[NG];
+  // sign and exponent from the pair's first point (shared by every point of
+  // the pair whose stencil passes)
+  const unsigned hc = (unsigned)(b0 >> 32);
+  const bool okc = emu2_centre_ok(hc);
+  bool ok0 = emu2_int<NG>(b0, nb0, gh0, gm0) && okc;
+  bool ok1 = emu2_int<NG>(b1, nb1, gh1, gm1) && okc;
+  // the FP32 sums of both points as float2 (one instruction per pair)
+  float2 fh[NG], fl[NG];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    hn0[i] = (unsigned)(nb0[i] >> 32);
-    hn1[i] = (unsigned)(nb1[i] >> 32);
+  for (int g = 0; g < NG; ++g) {
+    fh[g] = make_float2(__int2float_rn(gh0[g]), __int2float_rn(gh1[g]));
+    fl[g] = make_float2(__uint_as_float(gm0[g]), __uint_as_float(gm1[g]));
   }
-  ok = (emu_fast_ok(dhi(c.v[0]), hn0) ? 1u : 0u) | (emu_fast_ok(dhi(c.v[1]), hn1) ? 2u : 0u);
-  out.v[0] = cell_emu_fast<NG>(c.v[0], nb0, ci.v[0], w);
-  out.v[1] = cell_emu_fast<NG>(c.v[1], nb1, ci.v[1], w);
+  float2 S, C;
+  emu2_sum<NG>(fh, fl, w, S, C);
+  const float2 Kr = vfma(make_float2(emu2_cif(ci.v[0]), emu2_cif(ci.v[1])), C,
+                         vset(kMagic, float2()));
+  out.v[0] = emu2_apply(b0, hc, ci.v[0], S.x, Kr.x, ok0);
+  out.v[1] = emu2_apply(b1, hc, ci.v[1], S.y, Kr.y, ok1);
+  ok = (ok0 ? 1u : 0u) | (ok1 ? 2u : 0u);
 }
 template <>
 __device__ __forceinline__ void compute_vec<double, MODE_EMU>(
@@ -294,12 +208,12 @@ __device__ __forceinline__ void compute_vec<double, MODE_EMU + 2>(
 // BATCH: independent problems of the batched form; a tile's problem (pad[0])
 // gives its tensor maps, row pitch, ny and coefficients (TmaBatch) in place
 // of mapT, mapC, nx, ny and c0.
-template <class S, int LPR_, int H_, bool SWAP, int MODE, bool SEND, bool BATCH = false>
+template <class S, int LPR_, int H_, bool SWAP, int MODE, bool BATCH = false>
 __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     k_stencil_tma(const __grid_constant__ CUtensorMap mapT, const __grid_constant__ CUtensorMap mapC,
                   const TmaTile *__restrict__ tiles, S *__restrict__ T2, int nx, int ny, Coef c0,
                   unsigned *__restrict__ dev_err, void *__restrict__ fix, size_t fix_cap,
-                  const HaloSend send, const TmaBatch batch = TmaBatch()) {
+                  const TmaBatch batch = TmaBatch()) {
   using Sh = TmaShape<S, LPR_, H_>;
   using C = typename Num<S>::C;
   constexpr int V = Sh::V, NS = Sh::NS, LPR = Sh::LPR;
@@ -319,12 +233,6 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     nx = batch.geom[2 * t.pad[0]];  // row pitch
     ny = batch.geom[2 * t.pad[0] + 1];
     c0 = batch.coef[t.pad[0]];
-  }
-  // SEND: the subdomains reached by each combination of send options
-  int *nbc = reinterpret_cast<int *>(smem + NS * Sh::STAGE + 2 * NS * 8 + 64);
-  if (SEND && threadIdx.x < 27) {
-    const int k = threadIdx.x;
-    nbc[k] = send_sub(send, (int)(t.base / send.nloc), k % 3, (k / 3) % 3, k / 9);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -355,14 +263,16 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
         if (flags[0]) break;
         const unsigned bar = full0 + 8 * s;
         const unsigned dst = sbase + s * Sh::STAGE;
-        mbar_expect_tx(bar, Sh::TB + Sh::CB);
+        // loads 0 and 1 carry no Ci plane (their planes z0 - 2, z0 - 1 are
+        // never used)
+        mbar_expect_tx(bar, k >= 2 ? Sh::TB + Sh::CB : Sh::TB);
         const int mT = t.m0 - 1 + k, mC = t.m0 - 2 + k;  // march index of the T / Ci plane
         if (!SWAP) {
           tma_load_3d(dst, pmT, t.x0 - V, t.r0 - 1, t.zoff + mT, bar);
-          tma_load_3d(dst + Sh::TBA, pmC, t.x0, t.r0, t.zoff + mC, bar);
+          if (k >= 2) tma_load_3d(dst + Sh::TBA, pmC, t.x0, t.r0, t.zoff + mC, bar);
         } else {
           tma_load_3d(dst, pmT, t.x0 - V, mT, t.zoff + t.r0 - 1, bar);
-          tma_load_3d(dst + Sh::TBA, pmC, t.x0, mC, t.zoff + t.r0, bar);
+          if (k >= 2) tma_load_3d(dst + Sh::TBA, pmC, t.x0, mC, t.zoff + t.r0, bar);
         }
       }
       flags[1] = k;
@@ -380,7 +290,11 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       comp[j] = (t.r0 + rowi[j] < t.re) && xs + V > t.xb && xs < t.xe;
     }
     const bool full_vec = xs >= t.xb && xs + V <= t.xe;
-
+    // points of this lane's vector inside the tile's box
+    unsigned inm = 0u;
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+      if (xs + i >= t.xb && xs + i < t.xe) inm |= 1u << i;
     const long long sy = nx, sz = (long long)nx * ny;
     const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
     Vec<S> zm[Sh::RPT];
@@ -427,38 +341,47 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
         lds_vec(row + Sh::BW, dn);
         lds_vec(Tn + (r + 1) * Sh::BW + V + sl * V, zp);
         lds_vec(Cn + r * Sh::W + sl * V, ci);
-        C left = __shfl_up_sync(0xffffffffu, c.v[V - 1], 1, LPR);
-        C right = __shfl_down_sync(0xffffffffu, c.v[0], 1, LPR);
-        if (sl == 0) left = Num<S>::cv(row[-1]);
-        if (sl == LPR - 1) right = Num<S>::cv(row[V]);
-        unsigned deferred = 0u;  // bit i: point i left to the fix-up
+        C left, right;
+        if constexpr (sizeof(S) == 8) {
+          // FP64: the x neighbours from shared memory (the box's vector
+          // halo covers the row ends)
+          left = row[-1];
+          right = row[V];
+        } else {
+          left = __shfl_up_sync(0xffffffffu, c.v[V - 1], 1, LPR);
+          right = __shfl_down_sync(0xffffffffu, c.v[0], 1, LPR);
+          if (sl == 0) left = Num<S>::cv(row[-1]);
+          if (sl == LPR - 1) right = Num<S>::cv(row[V]);
+        }
+        Vec<S> out;
+        unsigned okm = (1u << V) - 1u;
         if (comp[j]) {
-          Vec<S> out;
           // (up, dn) are the row pair, (zm, zp) the march pair
           Vec<S> ym = SWAP ? zm[j] : up, yp = SWAP ? zp : dn;
           Vec<S> zmm = SWAP ? up : zm[j], zpp = SWAP ? dn : zp;
-          unsigned okm;
           compute_vec<S, MODE>(c, left, right, ym, yp, zmm, zpp, ci, w, out, okm);
+        }
+        if (comp[j]) {
+          // every point of the box is stored; points the fast path did not
+          // take are stored again by the fix-up launch
           S *dst = T2 + t.base + xs + srow * (t.r0 + r) + smarch * m;
-          if (full_vec && okm == (1u << V) - 1u) {
+          if (full_vec) {
             *reinterpret_cast<uint4 *>(dst) = pack(out);
           } else {
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-              const bool in = xs + i >= t.xb && xs + i < t.xe;
-              if (in && (okm >> i & 1u)) Num<S>::st(dst + i, out.v[i]);
-              if (in && !(okm >> i & 1u)) deferred |= 1u << i;
-            }
+            for (int i = 0; i < V; ++i)
+              if (inm >> i & 1u) Num<S>::st(dst + i, out.v[i]);
           }
         }
         if constexpr (is_emu(MODE)) {
           // The warp owns the whole row (one row per warp, two points per
-          // lane): it writes the row's point masks for this plane and lists
-          // the nonzero ones for the fix-up.
+          // lane): it lists each 32-point segment of the row with points
+          // the fast path did not take (its first point and a bit mask).
           static_assert(LPR == 32 && V == 2, "one FP64 row per warp");
-          if (__any_sync(0xffffffffu, deferred != 0u)) {
-            const unsigned b0 = __ballot_sync(0xffffffffu, deferred & 1u);
-            const unsigned b1 = __ballot_sync(0xffffffffu, deferred & 2u);
+          const unsigned defm = comp[j] ? (~okm & inm) : 0u;
+          if (__any_sync(0xffffffffu, defm != 0u)) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, defm & 1u);
+            const unsigned b1 = __ballot_sync(0xffffffffu, defm & 2u);
             if (lane < 2) {
               // points 32*lane .. 32*lane + 31: lanes 16*lane .. 16*lane + 15
               const unsigned h0 = (b0 >> (16 * lane)) & 0xFFFFu, h1 = (b1 >> (16 * lane)) & 0xFFFFu;
@@ -482,9 +405,6 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
     if (warp == 0 && lane == 0) flags[2] = consumed;
   }
   __syncthreads();
-  if constexpr (SEND) {
-    if (!flags[0]) send_tile<S, SWAP>(send, nbc, t, T2);
-  }
   // After an abort, wait (bounded) for copies issued but never consumed, so
   // that no bulk copy writes into this CTA's shared memory after it exits.
   if (threadIdx.x == 0 && flags[0]) {
@@ -497,16 +417,16 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
   }
 }
 
-// Fix-up of an emulated-cell launch: the points left by the kernel get
-// cell() (the same choice and arithmetic as every kernel: the shifted-
-// significand form where the stencil crosses one power of two, else the
-// FP64 cell). The kernel listed every 32-point row segment with such points; the
-// fix-up's warps take the entries in turn, lane l updating point p + l when
-// bit l is set. The last block to finish resets the list.
+// Fix-up of an emulated-cell launch: the points whose fast path the kernel
+// did not take get cell() (the same choice and arithmetic as every kernel:
+// the shifted-significand form where the stencil crosses one power of two,
+// else the FP64 cell). The kernel listed every 32-point row segment with such
+// points; the fix-up's warps take the entries in turn, lane l updating point
+// p + l when bit l is set. The last block to finish resets the list.
 __global__ void __launch_bounds__(256)
     k_fixup_f64(void *__restrict__ fix, size_t cap, double *__restrict__ T2,
                 const double *__restrict__ T, const double *__restrict__ Ci, int nx, int ny,
-                Coef c0, const HaloSend send) {
+                Coef c0) {
   const FixList fl = fix_list(fix, cap);
   const unsigned count = (unsigned)min((size_t)*(volatile unsigned *)fl.count, cap);
   const W<double> w = make_w(c0, 0.0);
@@ -520,20 +440,7 @@ __global__ void __launch_bounds__(256)
     const double tc = __ldg(T + p);
     const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
                           __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-    const double v = cell(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
-    T2[p] = v;
-    if (send.nbr) {
-      const int sub = (int)(p / send.nloc);
-      const long long q = p % send.nloc;
-      const int x = (int)(q % nx), y = (int)((q / nx) % ny), z = (int)(q / sz);
-      const int ox = send_opt(send, 0, x), oy = send_opt(send, 1, y), oz = send_opt(send, 2, z);
-      if (ox | oy | oz) {
-        const auto nb = [&send, sub](int k) {
-          return send_sub(send, sub, k % 3, (k / 3) % 3, k / 9);
-        };
-        send_value<double>(send, nb, T2, x, y, z, ox, oy, oz, v);
-      }
-    }
+    T2[p] = cell(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -548,11 +455,8 @@ __global__ void __launch_bounds__(256)
 template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t prepare_t(int *ctas_per_sm) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
-  auto kern = k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, false>;
+  auto kern = k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
   if (e == cudaSuccess && ctas_per_sm)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, kern, 32 * (Sh::CONSUMERS + 1),
                                                       Sh::SMEM);
@@ -562,7 +466,7 @@ cudaError_t prepare_t(int *ctas_per_sm) {
 template <class S, class Shp, bool SWAP, int MODE>
 cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     FixBuf fix, const HaloSend &send, cudaStream_t s) {
+                     FixBuf fix, cudaStream_t s) {
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
   CUtensorMap mT, mC;
   const bool ok = SWAP ? encode<S>(&mT, T, nx, ny, nzt, Sh::BW, 1, Sh::BH) &&
@@ -570,18 +474,13 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
                        : encode<S>(&mT, T, nx, ny, nzt, Sh::BW, Sh::BH, 1) &&
                              encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, Sh::H, 1);
   if (!ok) return cudaErrorInvalidValue;
-  if (send.nbr)
-    k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, true>
-        <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
-                                                            dev_err, fix.p, fix.cap, send);
-  else
-    k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE, false>
-        <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
-                                                            dev_err, fix.p, fix.cap, send);
+  k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>
+      <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
+                                                          dev_err, fix.p, fix.cap);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && is_emu(MODE)) {
     k_fixup_f64<<<kFixupBlocks, 256, 0, s>>>(fix.p, fix.cap, (double *)T2, (const double *)T,
-                                            (const double *)Ci, nx, ny, c, send);
+                                            (const double *)Ci, nx, ny, c);
     e = cudaGetLastError();
   }
   return e;
@@ -613,45 +512,45 @@ cudaError_t prepare_v(int variant, int *ctas) {
 template <class S, bool SWAP>
 cudaError_t launch_m(const TmaTile *tiles, int ntiles, void *T2, const void *T, const void *Ci,
                      int nx, int ny, long long nzt, const Coef &c, unsigned *dev_err,
-                     FixBuf fix, const HaloSend &send, cudaStream_t s) {
+                     FixBuf fix, cudaStream_t s) {
   if constexpr (sizeof(S) == 8) {
     if (c.f64_emu) {
       if (!fix.p) return cudaErrorInvalidValue;
       switch (weight_groups(c.wx, c.wy, c.wz)) {
         case 1:
           return launch_t<S, WideShape<S>, SWAP, emu_mode(1)>(tiles, ntiles, T2, T, Ci, nx, ny,
-                                                              nzt, c, dev_err, fix, send, s);
+                                                              nzt, c, dev_err, fix, s);
         case 2:
           return launch_t<S, WideShape<S>, SWAP, emu_mode(2)>(tiles, ntiles, T2, T, Ci, nx, ny,
-                                                              nzt, c, dev_err, fix, send, s);
+                                                              nzt, c, dev_err, fix, s);
         default:
           return launch_t<S, WideShape<S>, SWAP, emu_mode(3)>(tiles, ntiles, T2, T, Ci, nx, ny,
-                                                              nzt, c, dev_err, fix, send, s);
+                                                              nzt, c, dev_err, fix, s);
       }
     }
     return launch_t<S, WideShape<S>, SWAP, MODE_F64>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
-                                                     dev_err, fix, send, s);
+                                                     dev_err, fix, s);
   } else {
     return launch_t<S, WideShape<S>, SWAP, MODE_CELL>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c,
-                                                      dev_err, fix, send, s);
+                                                      dev_err, fix, s);
   }
 }
 
 template <class S>
 cudaError_t launch_v(int variant, const TmaTile *tiles, int ntiles, void *T2, const void *T,
                      const void *Ci, int nx, int ny, long long nzt, const Coef &c,
-                     unsigned *dev_err, FixBuf fix, const HaloSend &send, cudaStream_t s) {
+                     unsigned *dev_err, FixBuf fix, cudaStream_t s) {
   switch (variant) {
     case TMA_WIDE:
-      return launch_m<S, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, send, s);
+      return launch_m<S, false>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
     case TMA_WIDE_SWAP:
-      return launch_m<S, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, send, s);
+      return launch_m<S, true>(tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix, s);
   }
   return cudaErrorInvalidValue;
 }
 
 // The batched form's launch: non-swapped wide tiles, the storage type's cell
-// (FP64 batches: the FP64 cell, no fix-up), maps from the TmaBatch table.
+// (FP64 batches: the FP64 cell), maps from the TmaBatch table.
 template <class S>
 cudaError_t launch_batch_t(const TmaTile *tiles, int ntiles, void *T2, const TmaBatch &b,
                            unsigned *dev_err, cudaStream_t s) {
@@ -660,10 +559,9 @@ cudaError_t launch_batch_t(const TmaTile *tiles, int ntiles, void *T2, const Tma
   constexpr int MODE = sizeof(S) == 8 ? MODE_F64 : MODE_CELL;
   CUtensorMap none;
   std::memset(&none, 0, sizeof none);
-  k_stencil_tma<S, Shp::LPR, Shp::H, false, MODE, false, true>
+  k_stencil_tma<S, Shp::LPR, Shp::H, false, MODE, true>
       <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(none, none, tiles, (S *)T2, 0, 0,
-                                                          Coef(), dev_err, nullptr, 0,
-                                                          HaloSend(), b);
+                                                          Coef(), dev_err, nullptr, 0, b);
   return cudaGetLastError();
 }
 
@@ -672,7 +570,7 @@ cudaError_t prepare_batch_t() {
   using Shp = WideShape<S>;
   using Sh = TmaShape<S, Shp::LPR, Shp::H>;
   constexpr int MODE = sizeof(S) == 8 ? MODE_F64 : MODE_CELL;
-  return cudaFuncSetAttribute(k_stencil_tma<S, Shp::LPR, Shp::H, false, MODE, false, true>,
+  return cudaFuncSetAttribute(k_stencil_tma<S, Shp::LPR, Shp::H, false, MODE, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
 }
 
@@ -761,6 +659,7 @@ cudaError_t launch_stencil_tma_batch(igg_dtype dt, const TmaTile *tiles, int nti
   return cudaErrorInvalidValue;
 }
 
+
 size_t tma_fix_cap(const TmaTile *tiles, int ntiles) {
   size_t cap = 0;
   for (int i = 0; i < ntiles; ++i) {
@@ -783,18 +682,18 @@ cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm) {
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,
-                               FixBuf fix, const HaloSend &send, cudaStream_t s) {
+                               FixBuf fix, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   switch (dt) {
     case IGG_F64:
       return launch_v<double>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix,
-                              send, s);
+                              s);
     case IGG_F32:
       return launch_v<float>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err, fix,
-                             send, s);
+                             s);
     case IGG_BF16:
       return launch_v<__nv_bfloat16>(variant, tiles, ntiles, T2, T, Ci, nx, ny, nzt, c, dev_err,
-                                     fix, send, s);
+                                     fix, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -65,6 +65,7 @@ def lib():
     L.igg_step.argtypes = [P, P, P, P, I, D, D, D, D, D, P]
     L.igg_step_hidden.argtypes = [P, IP, P, P, P, I, D, D, D, D, D, P]
     L.igg_run.argtypes = [P, I, IP, P, P, P, I, D, D, D, D, D, P]
+    L.igg_run_host.argtypes = [P, I, IP, P, P, P, P, P, I, D, D, D, D, D, P]
     L.igg_reduce.argtypes = [I, P, P, ctypes.c_size_t, I, P, P]
     L.igg_device_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint), I]
     L.igg_grid_set_option.argtypes = [P, I, I]
@@ -72,7 +73,7 @@ def lib():
                  "igg_grid_shape", "igg_subdomain_info", "igg_update_halo",
                  "igg_update_halo_staggered", "igg_update_halo_fields",
                  "igg_acoustic_step", "igg_gp_step", "igg_step",
-                 "igg_step_hidden", "igg_run", "igg_reduce", "igg_device_status",
+                 "igg_step_hidden", "igg_run", "igg_run_host", "igg_reduce", "igg_device_status",
                  "igg_grid_set_option"):
         getattr(L, name).restype = I
     _lib = L
@@ -290,6 +291,25 @@ class Grid:
                              _ptr(Ci, n, d, "Ci"), dtype_code(d), float(lam), float(dt), float(dx),
                              float(dy), float(dz), _stream(stream)))
         return T if nt % 2 == 0 else T2
+
+    def run_host(self, nt, T_host, Ci_host, T, T2, Ci, lam, dt, dx, dy, dz, widths=None,
+                 stream=None):
+        """Fig. 1's solver from host fields (igg_run_host): T_host (T0 in,
+        the newest state out) and Ci_host are CPU tensors of the fields'
+        shape, best page-locked; T, T2, Ci device buffers. Enqueued on the
+        stream: synchronise it before reading T_host."""
+        n = self.nsub * self.nloc
+        d = T.dtype
+        for name, h in (("T_host", T_host), ("Ci_host", Ci_host)):
+            if not isinstance(h, torch.Tensor) or h.is_cuda or h.dtype != d or not h.is_contiguous() \
+                    or h.numel() != n:
+                raise ValueError(f"{name} must be a contiguous CPU tensor of {n} {d} elements")
+        w = _ints(widths) if widths is not None else None
+        _check(lib().igg_run_host(self._handle(), int(nt), w, ctypes.c_void_p(T_host.data_ptr()),
+                                  ctypes.c_void_p(Ci_host.data_ptr()), _ptr(T, n, d, "T"),
+                                  _ptr(T2, n, d, "T2"), _ptr(Ci, n, d, "Ci"), dtype_code(d),
+                                  float(lam), float(dt), float(dx), float(dy), float(dz),
+                                  _stream(stream)))
 
 
 def selftest_bounded_wait() -> int:

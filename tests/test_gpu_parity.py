@@ -180,6 +180,28 @@ def test_run_parity_of_nt(nt):
     assert rel_err(gpu, ref) <= FP64_TOL
 
 
+@pytest.mark.parametrize("nt", [3, 4])
+def test_run_host_matches_run_and_oracle(nt):
+    """igg_run_host (host fields in, H2D, T2 = copy(T), nt hidden steps, D2H
+    of the newest state) equals igg_run on device fields bit for bit, and the
+    oracle within the FP64 bar."""
+    n, dims, periods, o = (70, 18, 12), (2, 2, 1), (1, 0, 0), (2, 2, 2)
+    T0o, Cio, dd, ng = oracle_fields(n, dims, periods, o, 4)
+    dt = oracle.cfl_dt(*dd, 1.0, Cio.max())
+    ref = oracle.run_decomposed(T0o, Cio, nt, 1.0, dt, *dd, dims, periods, o)
+    with igg.Grid(n, dims=dims, overlap=o, periods=periods) as g:
+        T0, Ci = grid_fields(g, 4)
+        Th = torch.from_numpy(T0.copy()).pin_memory()
+        Ch = torch.from_numpy(Ci.copy()).pin_memory()
+        T, T2, Cd = (torch.empty(g.shape, dtype=torch.float64, device="cuda") for _ in range(3))
+        g.run_host(nt, Th, Ch, T, T2, Cd, 1.0, dt, *dd, widths=(16, 2, 2))
+        torch.cuda.synchronize()
+        A = dev(T0)
+        r = g.run(nt, A, A.clone(), dev(Ci), 1.0, dt, *dd, widths=(16, 2, 2))
+        assert torch.equal(Th.view(torch.int64), r.cpu().view(torch.int64))
+    assert rel_err(Th.numpy(), ref) <= FP64_TOL
+
+
 def test_minimum_size_one_inner_point():
     n = (3, 3, 3)
     gpu, ref = _run_both(n, (1, 1, 1), (0, 0, 0), (2, 2, 2), nt=3, widths=(2, 2, 2))
