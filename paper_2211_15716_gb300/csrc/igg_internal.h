@@ -39,7 +39,11 @@ constexpr int kTileY = 8;
 struct Coef {
   double wx, wy, wz, wc;
   int f64_emu;  // FP64 fields: 1 = emulated FP64 cell, 0 = FP64 cell
-  int pad;
+  // TMA full steps followed by a halo update: the row end cells x = 0 and
+  // x = n_x - 1 of every computed row are stored as well, with their values
+  // in T (boundary cells keep them; halo cells are overwritten by the halo
+  // update), so that every row store covers whole 32-byte sectors
+  int ends;
 };
 
 Coef make_coef(double lam, double dt, double dx, double dy, double dz);

@@ -52,7 +52,7 @@ Coef make_coef(double lam, double dt, double dx, double dy, double dz) {
   c.wz = k / (dz * dz);
   c.wc = -2.0 * (c.wx + c.wy + c.wz);
   c.f64_emu = 0;
-  c.pad = 0;
+  c.ends = 0;
   return c;
 }
 
@@ -729,6 +729,7 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   if (!widths) {
     TileSet *full = nullptr;
     if (int rc = build_full_tiles(g, V, &full)) return rc;
+    c.ends = with_halo && any_halo(g) ? 1 : 0;
     e = launch_tiles(g, V, dt, *full, T2, T, Ci, c, s);
     if (e != cudaSuccess) return cuda_error(e, "stencil launch");
     if (with_halo && any_halo(g)) {

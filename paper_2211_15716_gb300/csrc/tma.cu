@@ -295,6 +295,14 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 #pragma unroll
     for (int i = 0; i < V; ++i)
       if (xs + i >= t.xb && xs + i < t.xe) inm |= 1u << i;
+    // row end cells stored with their T values (Coef::ends; full-step tiles)
+    unsigned endm = 0u;
+    if (!BATCH && !SWAP && c0.ends) {
+#pragma unroll
+      for (int i = 0; i < V; ++i)
+        if (xs + i == 0 || xs + i == nx - 1) endm |= 1u << i;
+    }
+    const bool full_st = full_vec || (inm | endm) == (1u << V) - 1u;
     const long long sy = nx, sz = (long long)nx * ny;
     const long long srow = SWAP ? sz : sy, smarch = SWAP ? sy : sz;
     Vec<S> zm[Sh::RPT];
@@ -365,7 +373,12 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
           // every point of the box is stored; points the fast path did not
           // take are stored again by the fix-up launch
           S *dst = T2 + t.base + xs + srow * (t.r0 + r) + smarch * m;
-          if (full_vec) {
+          if (full_st) {
+            if (endm) {
+#pragma unroll
+              for (int i = 0; i < V; ++i)
+                if (endm >> i & 1u) out.v[i] = c.v[i];
+            }
             *reinterpret_cast<uint4 *>(dst) = pack(out);
           } else {
 #pragma unroll
@@ -421,8 +434,10 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 // did not take get cell() (the same choice and arithmetic as every kernel:
 // the shifted-significand form where the stencil crosses one power of two,
 // else the FP64 cell). The kernel listed every 32-point row segment with such
-// points; the fix-up's warps take the entries in turn, lane l updating point
-// p + l when bit l is set. The last block to finish resets the list.
+// points (its first point and a bit mask); the fix-up's warps take the
+// entries in turn, lane l updating point p + l when bit l is set, each warp
+// loading its next entry while it works on the current one. The last block
+// to finish resets the list.
 __global__ void __launch_bounds__(256)
     k_fixup_f64(void *__restrict__ fix, size_t cap, double *__restrict__ T2,
                 const double *__restrict__ T, const double *__restrict__ Ci, int nx, int ny,
@@ -433,14 +448,20 @@ __global__ void __launch_bounds__(256)
   const long long sy = nx, sz = (long long)nx * ny;
   const int lane = threadIdx.x & 31;
   const unsigned warps = gridDim.x * (blockDim.x >> 5);
-  for (unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < count; e += warps) {
-    const FixEntry en = fl.e[e];
-    if (!(en.bits >> lane & 1u)) continue;
-    const long long p = en.p + lane;
-    const double tc = __ldg(T + p);
-    const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
-                          __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-    T2[p] = cell(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+  unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  FixEntry en = {};
+  if (e < count) en = fl.e[e];
+  for (; e < count; e += warps) {
+    FixEntry nxt = {};
+    if (e + warps < count) nxt = fl.e[e + warps];
+    if (en.bits >> lane & 1u) {
+      const long long p = en.p + lane;
+      const double tc = __ldg(T + p);
+      const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
+                            __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
+      T2[p] = cell(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+    }
+    en = nxt;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
