@@ -107,21 +107,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = ("tma.cu", "tma_util.cuh", "cell.cuh", "igg_internal.h")
+KERNEL_SOURCES = ("tma.cu", "tma_util.cuh", "cell.cuh", "igg_internal.h", "runtime.cu")
 
 
 def kernel_source_sha256() -> str:
-    """Hash of the sources of the stencil kernel the roofline reports."""
+    """Hash of the sources of the stencil kernel the roofline reports and of
+    the runtime that builds its tile tables and arguments."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2211_15716_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
 
-def traffic_for(key: str):
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def traffic_for(key: str, path: str = TRAFFIC_JSON):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel sources changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)[key]
@@ -130,6 +133,50 @@ def traffic_for(key: str):
         return float(rec["dram_bytes_per_launch"])
     except Exception:
         return None
+
+
+_UNIT = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12,
+         "KB": 1e3, "MB": 1e6, "GB": 1e9}
+
+
+def record_traffic(csv_path: str, key: str, kernel: str, scale: float, how: str,
+                   path: str = TRAFFIC_JSON) -> dict:
+    """Writes profiles/traffic.json[key] from an ncu raw-page CSV export
+    (ncu -i <rep> --page raw --csv): the mean over the launches of `kernel`
+    (a substring of the kernel name) of dram__bytes_read.sum +
+    dram__bytes_write.sum, times `scale` (captured case -> bench launch),
+    with the hash of the current kernel sources, so that the figure is
+    dropped from the bench line as soon as those sources change."""
+    import csv
+    with open(csv_path, newline="") as f:
+        rows = list(csv.reader(f))
+    head = rows[0]
+    units = rows[1]
+    ik = head.index("Kernel Name")
+    ir, iw = head.index("dram__bytes_read.sum"), head.index("dram__bytes_write.sum")
+    tot = []
+    for r in rows[2:]:
+        if len(r) <= max(ik, ir, iw) or kernel not in r[ik]:
+            continue
+        b = float(r[ir].replace(",", "")) * _UNIT[units[ir]] + \
+            float(r[iw].replace(",", "")) * _UNIT[units[iw]]
+        tot.append(b)
+    if not tot:
+        raise SystemExit(f"no launch of {kernel} in {csv_path}")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except FileNotFoundError:
+        rec = {}
+    mean = sum(tot) / len(tot)
+    rec[key] = {"source_sha256": kernel_source_sha256(),
+                "dram_bytes_per_launch": int(round(mean * scale)),
+                "captured_bytes_per_launch": int(round(mean)), "launches": len(tot),
+                "scale": scale, "how": how}
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=2)
+        f.write("\n")
+    return rec[key]
 
 
 def oracle_baseline(budget_s: float = 12.0):
@@ -164,18 +211,15 @@ def oracle_baseline(budget_s: float = 12.0):
             "cell_updates_per_s": inner * reps / el}
 
 
-def grid_launches_per_hidden_step(grid, w, dtype="f64", f64_emu=True, fused=True) -> int:
-    """Kernel launches of one hidden step.  Fused (the default on TMA tiles):
-    one step launch that also stores the sent planes into the halo cells.
-    Split: the two boundary launches (z slabs with the x ends, y slabs), the
-    halo copies of each dimension with neighbours, and the inner block.  With
-    the emulated FP64 cell every stencil launch is followed by its fix-up."""
-    per_stencil = 1
-    if fused:
-        return per_stencil
+def grid_launches_per_step(grid, dtype="f64", f64_emu=True) -> int:
+    """Kernel launches of one step of the default (full-step) form: the
+    stencil launch, the emulated FP64 cell's fix-up launch (FP64 fields), and
+    the one-launch halo update of 3-D grids with neighbours."""
+    n = 1 + (1 if dtype == "f64" and f64_emu else 0)
     dims, periods = grid.dims, grid.periods
-    halo = sum(1 for d in range(3) if dims[d] > 1 or periods[d])
-    return per_stencil * (2 + 1) + halo
+    if any(dims[d] > 1 or periods[d] for d in range(3)):
+        n += 1
+    return n
 
 
 def run_reference(args, ws, rank):
@@ -528,6 +572,133 @@ def run_forms(args):
     return 0
 
 
+E2E_NT = 100       # steps of the end-to-end job (Fig. 1's nt)
+SUSTAINED_S = 0.5  # least duration of the sustained timed block
+PHASE_STEPS = 20   # eagerly queued steps timed per phase for the roofline
+
+
+def timed_steps(grid, w, fields, nt, stream, widths="default"):
+    """nt steps of the graph-captured loop on `stream`, CUDA-event timed:
+    (ms, fields with the newest state first)."""
+    T, T2, Ci, dt, dx, dy, dz = fields
+    wd = w.widths if widths == "default" else widths
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cur = grid.run(nt, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=wd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if cur is T2:
+        T, T2 = T2, T
+    return e0.elapsed_time(e1), (T, T2, Ci, dt, dx, dy, dz)
+
+
+def phase_ms(grid, w, fields, steps, hidden=True):
+    """Per-step device time of the stencil phase (the stencil launch with its
+    fix-up launch) and of the halo update, from the library's phase events
+    around `steps` eagerly queued steps: the same launches, tile tables and
+    arguments as the steps inside the timed graphs."""
+    T, T2, Ci, dt, dx, dy, dz = fields
+    grid.set_option(grid.OPT_PHASE_TIMES, 1)
+    for _ in range(steps):
+        if hidden:
+            grid.step_hidden(w.widths, T2, T, Ci, w.lam, dt, dx, dy, dz)
+        else:
+            grid.step(T2, T, Ci, w.lam, dt, dx, dy, dz)
+        T, T2 = T2, T
+    a, b, tot, n = grid.phase_times()
+    grid.set_option(grid.OPT_PHASE_TIMES, 0)
+    return a / n, b / n, (T, T2, Ci, dt, dx, dy, dz)
+
+
+def worst_case(args, grid, w_name, Ci, dt, dd, stream):
+    """The hidden step on the sign-changing T0 (sine modes about 0), same grid,
+    Ci and dt: ms per step and the share of points the emulated FP64 cell
+    left to its fix-up launch."""
+    from paper_2211_15716_gb300 import workloads as wl
+    w = wl.WORKLOADS[w_name]
+    T, T2, _ = wl.make_fields(w, grid, torch.float64)
+    f = (T, T2, Ci, dt, *dd)
+    _, f = timed_steps(grid, w, f, 4, stream)
+    grid.fixup_stats(clear=True)
+    steps = max(10, args.steps)
+    ms, f = timed_steps(grid, w, f, steps, stream)
+    segs, pts = grid.fixup_stats(clear=True)
+    inner = grid.nsub * (w.n[0] - 2) * (w.n[1] - 2) * (w.n[2] - 2)
+    bytes_step = 3 * grid.nsub * grid.nloc * 8
+    a, b, f = phase_ms(grid, w, f, 6)
+    del f, T, T2
+    torch.cuda.empty_cache()
+    return {"workload": w_name, "ms_per_step": round(ms / steps, 4),
+            "GB_s": round(bytes_step / (ms / steps * 1e-3) / 1e9, 1),
+            "fixup_point_share": round(pts / (steps * inner), 5),
+            "fixup_segments_per_step": round(segs / steps, 1),
+            "stencil_phase_ms": round(a, 4), "halo_ms": round(b, 4),
+            "note": "T0 = 8 sine modes of amplitude 0.1 about 0; parity at 1e-12 in the GPU tests"}
+
+
+def cfg1_other_dtype(args, grid, w, tdt, dd_dt, ref64, stream):
+    """The cfg1 hidden step with FP32 or BF16 fields: ms per step for the
+    default form and the split, and the error after E2E_NT steps against the
+    FP64 GPU form (max |dT| / max |T|)."""
+    from paper_2211_15716_gb300 import workloads as wl
+    dx, dy, dz, dt = dd_dt
+    T, T2, Ci = wl.make_fields(w, grid, tdt)
+    f = (T, T2, Ci, dt, dx, dy, dz)
+    _, f = timed_steps(grid, w, f, 4, stream)
+    steps = max(10, args.steps)
+    ms, f = timed_steps(grid, w, f, steps, stream)
+    a, b, f = phase_ms(grid, w, f, 6)
+    grid.set_option(grid.OPT_FUSED_HALO, 0)
+    ms_split, f = timed_steps(grid, w, f, steps, stream)
+    grid.set_option(grid.OPT_FUSED_HALO, 1)
+    s = T.element_size()
+    bytes_step = 3 * grid.nsub * grid.nloc * s
+    T, T2, Ci = wl.make_fields(w, grid, tdt)
+    cur = grid.run(E2E_NT, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)
+    err = float((cur.double() - ref64).abs().max() / ref64.abs().max())
+    del T, T2, Ci, cur, f
+    torch.cuda.empty_cache()
+    ms_s = ms / steps
+    return {"ms_per_step": round(ms_s, 4), "GB_s": round(bytes_step / (ms_s * 1e-3) / 1e9, 1),
+            "frac_of_hbm": round(bytes_step / (ms_s * 1e-3) / 1e9 / peaks()[0], 3),
+            "stencil_phase_ms": round(a, 4), "halo_ms": round(b, 4),
+            "split_ms_per_step": round(ms_split / steps, 4),
+            f"max_err_rel_vs_fp64_gpu_nt{E2E_NT}": err}
+
+
+def compact_forms(args, budget_s):
+    """The reshaped forms, each against the FP64 form on the same GPU at a
+    stated accuracy, within about budget_s seconds (later forms are skipped
+    once the budget is spent, and say so)."""
+    out, t0 = {}, time.perf_counter()
+    hbm = peaks()[0]
+    jobs = (("precision_1024", lambda: form_precision(20)),
+            ("batched_256", lambda: form_batched(max(20, args.steps))),
+            ("adjoint_256", form_adjoint),
+            ("acoustic_2x2x2x256", lambda: form_acoustic(20)),
+            ("gross_pitaevskii_2x2x2x256", lambda: form_gp(20)))
+    for name, fn in jobs:
+        if time.perf_counter() - t0 > budget_s:
+            out[name] = {"skipped": f"time budget of {budget_s:.0f} s spent"}
+            continue
+        t1 = time.perf_counter()
+        r = fn()
+        torch.cuda.empty_cache()
+        r["seconds"] = round(time.perf_counter() - t1, 1)
+        out[name] = _with_fracs(r, hbm)
+    return out
+
+
+def _with_fracs(r, hbm):
+    """Adds frac_of_hbm beside every T_eff_GB_s of a form's result."""
+    if isinstance(r, dict):
+        for k in list(r):
+            r[k] = _with_fracs(r[k], hbm)
+        if "T_eff_GB_s" in r:
+            r["frac_of_hbm"] = round(r["T_eff_GB_s"] / hbm, 3)
+    return r
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -535,14 +706,28 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="leave the reshaped forms out of the JSON line")
+    ap.add_argument("--forms-budget", type=float, default=60.0,
+                    help="seconds allowed for the reshaped forms")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="decomposed_2x2x2_512x256x256 (default) or a smaller case for profiling")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--forms", action="store_true",
-                    help="measure the precision, batched and adjoint forms (extra JSON lines)")
+                    help="only measure the reshaped forms (one JSON line each)")
     ap.add_argument("--profile", choices=["adjoint", "gp"],
                     help="run a short fixed workload of one kernel for an ncu capture")
+    ap.add_argument("--record-traffic", metavar="CSV",
+                    help="write profiles/traffic.json from an ncu raw CSV export (no GPU)")
+    ap.add_argument("--traffic-key", default=f"hidden step stencil f64 {WORKLOAD}")
+    ap.add_argument("--traffic-kernel", default="k_stencil_tma")
+    ap.add_argument("--traffic-scale", type=float, default=8.0)
+    ap.add_argument("--traffic-how", default="")
     args = ap.parse_args()
+    if args.record_traffic:
+        print(json.dumps(record_traffic(args.record_traffic, args.traffic_key, args.traffic_kernel,
+                                        args.traffic_scale, args.traffic_how)))
+        return 0
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
@@ -565,6 +750,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     igg_build.build()
+    headline = args.workload == WORKLOAD and args.dtype == "f64"
 
     w = wl.WORKLOADS[args.workload]
     tdtype = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[args.dtype]
@@ -581,108 +767,103 @@ def main():
     s = T.element_size()
     bytes_step = 3 * N * s
     stream = torch.cuda.current_stream()
+    fields = (T, T2, Ci, dt, dx, dy, dz)
 
     # warm-up (also captures the two-step CUDA graph)
-    cur = grid.run(args.warmup, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)
-    if cur is T2:
-        T, T2 = T2, T
-    torch.cuda.synchronize()
+    _, fields = timed_steps(grid, w, fields, args.warmup, stream)
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
-    # ---- timed region: K hidden steps -----------------------------------
+    # ---- timed region: exactly K hidden steps ----------------------------
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    e0.record(stream)
-    cur = grid.run(args.steps, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, fields = timed_steps(grid, w, fields, args.steps, stream)
     barrier()
-    ms = dist_max(e0.elapsed_time(e1), ws)
-    if cur is T2:
-        T, T2 = T2, T
+    ms = dist_max(ms, ws)
     ms_step = ms / args.steps
 
-    # ---- dominant kernel: the full-step stencil kernel on this stream ----
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kreps = max(10, args.steps // 2)
-    k0.record(stream)
-    for _ in range(kreps):
-        grid.step(T2, T, Ci, w.lam, dt, dx, dy, dz)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    k_ms = k0.elapsed_time(k1) / kreps
+    # ---- sustained block: the same loop for at least SUSTAINED_S seconds --
+    sus_steps = max(args.steps, 2 * int(math.ceil(SUSTAINED_S / (ms_step * 1e-3) / 2)))
+    barrier()
+    ms_sus, fields = timed_steps(grid, w, fields, sus_steps, stream)
+    barrier()
+    ms_sus = dist_max(ms_sus, ws)
 
-    # ---- per-sample step times (outside the timed region): median and a
-    # 95 % confidence interval of the median from order statistics ---------
+    # ---- dominant launch: the stencil phase of the same hidden steps ------
+    k_ms, halo_ms, fields = phase_ms(grid, w, fields, PHASE_STEPS)
+    clocks = sampler.stop()
+    plain_k_ms, _, fields = phase_ms(grid, w, fields, PHASE_STEPS, hidden=False)
+
+    # ---- per-sample step times: median and a 95 % confidence interval ----
+    T, T2, Ci = fields[:3]
     samples = step_samples(lambda: grid.run(2, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths),
                            40, stream, 2)
 
-    # ---- variants (outside the timed region): plain step, FP64 cell -------
+    # ---- variants (outside the timed region) ------------------------------
     variants = {}
-    vsteps = max(10, args.steps // 4)
-
-    def time_run(widths):
-        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        grid.run(2, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=widths)
-        v0.record(stream)
-        grid.run(vsteps, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=widths)
-        v1.record(stream)
-        torch.cuda.synchronize()
-        return v0.elapsed_time(v1) / vsteps
-
-    t_plain = time_run(None)
-    variants["plain_step_no_hiding"] = {"ms_per_step": round(t_plain, 4),
-                                        "GB_s": round(bytes_step / (t_plain * 1e-3) / 1e9, 1)}
+    vsteps = max(10, args.steps // 2)
+    t_plain, fields = timed_steps(grid, w, fields, vsteps, stream, widths=None)
+    t_plain /= vsteps
+    variants["plain_step_no_hiding"] = {
+        "ms_per_step": round(t_plain, 4), "GB_s": round(bytes_step / (t_plain * 1e-3) / 1e9, 1),
+        "note": "igg_run without widths: step then halo update, the launches of the default "
+                "hidden form"}
     grid.set_option(grid.OPT_FUSED_HALO, 0)
-    t_split = time_run(w.widths)
+    t_split, fields = timed_steps(grid, w, fields, vsteps, stream)
     grid.set_option(grid.OPT_FUSED_HALO, 1)
+    t_split /= vsteps
     variants["hidden_step_split"] = {"ms_per_step": round(t_split, 4),
                                      "GB_s": round(bytes_step / (t_split * 1e-3) / 1e9, 1),
-                                     "note": "boundary/inner split on two streams with plane copies"}
+                                     "note": "boundary/inner split on two streams"}
+    variants["plain_step_kernel"] = {
+        "stencil_phase_ms": round(plain_k_ms, 4),
+        "GB_s": round(bytes_step / (plain_k_ms * 1e-3) / 1e9, 1),
+        "note": "igg_step (no halo): the stencil launch without the halo-carrying row ends"}
     if tdtype == torch.float64:
         grid.set_option(grid.OPT_F64_EMU, 0)
-        t_nat = time_run(w.widths)
+        t_nat, fields = timed_steps(grid, w, fields, vsteps, stream)
         grid.set_option(grid.OPT_F64_EMU, 1)
+        t_nat /= vsteps
         variants["hidden_step_fp64_cell"] = {"ms_per_step": round(t_nat, 4),
                                              "GB_s": round(bytes_step / (t_nat * 1e-3) / 1e9, 1)}
+    grid.fixup_stats(clear=True)
+    _, fields = timed_steps(grid, w, fields, 2, stream)
+    segs, pts = grid.fixup_stats(clear=True)
     status = grid.device_status()
 
-    # ---- end to end: host inputs -> K steps -> host result ----------------
+    # ---- end to end through the library: igg_run_host, fixed nt -----------
+    T, T2, Ci = fields[:3]
+    T0, _, C0 = wl.make_fields(w, grid, tdtype)
     Th = torch.empty(T.shape, dtype=T.dtype, pin_memory=True)
     Ch = torch.empty(Ci.shape, dtype=Ci.dtype, pin_memory=True)
-    Rh = torch.empty(T.shape, dtype=T.dtype, pin_memory=True)
-    Th.copy_(T)
-    Ch.copy_(Ci)
+    Th.copy_(T0)
+    Ch.copy_(C0)
+    del T0, C0, _
     torch.cuda.synchronize()
     barrier()
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0 = time.perf_counter()
     x0.record(stream)
-    T.copy_(Th, non_blocking=True)
-    Ci.copy_(Ch, non_blocking=True)
-    T2.copy_(T)  # Fig. 1: T2 = copy(T), on the device
-    cur = grid.run(args.steps, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)
-    Rh.copy_(cur, non_blocking=True)
+    grid.run_host(E2E_NT, Th, Ch, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)
     x1.record(stream)
     torch.cuda.synchronize()
+    wall = time.perf_counter() - h0
     barrier()
     e2e_ms = dist_max(x0.elapsed_time(x1), ws)
-    assert torch.isfinite(Rh[0, 5, 5, :8].float()).all()
+    ref_nt = T2 if E2E_NT % 2 else T  # the newest state on the device
+    assert torch.equal(Th.view(-1)[:64].to(ref_nt.device), ref_nt.view(-1)[:64])
+    ref64 = ref_nt.double().clone() if (headline and rank == 0 and not args.no_forms) else None
 
     hbm, hbm_kind = peaks()
-    # our kernels per hidden step (fused halo update: one step launch, plus
-    # the fix-up launch of the emulated FP64 cell)
-    launches_per_step = grid_launches_per_hidden_step(grid, w, args.dtype, True, True)
+    launches_per_step = grid_launches_per_step(grid, args.dtype, True)
     value = ws * bytes_step / (ms_step * 1e-3) / 1e9
     achieved = bytes_step / (k_ms * 1e-3) / 1e9
-    traffic = traffic_for(f"full step {args.dtype} {args.workload}")
+    traffic = traffic_for(f"hidden step stencil {args.dtype} {args.workload}")
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -694,37 +875,65 @@ def main():
                    "cells": N, "inner_cells": inner, "bytes_per_step": bytes_step,
                    "l2": f"inputs larger than L2 ({bytes_step / 1e9:.2f} GB moved per step vs 129 MB L2)",
                    "graph": "two steps per CUDA graph launch",
-                   "hiding": "halo update fused into the step launch (sent planes stored into "
-                             "the neighbours' halo cells); the boundary/inner split is a variant"},
+                   "hiding": "all subdomains in one device's memory: each hidden step is the full "
+                             "step launch followed by the one-launch halo update of T2; the "
+                             "paper's boundary/inner split on two streams is a variant"},
         "cell_updates_per_s": ws * inner / (ms_step * 1e-3),
         "frac_of_8TBs": round(value / ws / 8000.0, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": traffic,
-                     "kernel": (f"k_stencil_tma<{args.dtype}> (TMA-pipelined, full step, all "
-                                "subdomains; with the emulated FP64 cell's fix-up launch), the "
-                                "step launch of the timed region without its halo tail"),
-                     "peak_kind": hbm_kind, "kernel_ms": round(k_ms, 4)},
-        "e2e": {"value": round(ws * bytes_step * args.steps / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-                "h2d_bytes_per_step": int(2 * N * s / args.steps),
-                "d2h_bytes_per_step": int(N * s / args.steps),
-                "note": ("one job: H2D of T and Ci from pinned memory, T2 = copy(T) on the "
-                         "device, K steps, D2H of the result")},
+                     "kernel": (f"k_stencil_tma<{args.dtype}> + k_fixup_f64 (the stencil phase of "
+                                "the timed hidden step: same launches, tiles and row-end stores), "
+                                "CUDA events around each step's stencil phase, "
+                                f"{PHASE_STEPS} steps"),
+                     "algorithmic_bytes_per_launch": bytes_step,
+                     "peak_kind": hbm_kind, "kernel_ms": round(k_ms, 4),
+                     "halo_update_ms": round(halo_ms, 4)},
+        "sustained": {"steps": sus_steps, "seconds": round(ms_sus * 1e-3, 3),
+                      "ms_per_step": round(ms_sus / sus_steps, 4),
+                      "value": round(ws * bytes_step / (ms_sus / sus_steps * 1e-3) / 1e9, 2)},
+        "e2e": {"value": round(ws * bytes_step * E2E_NT / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+                "nt": E2E_NT, "ms": round(e2e_ms, 3), "wall_s": round(wall, 4),
+                "h2d_bytes_per_step": int(2 * N * s // E2E_NT),
+                "d2h_bytes_per_step": int(N * s // E2E_NT),
+                "note": (f"igg_run_host: H2D of T0 and Ci from pinned memory, T2 = copy(T) on the "
+                         f"device, {E2E_NT} steps, D2H of the result, one C-ABI call")},
         "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_per_step": launches_per_step,
         "clocks": clocks,
         "variants": variants,
         "step_samples": samples,
         "device_status": status,
     }
     if tdtype == torch.float64:
-        line["f64_cell"] = ("emulated: exact integer second differences, float-float weights, "
-                            "2 FP64 FMAs per point; stencils crossing one power of two from "
-                            "shifted significands, the FP64 cell for sign changes and wider "
-                            "spreads (both in the fix-up launch)")
+        line["f64_cell"] = ("emulated: exact integer second differences from the bit patterns, "
+                            "float-pair weighted sums, one FP64 FMA and an integer ulp correction "
+                            "per point; other stencils (sign changes, powers of two crossed) in "
+                            "the fix-up launch")
+        line["fixup_point_share"] = round(pts / (2 * inner), 6)
+    if headline:
+        line["variants"]["worst_case_sign_changing_field"] = worst_case(
+            args, grid, WORKLOAD + "_signed", fields[2], dt, (dx, dy, dz), stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         line["cpu_baseline"] = oracle_baseline()
+    if headline and rank == 0 and not args.no_forms:
+        forms = {}
+        t_f = time.perf_counter()
+        for name, tdt in (("cfg1_f32", torch.float32), ("cfg1_bf16", torch.bfloat16)):
+            forms[name] = cfg1_other_dtype(args, grid, w, tdt, (dx, dy, dz, dt), ref64, stream)
+        del ref64
+        grid.finalize()
+        grid = None
+        del fields, T, T2, Ci
+        torch.cuda.empty_cache()
+        left = args.forms_budget - (time.perf_counter() - t_f)
+        forms.update(compact_forms(args, max(0.0, left)))
+        forms["seconds"] = round(time.perf_counter() - t_f, 1)
+        line["forms"] = forms
     if rank == 0:
         print(json.dumps(line), flush=True)
-    grid.finalize()
+    if grid is not None:
+        grid.finalize()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0

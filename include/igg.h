@@ -186,20 +186,53 @@ int igg_selftest_bounded_wait(unsigned *status);
  *     differences are formed exactly from the bit patterns as integers,
  *     weighted in float-float pairs and applied with one FP64 FMA and an
  *     integer ulp correction (per-step error within about one ulp of T2 plus
- *     2^-44 of Ci sum_d |w_d D_d|); stencils across one power of two take
- *     the same sums from shifted significands and two FP64 FMAs; other
- *     points, and all points with 0 (or weights above 2^40), use the FP64
- *     cell (8 FP64 instructions per point).
+ *     2^-44 of Ci sum_d |w_d D_d|); stencils across powers of two or across
+ *     zero put their values on the grid of the largest value's ulp (the
+ *     aligned path, two FP64 FMAs, error within a few of those ulps); the
+ *     rest (relative second differences above about 2^-5, values near
+ *     overflow or underflow, weights above 2^40) use the FP64 cell (8 FP64
+ *     instructions per point). On the TMA kernel the points outside the
+ *     one-FMA path go to a fix-up launch, so fields where many stencils
+ *     change sign or exponent step several times slower; the FP64 cell
+ *     (option 0) is then the faster choice (see igg_fixup_stats).
  *   IGG_OPT_FUSED_HALO (default 1): igg_step_hidden (and igg_run with
  *     widths) run as the full step launch followed by the one-launch halo
  *     update (all subdomains being in the device's memory, no transfer is
  *     left to overlap, and the split's extra launches cost more than they
  *     hide); 0 selects the boundary/inner split described at
- *     igg_step_hidden. Bit-identical results either way. */
+ *     igg_step_hidden. Bit-identical results either way.
+ *   IGG_OPT_PHASE_TIMES (default 0): every step queued outside CUDA-graph
+ *     capture (igg_step, igg_step_hidden, the odd last step of igg_run)
+ *     records three CUDA events on its stream: at its start, after its
+ *     stencil launches (with the emulated FP64 cell's fix-up launch), at its
+ *     end; igg_phase_times reads them. Steps inside igg_run's graphs are not
+ *     timed. Setting the option drops the steps recorded so far. */
 #define IGG_OPT_TMA 1
 #define IGG_OPT_F64_EMU 2
 #define IGG_OPT_FUSED_HALO 3
+#define IGG_OPT_PHASE_TIMES 4
 int igg_grid_set_option(igg_grid *grid, int option, int value);
+
+/* Per-phase device time of the steps recorded under IGG_OPT_PHASE_TIMES
+ * since the last call (at most 4096 steps; later steps are not recorded):
+ * ms[0] = the stencil phase (full-step form: the stencil launch and its
+ * fix-up launch; split form: from the step's start to the end of the
+ * high-priority stream's boundary slabs and halo update), ms[1] = the rest
+ * of the step (full-step form: the halo update; split form: the remainder
+ * of the inner block until both streams joined), ms[2] = ms[0] + ms[1],
+ * each summed over the steps; *steps = their number. Waits for the last
+ * recorded step; the record is then emptied. No counterpart in the paper
+ * (which times whole steps): a measurement aid of the library. */
+int igg_phase_times(igg_grid *grid, double ms[3], int *steps);
+
+/* Points the emulated FP64 cell left to its fix-up launch: counts[0] = the
+ * 32-point row segments listed, counts[1] = the points in them, summed over
+ * every FP64 step the grid ran with the TMA kernel since the grid was made
+ * (or last cleared); clear != 0 resets both to 0. Synchronises the device.
+ * No counterpart in the paper: it shows how much of a field takes the slow
+ * path of the emulated cell (stencils that change sign or cross powers of
+ * two). */
+int igg_fixup_stats(igg_grid *grid, unsigned long long counts[2], int clear);
 
 /* ---------------------------------------------------------------------------
  * Diffusion step (Fig. 1 step!) on every subdomain:

@@ -135,9 +135,11 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // Stencils whose exponents take two neighbouring values (the shells where a
 // smooth field crosses a power of two) get the same weighted sum from exact
 // differences of the significands shifted to the smaller exponent's scale
-// (emu_spread_d). Stencils with mixed signs, a wider exponent spread or E
-// outside the ranges take cell_f64. The choice depends only on the point's
-// inputs, so every kernel makes the same choice and produces the same bits.
+// (emu_spread_d). These helpers form the adjoint's gradient sum (adj_cell.cuh);
+// the step's cell (cell_emu, below) uses the one-FMA fast path and, for
+// stencils across powers of two or across zero, the aligned path, else
+// cell_f64. The choice depends only on the point's inputs, so every kernel
+// makes the same choice and produces the same bits.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double v) {
   return (unsigned long long)__double_as_longlong(v);
@@ -295,15 +297,6 @@ __device__ __forceinline__ bool emu_spread_d(double tc, const unsigned long long
   }
   scale_hi = (hc & 0x80000000u) | (emin << 20);
   return ok;
-}
-
-// The emulated update of a stencil crossing one power of two (emu_spread_d
-// holds): tc + ci * l(T) from the shifted significands' differences.
-__device__ __forceinline__ double cell_emu_spread(double tc, const long long *D, unsigned sh,
-                                                  double ci, const W<double> &w) {
-  if (w.ng == 1) return emu_apply(tc, ci, emu_lap_d<1>(D, sh, w));
-  if (w.ng == 2) return emu_apply(tc, ci, emu_lap_d<2>(D, sh, w));
-  return emu_apply(tc, ci, emu_lap_d<3>(D, sh, w));
 }
 
 // ---------------------------------------------------------------------------
@@ -492,20 +485,126 @@ __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long l
   return cell_emu_fast<3>(tc, nb, ci, w, ok);
 }
 
-// One point: the emulated cell's fast path where it applies, else where the
-// stencil crosses at most one power of two the emulated cell from shifted
-// significands, else cell_f64.
+// ---------------------------------------------------------------------------
+// Aligned path of the emulated FP64 cell: stencils whose values differ in
+// exponent (a field crossing powers of two) or in sign (a field crossing 0).
+//
+// Every value is put on the grid of u = 2^(Er-1075), Er the largest exponent
+// field of the seven: its significand (leading bit included; none for 0 and
+// subnormals, whose exponent field counts as 1) shifted right by Er - E and
+// rounded to the nearest integer (halves up), negated when its sign differs
+// from the centre's. Values of exponent Er are exact, the others within u/2;
+// the second differences of these integers (|I| <= 2^53) are exact. The
+// weighted sum S + C = sum_g w_g G_g is formed as on the fast path (same
+// split, same float-pair sums) and applied with two FP64 FMAs,
+//   T2 = fma(+-Ci, S u, fma(+-Ci, C u, T)),
+// so T2 may leave T's binade or sign. The error: the rounding of the values
+// to u (at most 2 Ci sum_d w_d u), the two FMAs (an ulp of T2 each, |T2|
+// being at most about 2^(Er-1022): within u each) and 2^-44 of
+// Ci sum_g |w_g G_g| u, i.e. a few u, u being the ulp of the stencil's
+// largest value, like the roundings of the FP64 cell's differences.
+// It applies when Er lies in [180, 2008] and every |G_g| < 2^47.
+// ---------------------------------------------------------------------------
+// b on the grid of 2^(er-1075), signed relative to the centre (bit pattern cb)
+__device__ __forceinline__ long long emu3_aligned(unsigned long long b, unsigned long long cb,
+                                                  unsigned er) {
+  const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+  const unsigned long long m =
+      (b & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(e != 0u) << 52);
+  const unsigned d = min(er - max(e, 1u), 63u);  // m < 2^53: shifts past 53 give 0
+  const unsigned long long q = d ? (m + (1ull << (d - 1u))) >> d : m;
+  return ((b ^ cb) >> 63) ? -(long long)q : (long long)q;
+}
+
+// Integer part of the aligned path: the group sums of the aligned values'
+// second differences split as on the fast path (gh, gm), and er. True when
+// er lies in [180, 2008] and every |Gh| < 2^24.
+template <int NG>
+__device__ __forceinline__ bool emu3_int(unsigned long long bc, const unsigned long long *nb,
+                                         int *gh, unsigned *gm, unsigned &er) {
+  unsigned e = (unsigned)(bc >> 52) & 0x7FFu;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) e = max(e, (unsigned)(nb[i] >> 52) & 0x7FFu);
+  er = max(e, 1u);
+  long long I[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) I[i] = emu3_aligned(nb[i], bc, er);
+  const long long c2 = 2 * emu3_aligned(bc, bc, er), B = 1ll << 22;
+  long long G[NG];  // G_g + 2^22
+  if constexpr (NG == 1) {
+    G[0] = (I[0] + I[1] - c2) + (I[2] + I[3] - c2) + (I[4] + I[5] - c2) + B;
+  } else if constexpr (NG == 2) {
+    G[0] = I[0] + I[1] - c2 + B;
+    G[1] = (I[2] + I[3] - c2) + (I[4] + I[5] - c2) + B;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) G[d] = I[2 * d] + I[2 * d + 1] - c2 + B;
+  }
+  unsigned r = 0u;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const unsigned lo = (unsigned)G[g];
+    gh[g] = (int)__funnelshift_r(lo, (unsigned)((unsigned long long)G[g] >> 32), 23);
+    gm[g] = (lo & 0x7FFFFFu) | 0x4B000000u;
+    r |= (unsigned)gh[g] + (1u << 24);
+  }
+  return er - 180u <= 1828u && r < (1u << 25);
+}
+
+// The aligned path for one point; ok tells whether it applies.
+template <int NG>
+__device__ __forceinline__ double cell_emu_aligned(double tc, const unsigned long long *nb,
+                                                   double ci, const W<double> &w, bool &ok) {
+  const unsigned long long bc = dbits(tc);
+  int gh[NG];
+  unsigned gm[NG], er;
+  ok = emu3_int<NG>(bc, nb, gh, gm, er);
+  float fh[NG], fl[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    fh[g] = __int2float_rn(gh[g]);
+    fl[g] = __uint_as_float(gm[g]);
+  }
+  EmuLap L;
+  emu2_sum<NG>(fh, fl, w, L.S, L.C);
+  L.eoff = (er << 20) - (179u << 20);
+  L.sign = (unsigned)(bc >> 32) & 0x80000000u;
+  return emu_apply(tc, ci, L);
+}
+
+__device__ __forceinline__ double cell_emu_aligned(double tc, const unsigned long long *nb,
+                                                   double ci, const W<double> &w, bool &ok) {
+  if (w.ng == 1) return cell_emu_aligned<1>(tc, nb, ci, w, ok);
+  if (w.ng == 2) return cell_emu_aligned<2>(tc, nb, ci, w, ok);
+  return cell_emu_aligned<3>(tc, nb, ci, w, ok);
+}
+
+// One point: the emulated cell's fast path where it applies, else its
+// aligned path where that applies, else cell_f64.
 __device__ __forceinline__ double cell_emu(double tc, const double *tn, double ci,
                                            const W<double> &w) {
   unsigned long long nb[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) nb[i] = dbits(tn[i]);
   bool ok;
-  const double r = cell_emu_fast(tc, nb, ci, w, ok);
+  double r = cell_emu_fast(tc, nb, ci, w, ok);
   if (ok) return r;
-  long long D[3];
-  unsigned sh;
-  if (emu_spread_d(tc, nb, D, sh)) return cell_emu_spread(tc, D, sh, ci, w);
+  r = cell_emu_aligned(tc, nb, ci, w, ok);
+  if (ok) return r;
+  return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+}
+
+// cell_emu of a point whose fast path is known not to apply (the points a
+// kernel left to its fix-up): the aligned path, else cell_f64.
+__device__ __forceinline__ double cell_emu_not_fast(double tc, const double *tn, double ci,
+                                                    const W<double> &w) {
+  if (!w.emu) return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
+  unsigned long long nb[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) nb[i] = dbits(tn[i]);
+  bool ok;
+  const double r = cell_emu_aligned(tc, nb, ci, w, ok);
+  if (ok) return r;
   return cell_f64(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], ci, w);
 }
 

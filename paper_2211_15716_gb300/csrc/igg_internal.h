@@ -170,15 +170,16 @@ cudaError_t tma_prepare(igg_dtype dt, int variant, int *ctas_per_sm);
 // Fix-up buffer of an FP64 tile set of the TMA kernel (emulated cell): room
 // for cap entries of 16 bytes (one per 32-point row segment with points left
 // to the fix-up, so cap = the set's computed points / 32 suffices), then the
-// entry count and a block counter, both zero on entry. The kernel fills it;
-// the fix-up launch that follows on the same stream updates the listed
-// points and resets the count and the counter.
+// entry count and a block counter, both zero on entry, then two 64-bit
+// totals (segments and points fixed up so far). The kernel fills it; the
+// fix-up launch that follows on the same stream updates the listed points,
+// adds to the totals and resets the count and the counter.
 struct FixBuf {
   void *p = nullptr;
   size_t cap = 0;
 };
 size_t tma_fix_cap(const TmaTile *tiles, int ntiles);
-inline size_t tma_fix_bytes(size_t cap) { return cap * 16 + 2 * sizeof(unsigned); }
+inline size_t tma_fix_bytes(size_t cap) { return cap * 16 + 2 * sizeof(unsigned) + 16; }
 cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, int ntiles,
                                void *T2, const void *T, const void *Ci, int nx, int ny,
                                long long nzt, const Coef &c, unsigned *dev_err,

@@ -13,6 +13,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "igg_internal.h"
 
 namespace igg {
@@ -370,6 +372,11 @@ struct igg_grid {
   bool tma_enabled = true;      // TMA kernel for the regular boxes when available
   int f64_emu = 1;              // FP64 fields: emulated FP64 cell (1) or FP64 cell (0)
   bool fused_halo = true;       // hidden steps: halo update fused into one step launch
+  // IGG_OPT_PHASE_TIMES: three events per step queued outside graph
+  // capture (start, end of the stencil launches, end of the step)
+  bool phase_times = false;
+  std::vector<cudaEvent_t> pev;
+  int pev_used = 0;
 };
 
 namespace {
@@ -710,6 +717,34 @@ bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->nco
 // update (the option; the alternative is the boundary/inner split).
 bool use_fused_halo(const igg_grid *g) { return g->fused_halo; }
 
+// NVTX range over a host scope: the enqueue of one phase of the step (the
+// profiler places the GPU work it launches beneath it).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Event k of the current step's phase triple when phase timing is on and s
+// is not being captured into a graph (nullptr otherwise); the triples are
+// made on demand, at most kMaxPhaseSteps steps between two queries.
+constexpr int kMaxPhaseSteps = 4096;
+cudaEvent_t phase_event(igg_grid *g, cudaStream_t s, int k) {
+  if (!g->phase_times) return nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return nullptr;
+  if (k == 0 && g->pev_used >= 3 * kMaxPhaseSteps) return nullptr;
+  const int i = k == 0 ? g->pev_used : g->pev_used - 3 + k;
+  if (i < 0) return nullptr;
+  while ((int)g->pev.size() <= i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    g->pev.push_back(e);
+  }
+  if (k == 0) g->pev_used += 3;
+  return g->pev[i];
+}
+
 // One step of Fig. 1's loop, queued on s: plain (full step, then halo update
 // of T2 on s) or hidden (boundary set + halo on the high-priority stream,
 // inner block on the low-priority stream, s joins both).
@@ -726,16 +761,27 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   // the full step launch followed by the one-launch halo update is faster
   // than the split's extra launches
   if (low_dim(g) || use_fused_halo(g)) widths = nullptr;
+  NvtxRange step_range(with_halo ? "igg step + halo" : "igg step");
+  cudaEvent_t p0 = phase_event(g, s, 0);
+  if (p0 && (e = cudaEventRecord(p0, s)) != cudaSuccess) return cuda_error(e, "record");
   if (!widths) {
     TileSet *full = nullptr;
     if (int rc = build_full_tiles(g, V, &full)) return rc;
     c.ends = with_halo && any_halo(g) ? 1 : 0;
-    e = launch_tiles(g, V, dt, *full, T2, T, Ci, c, s);
+    {
+      NvtxRange r("stencil");
+      e = launch_tiles(g, V, dt, *full, T2, T, Ci, c, s);
+    }
     if (e != cudaSuccess) return cuda_error(e, "stencil launch");
+    if (cudaEvent_t p1 = p0 ? phase_event(g, s, 1) : nullptr)
+      if ((e = cudaEventRecord(p1, s)) != cudaSuccess) return cuda_error(e, "record");
     if (with_halo && any_halo(g)) {
+      NvtxRange r("halo update");
       e = enqueue_halo(g, T2, dtype_size(dt), s);
       if (e != cudaSuccess) return cuda_error(e, "halo launch");
     }
+    if (cudaEvent_t p2 = p0 ? phase_event(g, s, 2) : nullptr)
+      if ((e = cudaEventRecord(p2, s)) != cudaSuccess) return cuda_error(e, "record");
     return IGG_OK;
   }
   SplitTiles *st = nullptr;
@@ -745,16 +791,27 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   if ((e = cudaStreamWaitEvent(g->hi, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
   if ((e = cudaStreamWaitEvent(g->lo, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
   e = cudaSuccess;
-  for (const TileSet &b : st->boundary)
-    if (e == cudaSuccess) e = launch_tiles(g, V, dt, b, T2, T, Ci, c, g->hi);
-  if (e == cudaSuccess && with_halo && any_halo(g)) e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
+  {
+    NvtxRange r("boundary slabs + halo update (high priority)");
+    for (const TileSet &b : st->boundary)
+      if (e == cudaSuccess) e = launch_tiles(g, V, dt, b, T2, T, Ci, c, g->hi);
+    if (e == cudaSuccess && with_halo && any_halo(g))
+      e = enqueue_halo(g, T2, dtype_size(dt), g->hi);
+  }
   if (e != cudaSuccess) return cuda_error(e, "boundary/halo launch");
-  e = launch_tiles(g, V, dt, st->inner, T2, T, Ci, c, g->lo);
+  {
+    NvtxRange r("inner block (low priority)");
+    e = launch_tiles(g, V, dt, st->inner, T2, T, Ci, c, g->lo);
+  }
   if (e != cudaSuccess) return cuda_error(e, "inner launch");
   if ((e = cudaEventRecord(g->ev_hi, g->hi)) != cudaSuccess) return cuda_error(e, "record");
+  if (cudaEvent_t p1 = p0 ? phase_event(g, s, 1) : nullptr)
+    if ((e = cudaEventRecord(p1, g->hi)) != cudaSuccess) return cuda_error(e, "record");
   if ((e = cudaEventRecord(g->ev_lo, g->lo)) != cudaSuccess) return cuda_error(e, "record");
   if ((e = cudaStreamWaitEvent(s, g->ev_hi, 0)) != cudaSuccess) return cuda_error(e, "wait");
   if ((e = cudaStreamWaitEvent(s, g->ev_lo, 0)) != cudaSuccess) return cuda_error(e, "wait");
+  if (cudaEvent_t p2 = p0 ? phase_event(g, s, 2) : nullptr)
+    if ((e = cudaEventRecord(p2, s)) != cudaSuccess) return cuda_error(e, "record");
   return IGG_OK;
 }
 
@@ -782,6 +839,7 @@ void destroy_grid(igg_grid *g) {
     for (int d = 0; d < 3; ++d) cudaFree(kv.second.copies[d]);
   cudaFree(g->dev_err);
   cudaFree(g->nbr);
+  for (cudaEvent_t e : g->pev) cudaEventDestroy(e);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_hi) cudaEventDestroy(g->ev_hi);
   if (g->ev_lo) cudaEventDestroy(g->ev_lo);
@@ -1179,6 +1237,7 @@ int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const v
       }
       g->graphs.emplace(key, exec);
     }
+    NvtxRange r("igg_run graph launches (two steps each)");
     for (int i = 0; i < nt / 2; ++i) {
       cudaError_t e = cudaGraphLaunch(exec, s);
       if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
@@ -1203,12 +1262,17 @@ int igg_run_host(igg_grid *g, int nt, const int widths[3], void *T_host, const v
   DeviceGuard dg(g->device);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)g->nsub * (size_t)g->nloc * dtype_size(dt);
-  cudaError_t e = cudaMemcpyAsync(T, T_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Ci, Ci_host, bytes, cudaMemcpyHostToDevice, s);
-  // Fig. 1: T2 = copy(T) (the boundary values stay fixed in both buffers)
-  if (e == cudaSuccess) e = cudaMemcpyAsync(T2, T, bytes, cudaMemcpyDeviceToDevice, s);
+  cudaError_t e;
+  {
+    NvtxRange r("igg_run_host inputs (H2D, T2 = T)");
+    e = cudaMemcpyAsync(T, T_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Ci, Ci_host, bytes, cudaMemcpyHostToDevice, s);
+    // Fig. 1: T2 = copy(T) (the boundary values stay fixed in both buffers)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T2, T, bytes, cudaMemcpyDeviceToDevice, s);
+  }
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(inputs)");
   if (int rc = igg_run(g, nt, widths, T, T2, Ci, dt, lam, dtime, dx, dy, dz, stream)) return rc;
+  NvtxRange r("igg_run_host result (D2H)");
   e = cudaMemcpyAsync(T_host, nt % 2 ? T2 : T, bytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(result)");
   return IGG_OK;
@@ -1401,12 +1465,18 @@ int igg_device_status(igg_grid *g, unsigned *status, int clear) {
 int igg_grid_set_option(igg_grid *g, int option, int value) {
   clear_error();
   if (int rc = check_grid(g)) return rc;
-  if (option != IGG_OPT_TMA && option != IGG_OPT_F64_EMU && option != IGG_OPT_FUSED_HALO)
+  if (option != IGG_OPT_TMA && option != IGG_OPT_F64_EMU && option != IGG_OPT_FUSED_HALO &&
+      option != IGG_OPT_PHASE_TIMES)
     return set_error(IGG_EINVAL, "unknown option %d", option);
   DeviceGuard dg(g->device);
   cudaError_t e1 = cudaStreamSynchronize(g->hi), e2 = cudaStreamSynchronize(g->lo);
   if (e1 != cudaSuccess) return cuda_error(e1, "set_option");
   if (e2 != cudaSuccess) return cuda_error(e2, "set_option");
+  if (option == IGG_OPT_PHASE_TIMES) {  // kernels, tables and graphs are unchanged
+    g->phase_times = value != 0;
+    g->pev_used = 0;
+    return IGG_OK;
+  }
   if (option == IGG_OPT_TMA) g->tma_enabled = value != 0;
   else if (option == IGG_OPT_F64_EMU) g->f64_emu = value != 0 ? 1 : 0;
   else g->fused_halo = value != 0;
@@ -1420,6 +1490,55 @@ int igg_grid_set_option(igg_grid *g, int option, int value) {
   g->split.clear();
   for (auto &kv : g->full) free_tiles(kv.second);
   g->full.clear();
+  return IGG_OK;
+}
+
+int igg_phase_times(igg_grid *g, double ms[3], int *steps) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (!ms || !steps) return set_error(IGG_EINVAL, "ms or steps is NULL");
+  DeviceGuard dg(g->device);
+  ms[0] = ms[1] = ms[2] = 0.0;
+  const int n = g->pev_used / 3;
+  *steps = n;
+  g->pev_used = 0;
+  if (n == 0) return IGG_OK;
+  cudaError_t e = cudaEventSynchronize(g->pev[3 * n - 1]);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    float a = 0.f, b = 0.f;
+    e = cudaEventElapsedTime(&a, g->pev[3 * i], g->pev[3 * i + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, g->pev[3 * i + 1], g->pev[3 * i + 2]);
+    ms[0] += a;
+    ms[1] += b;
+    ms[2] += (double)a + b;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "phase times");
+  return IGG_OK;
+}
+
+int igg_fixup_stats(igg_grid *g, unsigned long long counts[2], int clear) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (!counts) return set_error(IGG_EINVAL, "counts is NULL");
+  DeviceGuard dg(g->device);
+  counts[0] = counts[1] = 0ull;
+  cudaError_t e = cudaDeviceSynchronize();
+  std::vector<FixBuf *> bufs;
+  for (auto &kv : g->full) bufs.push_back(&kv.second.fix);
+  for (auto &kv : g->split) {
+    for (auto &b : kv.second.boundary) bufs.push_back(&b.fix);
+    bufs.push_back(&kv.second.inner.fix);
+  }
+  for (FixBuf *f : bufs) {
+    if (!f->p || e != cudaSuccess) continue;
+    unsigned long long t[2];
+    char *tot = (char *)f->p + tma_fix_bytes(f->cap) - 16;
+    e = cudaMemcpy(t, tot, sizeof t, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && clear) e = cudaMemset(tot, 0, sizeof t);
+    counts[0] += t[0];
+    counts[1] += t[1];
+  }
+  if (e != cudaSuccess) return cuda_error(e, "fix-up stats");
   return IGG_OK;
 }
 

@@ -69,7 +69,6 @@ template <class S>
 __device__ __forceinline__ void lds_vec(const S *p, Vec<S> &o) {
   unpack(*reinterpret_cast<const uint4 *>(p), o);
 }
-
 // A tile set's fix-up buffer (layout in igg_internal.h): the entries, then
 // the entry count and a block counter.
 struct FixEntry {
@@ -80,11 +79,12 @@ struct FixEntry {
 struct FixList {
   FixEntry *e;
   unsigned *count, *done;
+  unsigned long long *totals;  // segments and points fixed up since the buffer was made
 };
 __device__ __forceinline__ FixList fix_list(void *fix, size_t cap) {
   FixEntry *e = reinterpret_cast<FixEntry *>(fix);
   unsigned *c = reinterpret_cast<unsigned *>(e + cap);
-  return {e, c, c + 1};
+  return {e, c, c + 1, reinterpret_cast<unsigned long long *>(c + 2)};
 }
 constexpr int kFixupBlocks = 8 * 152;
 
@@ -143,8 +143,8 @@ __device__ __forceinline__ void compute_vec<double, MODE_F64>(
 
 // Emulated fast path for both points, computed unconditionally (no branch
 // in the common case); ok marks the points whose fast path applies, the
-// others are listed for the fix-up launch (cell(): the shifted-significand
-// form across one power of two, else the FP64 cell).
+// others are listed for the fix-up launch (the aligned path across powers of
+// two or zero, else the FP64 cell).
 template <int NG>
 __device__ __forceinline__ void compute_vec_emu(
     const Vec<double> &c, double left, double right, const Vec<double> &ym, const Vec<double> &yp,
@@ -431,13 +431,14 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 }
 
 // Fix-up of an emulated-cell launch: the points whose fast path the kernel
-// did not take get cell() (the same choice and arithmetic as every kernel:
-// the shifted-significand form where the stencil crosses one power of two,
-// else the FP64 cell). The kernel listed every 32-point row segment with such
-// points (its first point and a bit mask); the fix-up's warps take the
-// entries in turn, lane l updating point p + l when bit l is set, each warp
-// loading its next entry while it works on the current one. The last block
-// to finish resets the list.
+// did not take get what cell() gives them (the same choice and arithmetic
+// as every kernel: the aligned path for stencils across powers of two or
+// zero, else the FP64 cell). The kernel listed every 32-point row segment
+// with such points (its first point and a bit mask); the fix-up's warps take
+// the entries in turn, lane l updating point p + l when bit l is set, each
+// warp loading its next entry while it works on the current one. Each block adds
+// its segments and points to the list's totals; the last block to finish
+// resets the list.
 __global__ void __launch_bounds__(256)
     k_fixup_f64(void *__restrict__ fix, size_t cap, double *__restrict__ T2,
                 const double *__restrict__ T, const double *__restrict__ Ci, int nx, int ny,
@@ -451,20 +452,34 @@ __global__ void __launch_bounds__(256)
   unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   FixEntry en = {};
   if (e < count) en = fl.e[e];
+  unsigned segs = 0u, pts = 0u;
   for (; e < count; e += warps) {
     FixEntry nxt = {};
     if (e + warps < count) nxt = fl.e[e + warps];
+    segs += 1u;
+    pts += __popc(en.bits);
     if (en.bits >> lane & 1u) {
       const long long p = en.p + lane;
       const double tc = __ldg(T + p);
       const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
                             __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-      T2[p] = cell(tc, tn[0], tn[1], tn[2], tn[3], tn[4], tn[5], __ldg(Ci + p), w);
+      T2[p] = cell_emu_not_fast(tc, tn, __ldg(Ci + p), w);
     }
     en = nxt;
   }
+  __shared__ unsigned bsum[2];
+  if (threadIdx.x == 0) bsum[0] = bsum[1] = 0u;
+  __syncthreads();
+  if (lane == 0 && segs) {
+    atomicAdd(&bsum[0], segs);
+    atomicAdd(&bsum[1], pts);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (bsum[0]) {
+      atomicAdd(fl.totals, (unsigned long long)bsum[0]);
+      atomicAdd(fl.totals + 1, (unsigned long long)bsum[1]);
+    }
     __threadfence();
     if (atomicAdd(fl.done, 1u) == gridDim.x - 1) {
       *fl.count = 0u;

@@ -69,12 +69,14 @@ def lib():
     L.igg_reduce.argtypes = [I, P, P, ctypes.c_size_t, I, P, P]
     L.igg_device_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint), I]
     L.igg_grid_set_option.argtypes = [P, I, I]
+    L.igg_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), IP]
+    L.igg_fixup_stats.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong), I]
     for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
                  "igg_grid_shape", "igg_subdomain_info", "igg_update_halo",
                  "igg_update_halo_staggered", "igg_update_halo_fields",
                  "igg_acoustic_step", "igg_gp_step", "igg_step",
                  "igg_step_hidden", "igg_run", "igg_run_host", "igg_reduce", "igg_device_status",
-                 "igg_grid_set_option"):
+                 "igg_grid_set_option", "igg_phase_times", "igg_fixup_stats"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -191,6 +193,7 @@ class Grid:
     OPT_TMA = 1
     OPT_F64_EMU = 2
     OPT_FUSED_HALO = 3
+    OPT_PHASE_TIMES = 4
 
     def set_option(self, option: int, value: int):
         """igg_grid_set_option (OPT_TMA: 1 = TMA kernel for regular boxes)."""
@@ -201,6 +204,21 @@ class Grid:
         st = ctypes.c_uint()
         _check(lib().igg_device_status(self._handle(), ctypes.byref(st), int(clear)))
         return st.value
+
+    def phase_times(self):
+        """igg_phase_times: (stencil-phase ms, rest-of-step ms, total ms,
+        steps) summed over the steps recorded under OPT_PHASE_TIMES."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_int()
+        _check(lib().igg_phase_times(self._handle(), ms, ctypes.byref(n)))
+        return ms[0], ms[1], ms[2], n.value
+
+    def fixup_stats(self, clear: bool = False):
+        """igg_fixup_stats: (row segments, points) left to the emulated FP64
+        cell's fix-up launch so far."""
+        c = (ctypes.c_ulonglong * 2)()
+        _check(lib().igg_fixup_stats(self._handle(), c, int(clear)))
+        return int(c[0]), int(c[1])
 
     def empty(self, dtype=torch.float64, device="cuda"):
         return torch.empty(self.shape, dtype=dtype, device=device)

@@ -8,6 +8,8 @@ Workloads (each the physics of Fig. 1 with seeded, randomised inputs):
   * single 64^3 FP64 grid, Gaussian bump, c0 ~ U[1.5, 2.5], nt = 100;
   * 2x2x2 subdomains of 512x256x256 FP64 (overlap 2, periodic in x),
     hidden communication with widths (16, 2, 2), same physics, nt = 100;
+  * the same decomposed grid with T0 = 8 sine modes of amplitude 0.1 about 0
+    (a field that changes sign);
   * a 1024^3 grid in FP32 / BF16 storage with Ci ~ U[0.4, 0.67] and 8 sine
     modes of amplitude 0.1 on 1.7 (error check at 128^3).
 """
@@ -59,6 +61,15 @@ WORKLOADS = {
     "decomposed_2x2x2_256x128x128": Workload(
         "decomposed_2x2x2_256x128x128", (256, 128, 128), dims=(2, 2, 2), periods=(1, 0, 0),
         widths=(16, 2, 2), seed=1),
+    # the same grid and physics with a sign-changing T0 (the sine modes about
+    # 0): the emulated FP64 cell's worst case (stencils across zero and across
+    # powers of two)
+    "decomposed_2x2x2_512x256x256_signed": Workload(
+        "decomposed_2x2x2_512x256x256_signed", (512, 256, 256), dims=(2, 2, 2), periods=(1, 0, 0),
+        widths=(16, 2, 2), seed=1, t0="sines0"),
+    "decomposed_2x2x2_256x128x128_signed": Workload(
+        "decomposed_2x2x2_256x128x128_signed", (256, 128, 128), dims=(2, 2, 2), periods=(1, 0, 0),
+        widths=(16, 2, 2), seed=1, t0="sines0"),
     "precision_1024": Workload("precision_1024", (1024, 1024, 1024), nt=1000, seed=2, t0="sines",
                                ci="uniform"),
     "precision_128": Workload("precision_128", (128, 128, 128), nt=1000, seed=2, t0="sines",
@@ -72,6 +83,8 @@ def host_fields(w: Workload, grid: Grid, sub: int):
     g = grid.global_indices(sub)
     if w.t0 == "gaussian":
         T = synth.gaussian_bump(*g, ng, l=w.l)
+    elif w.t0 == "sines0":
+        T = synth.sine_modes(w.seed, *g, ng, l=w.l, base=0.0)
     else:
         T = synth.sine_modes(w.seed, *g, ng, l=w.l)
     if w.ci == "c0":

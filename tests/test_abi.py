@@ -77,6 +77,9 @@ def test_null_arguments(L):
     assert L.igg_finalize_global_grid(None) == 0
     assert L.igg_run_host(None, 1, None, None, None, None, None, None, 0, 1.0, 1.0, 1.0, 1.0, 1.0,
                           None) == -1
+    ms, n = (ctypes.c_double * 3)(), ctypes.c_int()
+    assert L.igg_phase_times(None, ms, ctypes.byref(n)) == -1
+    assert L.igg_fixup_stats(None, (ctypes.c_ulonglong * 2)(), 0) == -1
     out = ctypes.c_double()
     assert L.igg_reduce(9, None, None, 0, 0, ctypes.byref(out), None) == -1
     assert L.igg_reduce(0, None, None, 0, 7, ctypes.byref(out), None) == -1

@@ -14,6 +14,12 @@ import torch.multiprocessing as mp
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
 def _worker(rank, ws, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
                       WORLD_SIZE=str(ws))
@@ -86,3 +92,40 @@ def test_median_ci95_order_statistics():
         _, a, b = bench.median_ci95(xs)
         hits += a <= 0.6931471805599453 <= b  # median of Exp(1) = ln 2
     assert 0.93 <= hits / 2000 <= 0.99
+
+
+def test_record_traffic_from_ncu_csv_and_hash_check(tmp_path):
+    """The traffic recorder averages dram read + write over the kernel's
+    launches in an ncu raw CSV (units row honoured), scales it, and the bench
+    drops the figure once the recorded source hash no longer matches."""
+    import json
+    bench = _bench()
+    csv = tmp_path / "raw.csv"
+    csv.write_text(
+        '"ID","Kernel Name","dram__bytes_read.sum","dram__bytes_write.sum"\n'
+        '"","","Mbyte","Kbyte"\n'
+        '"0","void k_stencil_tma<double>(...)","100.5","2,000"\n'
+        '"1","k_fixup_f64(...)","7","7"\n'
+        '"2","void k_stencil_tma<double>(...)","99.5","2,000"\n')
+    out = tmp_path / "traffic.json"
+    rec = bench.record_traffic(str(csv), "k", "k_stencil_tma", 8.0, "test", path=str(out))
+    assert rec["launches"] == 2
+    assert rec["captured_bytes_per_launch"] == int(100e6 + 2e6)
+    assert rec["dram_bytes_per_launch"] == int(8 * (100e6 + 2e6))
+    assert bench.traffic_for("k", path=str(out)) == 8 * (100e6 + 2e6)
+    d = json.loads(out.read_text())
+    d["k"]["source_sha256"] = "0" * 64
+    out.write_text(json.dumps(d))
+    assert bench.traffic_for("k", path=str(out)) is None
+    assert bench.traffic_for("missing", path=str(out)) is None
+
+
+def test_launch_count_of_default_step():
+    bench = _bench()
+
+    class G:
+        dims, periods = (2, 2, 2), (1, 0, 0)
+    assert bench.grid_launches_per_step(G(), "f64", True) == 3
+    assert bench.grid_launches_per_step(G(), "f32", True) == 2
+    G.dims, G.periods = (1, 1, 1), (0, 0, 0)
+    assert bench.grid_launches_per_step(G(), "f64", True) == 2

@@ -180,3 +180,127 @@ def test_split_halves_exact():
         l = float(u2f((lo & 0x7FFFFF) | 0x4B000000)) - 1.5 * 2 ** 23
         assert h * (1 << 23) + l == G and -(2 ** 22) <= l < 2 ** 22
         assert float(f32(h)) == h and float(f32(l)) == l
+
+
+# ---------------------------------------------------------------------------
+# The aligned path: stencils across powers of two or across zero
+# ---------------------------------------------------------------------------
+def aligned_cell(tc, nb, ci, w, ng):
+    """(T2, ok, er, P) of the aligned path: every value on the grid of
+    u = 2^(er-1075) (er the largest exponent field), rounded half up and
+    signed relative to the centre; the fast path's split and sums; two FP64
+    FMAs (C u first, then S u)."""
+    bc = bits(tc)
+    vals = [bc] + [bits(v) for v in nb]
+    er = max(max((b >> 52) & 0x7FF for b in vals), 1)
+
+    def al(b):
+        e = (b >> 52) & 0x7FF
+        m = (b & (2 ** 52 - 1)) | ((e != 0) << 52)
+        d = min(er - max(e, 1), 63)
+        q = (m + (1 << (d - 1))) >> d if d else m
+        return -q if (b ^ bc) >> 63 else q
+
+    I = [al(b) for b in vals[1:]]
+    c2 = 2 * al(bc)
+    D = [I[2 * d] + I[2 * d + 1] - c2 for d in range(3)]
+    ok = 180 <= er <= 2008
+    gh, gl = [], []
+    for grp in groups(ng):
+        G = sum(D[d] for d in grp)
+        h = (G + (1 << 22)) >> 23
+        ok = ok and abs(h) < (1 << 24)
+        gh.append(f32(h))
+        gl.append(f32(u2f((((G + (1 << 22)) & 0x7FFFFF) | 0x4B000000)) - f32(1.5 * 2 ** 23)))
+    wg = [split_w(w[grp[0]]) for grp in groups(ng)]
+    ah = [f32(a * f32(2.0 ** 23)) for a, _ in wg]
+    al_ = [f32(b * f32(2.0 ** 23)) for _, b in wg]
+    bh = [a for a, _ in wg]
+    P = [fma(ah[g], gh[g], f32(0)) for g in range(ng)]
+    Ee = [fma(ah[g], gh[g], -P[g]) for g in range(ng)]
+    R = fma(bh[0], gl[0], f32(0))
+    for g in range(1, ng):
+        R = fma(bh[g], gl[g], R)
+    for g in range(ng):
+        R = fma(al_[g], gh[g], R)
+    if ng == 1:
+        S, C = P[0], f32(Ee[0] + R)
+    elif ng == 2:
+        S, e = two_sum(P[0], P[1])
+        C = f32(f32(Ee[0] + Ee[1]) + f32(e + R))
+    else:
+        s1, e1 = two_sum(P[0], P[1])
+        S, e2 = two_sum(s1, P[2])
+        C = f32(f32(f32(Ee[0] + Ee[1]) + f32(Ee[2] + e1)) + f32(e2 + R))
+    u = Fr(2) ** (er - 1075)
+    sg = -1 if bc >> 63 else 1
+    t1 = float(Fr(tc) + sg * Fr(ci) * Fr(float(C)) * u)
+    t2 = float(Fr(t1) + sg * Fr(ci) * Fr(float(S)) * u)
+    return t2, ok, er, [Fr(float(p)) for p in P]
+
+
+def check_aligned(ng, w, cases, seed=8):
+    rng = np.random.default_rng(seed)
+    worst, nok = 0.0, 0
+    for tc, nb in cases:
+        ci = float(rng.uniform(0.4, 0.67))
+        r, ok, er, P = aligned_cell(tc, nb, ci, w, ng)
+        if not ok:
+            continue
+        nok += 1
+        u = Fr(2) ** (er - 1075)
+        mag = Fr(ci) * sum(abs(p) for p in P) * u
+        # rounding of the values to u, one rounding per FMA (|T2| < 2^(er-1022)),
+        # and 2^-44 of the weighted sum's terms
+        bound = (2 * Fr(ci) * sum(Fr(x) for x in w) + 1) * u + Fr(2) ** -44 * mag
+        worst = max(worst, float(abs(Fr(r) - exact_step(tc, nb, ci, w)) / bound))
+    return worst, nok
+
+
+def smooth_stencils(rng, n, centre, h=1e-3):
+    """Stencils of smooth fields a + b.x + c x^2 around the given centres."""
+    out = []
+    for _ in range(n):
+        t = centre(rng)
+        g = rng.standard_normal(3) * 0.5
+        c = rng.standard_normal(3) * 0.5
+        nb = tuple(float(t + s * g[d] * h + c[d] * h * h) for d in range(3) for s in (-1, 1))
+        out.append((t, nb))
+    return out
+
+
+def test_aligned_cell_within_bound_across_zero_and_powers_of_two():
+    rng = np.random.default_rng(9)
+    w = (0.0412, 0.1653, 0.1653)
+    # across zero: centres within a few h of 0, neighbours of both signs
+    across0 = smooth_stencils(rng, 300, lambda r: float(r.uniform(-3e-3, 3e-3)))
+    # across powers of two: centres at 2^k (1 - small)
+    across2 = smooth_stencils(rng, 300, lambda r: float(2.0 ** r.integers(-3, 4) * (1 + r.uniform(-1e-3, 1e-3))))
+    for cases, ng, wt in ((across0, 2, w), (across2, 2, w), (across0, 1, (0.16,) * 3),
+                          (across2, 3, (0.05, 0.09, 0.013))):
+        worst, nok = check_aligned(ng, wt, cases)
+        assert nok > 250 and worst <= 1.0, (ng, worst, nok)
+
+
+def test_aligned_integers_equal_bit_differences_on_one_binade():
+    """On stencils of one sign and one exponent the aligned integers are the
+    significands themselves: the group sums equal the fast path's bit-pattern
+    differences (negated for negative values)."""
+    rng = np.random.default_rng(10)
+    for sign in (1.0, -1.0):
+        for tc, nb in stencils(rng, 100, 1e-5, sign=sign):
+            bc = bits(tc)
+            if any((bits(v) >> 52) != (bc >> 52) for v in nb):
+                continue
+            D_fast = [bits(nb[2 * d]) + bits(nb[2 * d + 1]) - 2 * bc for d in range(3)]
+            mant = lambda b: (b & (2 ** 52 - 1)) | (1 << 52)  # noqa: E731
+            D_al = [mant(bits(nb[2 * d])) + mant(bits(nb[2 * d + 1])) - 2 * mant(bc) for d in range(3)]
+            assert D_fast == D_al
+
+
+def test_aligned_path_refuses_large_relative_curvature():
+    """A stencil whose group sum reaches 2^47 units of its largest value's ulp
+    (relative second difference near 2^-5) is left to the FP64 cell."""
+    w = (0.03, 0.12, 0.12)
+    assert not aligned_cell(1e-3, (1e-3, 1e-3, 1e-3, 1e-3, -1e-3, 1.3e-3), 0.5, w, 2)[1]
+    assert aligned_cell(1e-3, (1.001e-3, 0.999e-3, 1e-3, 1e-3, 0.998e-3, 1.002e-3), 0.5, w, 2)[1]

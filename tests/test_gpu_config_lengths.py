@@ -1,0 +1,213 @@
+"""GPU parity at the workloads' own sizes and run lengths, through the C ABI:
+the single-xPU step plus the three calls give the global-grid solution over a
+whole run (Sec. Approach; Fig. 1's time loop), not just over a few steps.
+
+* the 2x2x2 x 512x256x256 FP64 workload, hidden communication (16, 2, 2),
+  nt = 100, every point against the oracle's decomposed run within 1e-12 of
+  max|T|;
+* the same grid with a sign-changing T0 (sine modes about 0, the emulated
+  FP64 cell's worst case), full size nt = 4 and 256x128x128 nt = 40;
+* 128^3 with T0 = 1.7 + sine modes, Ci ~ U[0.4, 0.67], nt = 1000: FP32 within
+  its stated bound; BF16 storage nearly freezes (most increments fall below
+  half a BF16 ulp), so its error is close to the change of the FP64 field
+  over the run (both recorded figures asserted);
+* 32^3, nt = 200, one checkpoint every 16 steps: the checkpointed gradient
+  against the oracle's uncheckpointed adjoint within 1e-10, and
+  torch.autograd against central differences within 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+igg = pytest.importorskip("paper_2211_15716_gb300")
+from paper_2211_15716_gb300 import autograd as ag  # noqa: E402
+from paper_2211_15716_gb300 import workloads as wl  # noqa: E402
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2211_15716_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    oracle.build()
+    oracle.set_threads(0)
+
+
+def rel_err(gpu, ref):
+    return float(np.abs(gpu - ref).max() / np.abs(ref).max())
+
+
+def _decomposed_run(name, nt):
+    w = wl.WORKLOADS[name]
+    with igg.Grid(w.n, dims=w.dims, overlap=w.overlap, periods=w.periods) as g:
+        T, T2, Ci = wl.make_fields(w, g)
+        dx, dy, dz, dt = wl.setup(w, g, Ci)
+        T0 = T.cpu().numpy()
+        Cih = Ci.cpu().numpy()
+        g.fixup_stats(clear=True)
+        res = g.run(nt, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)
+        gpu = res.cpu().numpy()
+        segs, pts = g.fixup_stats(clear=True)
+        assert g.device_status() == 0
+        del T, T2, Ci, res
+    ref = oracle.run_decomposed(T0, Cih, nt, w.lam, dt, dx, dy, dz, w.dims, w.periods, w.overlap,
+                                widths=w.widths)
+    inner = np.prod([k - 2 for k in w.n]) * np.prod(w.dims)
+    return gpu, ref, pts / (nt * inner)
+
+
+def test_bench_workload_nt100_matches_oracle():
+    gpu, ref, share = _decomposed_run("decomposed_2x2x2_512x256x256", 100)
+    assert rel_err(gpu, ref) <= FP64_TOL
+    assert share < 0.01  # the Gaussian bump crosses 2.0 on one shell only
+
+
+@pytest.mark.parametrize("name,nt", [("decomposed_2x2x2_512x256x256_signed", 4),
+                                     ("decomposed_2x2x2_256x128x128_signed", 40)])
+def test_sign_changing_field_matches_oracle(name, nt):
+    gpu, ref, share = _decomposed_run(name, nt)
+    assert rel_err(gpu, ref) <= FP64_TOL
+    # about a third of the stencils cross a power of two or zero: the fix-up
+    # launch gives them the aligned path (or the FP64 cell)
+    assert share > 0.1
+
+
+def _precision_case():
+    m = 128
+    w = wl.WORKLOADS["precision_128"]
+    g = igg.Grid((m, m, m))
+    T0, Ci = wl.host_fields(w, g, 0)
+    T0, Ci = np.ascontiguousarray(T0), np.ascontiguousarray(Ci)
+    dd = [oracle.spacing(1.0, m)] * 3
+    dt = oracle.cfl_dt(*dd, 1.0, Ci.max())
+    return w, g, T0, Ci, dd, dt
+
+
+def test_precision_128cube_nt1000_fp32_bound_and_bf16_freeze():
+    w, g, T0, Ci, dd, dt = _precision_case()
+    nt = 1000
+    try:
+        ref = oracle.run(T0, Ci, nt, 1.0, dt, *dd)
+        scale = np.abs(ref).max()
+        out = {}
+        for name, tdt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+            T, T2, Cd = wl.make_fields(w, g, tdt)
+            start = T.double().cpu().numpy()[0]
+            out[name] = (g.run(nt, T, T2, Cd, 1.0, dt, *dd).double().cpu().numpy()[0], start)
+    finally:
+        g.finalize()
+    # FP32: input rounding plus about two FP32 ulps per step, non-expansive
+    err32 = np.abs(out["f32"][0] - ref).max()
+    assert err32 <= (1 + nt) * 2 * 2.0 ** -24 * scale, err32
+    assert err32 / scale < 1e-5
+    # BF16 storage: most increments (~1e-5 of T) are below half a BF16 ulp
+    # (2^-8 of T), so the field barely moves from its initial BF16 values and
+    # its error is close to the change of the FP64 field over the run (the
+    # recorded figures: 0.24 and 0.26 of max|T|)
+    bf, bf0 = out["bf16"]
+    change = np.abs(ref - T0).max() / scale
+    err16 = np.abs(bf - ref).max() / scale
+    moved = np.abs(bf - bf0).max() / scale
+    assert change == pytest.approx(0.26, abs=0.02), change
+    assert err16 == pytest.approx(0.24, abs=0.02), err16
+    assert moved < 0.5 * change, moved
+
+
+def _adjoint_case(n):
+    g1 = [np.arange(k) for k in n]
+    Ci_star = np.ascontiguousarray(synth.ci_smooth(4, *g1, n))
+    Ci = np.full(Ci_star.shape, 0.53)
+    T0 = np.ascontiguousarray(np.broadcast_to(synth.gaussian_bump(*g1, n, sigma=0.15), Ci.shape))
+    dd = [oracle.spacing(1.0, k) for k in n]
+    dt = oracle.cfl_dt(*dd, 1.0, max(Ci.max(), Ci_star.max()))
+    return T0, Ci, Ci_star, dd, dt
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda().reshape(1, *a.shape)
+
+
+def test_adjoint_32cube_nt200_checkpoint16_matches_oracle():
+    n, nt, every = (32, 32, 32), 200, 16
+    T0, Ci, Ci_star, dd, dt = _adjoint_case(n)
+    T_obs = oracle.forward_states(T0, Ci_star, nt, 1.0, dt, *dd)[-1]
+    T_obs = T_obs + 1e-3 * np.random.default_rng(5).standard_normal(T_obs.shape)
+    J, gT0, gCi = oracle.gradient(T0, Ci, T_obs, nt, 1.0, dt, *dd)
+    with igg.Grid(n) as g:
+        T_nt, ckpt = ag.forward_checkpointed(g, nt, every, _dev(T0), _dev(Ci), 1.0, dt, *dd)
+        gT, gC = ag.adjoint_checkpointed(g, nt, every, ckpt, _dev(Ci), ag.residual(T_nt, _dev(T_obs)),
+                                         1.0, dt, *dd)
+        torch.cuda.synchronize()
+        gT, gC = gT.cpu().numpy()[0], gC.cpu().numpy()[0]
+    assert np.linalg.norm(gT - gT0) <= 1e-10 * np.linalg.norm(gT0)
+    assert np.linalg.norm(gC - gCi) <= 1e-10 * np.linalg.norm(gCi)
+
+
+def test_autograd_32cube_nt200_checkpoint16_finite_differences():
+    n, nt, every = (32, 32, 32), 200, 16
+    T0, Ci, Ci_star, dd, dt = _adjoint_case(n)
+    with igg.Grid(n) as g:
+        T_obs = ag.solve(_dev(T0), _dev(Ci_star), g, nt, 1.0, dt, *dd, every=every).detach()
+        rng = np.random.default_rng(6)
+        T_obs = T_obs + 1e-3 * torch.from_numpy(rng.standard_normal(T_obs.shape)).cuda()
+        C = _dev(Ci).requires_grad_(True)
+        T = _dev(T0).requires_grad_(True)
+
+        def J(Tin, Cin):
+            return 0.5 * ((ag.solve(Tin, Cin, g, nt, 1.0, dt, *dd, every=every) - T_obs) ** 2).sum()
+
+        J(T, C).backward()
+        with torch.no_grad():
+            for which in ("Ci", "T0"):
+                v = torch.from_numpy(rng.standard_normal(C.shape)).cuda()
+                base = C if which == "Ci" else T
+                h = 1e-6 * base.norm() / v.norm()
+                if which == "Ci":
+                    fd = (J(T, C + h * v) - J(T, C - h * v)) / (2 * h)
+                    ad = (C.grad * v).sum()
+                else:
+                    fd = (J(T + h * v, C) - J(T - h * v, C)) / (2 * h)
+                    ad = (T.grad * v).sum()
+                assert abs(float(fd - ad)) <= 1e-6 * abs(float(ad)), (which, float(fd), float(ad))
+
+
+def test_phase_times_and_fixup_stats():
+    """Phase events are recorded for eagerly queued steps only, per phase;
+    the fix-up counters see points on a field that crosses zero and none on
+    FP32 fields."""
+    w = wl.WORKLOADS["decomposed_2x2x2_256x128x128_signed"]
+    with igg.Grid(w.n, dims=w.dims, overlap=w.overlap, periods=w.periods) as g:
+        T, T2, Ci = wl.make_fields(w, g)
+        dx, dy, dz, dt = wl.setup(w, g, Ci)
+        g.set_option(g.OPT_PHASE_TIMES, 1)
+        assert g.phase_times()[3] == 0
+        g.run(4, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)  # graph: not timed
+        torch.cuda.synchronize()
+        assert g.phase_times()[3] == 0
+        g.run(3, T, T2, Ci, w.lam, dt, dx, dy, dz, widths=w.widths)  # one eager step
+        for _ in range(2):
+            g.step_hidden(w.widths, T2, T, Ci, w.lam, dt, dx, dy, dz)
+            g.step(T, T2, Ci, w.lam, dt, dx, dy, dz)
+        a, b, tot, n = g.phase_times()
+        assert n == 5 and a > 0 and b > 0 and tot == pytest.approx(a + b)
+        assert g.phase_times()[3] == 0
+        g.set_option(g.OPT_PHASE_TIMES, 0)
+        g.step(T2, T, Ci, w.lam, dt, dx, dy, dz)
+        assert g.phase_times()[3] == 0
+        g.fixup_stats(clear=True)
+        g.step(T2, T, Ci, w.lam, dt, dx, dy, dz)
+        segs, pts = g.fixup_stats()
+        assert 0 < pts <= 32 * segs and segs > 0
+        assert g.fixup_stats(clear=True) == (segs, pts)
+        assert g.fixup_stats() == (0, 0)
+        T32, T232, C32 = wl.make_fields(w, g, torch.float32)
+        g.run(2, T32, T232, C32, w.lam, dt, dx, dy, dz, widths=w.widths)
+        assert g.fixup_stats() == (0, 0)
