@@ -40,6 +40,8 @@ namespace {
 
 // exponent half-widths of the pair path's input ranges
 constexpr unsigned kPairLamE = 40, kPairCiE = 20;
+static_assert(kPairLamE <= kPairMaxRadius && kPairCiE <= kPairMaxRadius,
+              "pair_ok radii must stay inside pair_split's range");
 
 // lam as a pair, NaN in h when lam lies outside the pair range (the
 // point's lam_out then takes the FP64 sum)

@@ -43,6 +43,8 @@ namespace {
 // weights zero or in [2^-18, 2^18]: no partial product or error term leaves
 // the normal FP32 range
 constexpr unsigned kGpWE = 40, kGpQE = 36;
+static_assert(kGpWE <= kPairMaxRadius && kGpQE <= kPairMaxRadius,
+              "pair_ok radii must stay inside pair_split's range");
 
 // weights as pairs, the sign of the half step applied (x, y, z, centre);
 // dt and g as pairs

@@ -18,6 +18,8 @@ struct FF {
 };
 
 // True when x is zero or its exponent field lies in [1023 - r, 1023 + r].
+// Radii of at most 127 keep that inside pair_split's range [949, 1150].
+constexpr unsigned kPairMaxRadius = 127;
 __device__ __forceinline__ bool pair_ok(double x, unsigned r) {
   const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
   const unsigned E = (hw >> 20) & 0x7FFu;
@@ -25,7 +27,8 @@ __device__ __forceinline__ bool pair_ok(double x, unsigned r) {
 }
 
 // x = h + l by bit moves; meaningful for zero and exponent fields in
-// [949, 1151] (callers check pair_ok), any input runs without faults.
+// [949, 1150] (at 1151 the head's FP32 exponent field would be 255; callers
+// check pair_ok with radii of at most 127), any input runs without faults.
 __device__ __forceinline__ FF pair_split(double x) {
   const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
   const unsigned s = hw & 0x80000000u;

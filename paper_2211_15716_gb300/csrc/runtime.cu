@@ -1418,9 +1418,15 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
   ci_pairs.s = s;
   if (dt == IGG_F64 && g->tma_enabled &&
       adjoint_tma_applies(dt, g->n[0], work, lam_nt, ckpt, Ci, gCi)) {
-    cudaError_t ea = cudaMallocAsync(&ci_pairs.p, (size_t)g->nloc * 8, s);
-    if (ea == cudaSuccess) ea = launch_pair_ci(Ci, ci_pairs.p, g->nloc, s);
-    if (ea != cudaSuccess) return cuda_error(ea, "Ci pairs");
+    // without room for the pairs the adjoint steps take the kernel that
+    // reads Ci itself (the same bits): a failed allocation is not an error
+    if (cudaMallocAsync(&ci_pairs.p, (size_t)g->nloc * 8, s) != cudaSuccess) {
+      ci_pairs.p = nullptr;
+      (void)cudaGetLastError();
+    } else {
+      cudaError_t ea = launch_pair_ci(Ci, ci_pairs.p, g->nloc, s);
+      if (ea != cudaSuccess) return cuda_error(ea, "Ci pairs");
+    }
   }
   cudaError_t e = cudaMemcpyAsync(LA, lam_nt, bytes, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(gCi, 0, (size_t)g->nloc * sizeof(double), s);

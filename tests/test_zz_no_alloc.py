@@ -2,8 +2,7 @@
 called through the C ABI and checked against igg_reduce on two calls in a
 row. It serves callers that cannot allocate device memory while they reduce
 (a fixed device-memory budget, an allocator that owns all memory, capture
-regions that forbid allocation calls). This file is collected last so that a
-run stopping at the first failure has run every other test before it."""
+regions that forbid allocation calls)."""
 import ctypes
 
 import numpy as np
@@ -73,3 +72,36 @@ def test_noalloc_rejects_too_large(L):
                               ctypes.c_void_p(out.data_ptr()), None)
     assert rc == -1
     assert "exceeds the maximum" in L.igg_last_error().decode()
+
+
+def _call(L, fn, op, a, b, n, code):
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    pa = ctypes.c_void_p(a.data_ptr()) if a is not None else None
+    pb = ctypes.c_void_p(b.data_ptr()) if b is not None else None
+    rc = getattr(L, fn)(op, pa, pb, n, code, ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == 0, L.igg_last_error().decode()
+    torch.cuda.synchronize()
+    return out.item()
+
+
+def test_noalloc_empty_input_gives_identity(L):
+    """n == 0 (no input pointers needed): SUM gives 0 and MAX gives -inf,
+    the same as igg_reduce."""
+    from paper_2211_15716_gb300 import igg
+    L.igg_reduce.argtypes = L.igg_reduce_noalloc.argtypes
+    for fn in ("igg_reduce_noalloc", "igg_reduce"):
+        assert _call(L, fn, 1, None, None, 0, 0) == 0.0
+        assert _call(L, fn, 0, None, None, 0, 0) == float("-inf")
+    assert igg.reduce(1, torch.empty(0, dtype=torch.float64, device="cuda")).item() == 0.0
+
+
+def test_noalloc_sum_and_max_without_b(L):
+    """SUM and MAX read only a: b may be NULL, with the results of igg_reduce."""
+    from paper_2211_15716_gb300 import igg
+    rng = np.random.default_rng(6)
+    a = torch.from_numpy(rng.uniform(-2.0, 3.0, 2 * 65536 + 7)).cuda()
+    assert _call(L, "igg_reduce_noalloc", 0, a, None, a.numel(), 0) == igg.reduce(0, a).item()
+    assert _call(L, "igg_reduce_noalloc", 1, a, None, a.numel(), 0) == pytest.approx(
+        igg.reduce(1, a).item(), rel=1e-13)
+    assert _call(L, "igg_reduce_noalloc", 1, a, None, a.numel(), 0) == pytest.approx(
+        float(a.sum()), rel=1e-12)
