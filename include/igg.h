@@ -164,6 +164,7 @@ int igg_update_halo_fields(igg_grid *grid, void *const fields[], const int *size
  * Synchronises the device; clear != 0 resets the word to 0. */
 #define IGG_DEV_ERR_TIMEOUT 1u
 #define IGG_DEV_ERR_DRAIN 2u
+#define IGG_DEV_ERR_BOUNDS 4u
 int igg_device_status(igg_grid *grid, unsigned *status, int clear);
 
 /* Self-test of that failure detection, without a GPU fault: on the current
@@ -224,6 +225,20 @@ int igg_grid_set_option(igg_grid *grid, int option, int value);
  * recorded step; the record is then emptied. No counterpart in the paper
  * (which times whole steps): a measurement aid of the library. */
 int igg_phase_times(igg_grid *grid, double ms[3], int *steps);
+
+/* Bounds-checked build. The library compiled with -DIGG_BOUNDS_CHECK (built
+ * beside the release library as libigg_checked.so, chosen by the Python
+ * binding when the environment has IGG_BOUNDS_CHECK=1) tests every global
+ * index of the default step's kernels (the TMA stencil's stores, the fix-up
+ * launch, the one-launch halo update) against its field's extent before the
+ * access; a failing test skips the access (no trap) and sets a device flag.
+ * igg_bounds_checked: 1 in that build, 0 in the release build.
+ * igg_bounds_status: *status = IGG_DEV_ERR_BOUNDS when any test failed since
+ * the last clear (always 0 in the release build); synchronises the device;
+ * clear != 0 resets the flags. Not in the paper: a debugging aid standing in
+ * for a memory checker. */
+int igg_bounds_checked(void);
+int igg_bounds_status(unsigned *status, int clear);
 
 /* Points the emulated FP64 cell left to its fix-up launch: counts[0] = the
  * 32-point row segments listed, counts[1] = the points in them, summed over
@@ -404,7 +419,13 @@ int igg_batch_run(igg_batch *batch, int nt, void *T, void *T2, const void *Ci,
  * x {resident, half of resident} CTAs per SM) for `reps` steps T -> T2 on the
  * caller's fields, on `stream`, keeps the fastest and returns it in
  * best_cfg[3] with its time per step in *best_ms. Writes T2's inner points
- * and synchronises `stream`. */
+ * and synchronises `stream`. reps = 0 times 3 steps.
+ * The choice is cached per (GPU name, dtype, problem sizes): in the process,
+ * and in the file named by the environment variable IGG_AUTOTUNE_CACHE when
+ * it is set (lines appended, read once per process). A call whose key is
+ * cached applies the cached tiling without timing anything (T2 untouched;
+ * *best_ms = the cached time); reps < 0 ignores the cache, times 3 steps and
+ * stores the new choice. */
 int igg_batch_autotune(igg_batch *batch, void *T2, const void *T,
                        const void *Ci, int reps, void *stream, int best_cfg[3],
                        float *best_ms);

@@ -8,7 +8,7 @@ ctypes binding. The library is loaded on first use, never replaced by a CPU
 path.
 """
 from .igg import (BF16, F32, F64, Batch, RED_MAX, RED_SUM, RED_SUM_DIV, RED_SUM_SQDIFF, Grid,
-                  IggError, dtype_code, lib, library_path, reduce)
+                  IggError, bounds_status, dtype_code, lib, library_path, reduce)
 
-__all__ = ["Grid", "Batch", "IggError", "reduce", "lib", "library_path", "dtype_code", "F64", "F32", "BF16",
-           "RED_MAX", "RED_SUM", "RED_SUM_DIV", "RED_SUM_SQDIFF"]
+__all__ = ["Grid", "Batch", "IggError", "reduce", "lib", "library_path", "dtype_code", "bounds_status",
+           "F64", "F32", "BF16", "RED_MAX", "RED_SUM", "RED_SUM_DIV", "RED_SUM_SQDIFF"]

@@ -16,10 +16,20 @@
 // 16-byte vector kernel, one CTA per tile of rows;
 // variants 0-2 the persistent scalar kernel with 32x8, 32x4 or 64x4 column
 // tiles.
+//
+// Autotune cache: the tuned tiling is kept per (GPU name, dtype, problem
+// sizes), in the process and, when the environment variable
+// IGG_AUTOTUNE_CACHE names a file, in that file (one line per key:
+// "<key> <variant> <zb> <ctas_per_sm> <ms>"), so that a later batch of the
+// same shapes, in this process or another, skips the timing.
 #include <algorithm>
 #include <array>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <string>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -37,6 +47,78 @@ constexpr int kBatchTma = kBatchVector + 1;
 
 // CTAs per SM of each persistent variant for this dtype (occupancy query).
 int max_ctas_per_sm(igg_dtype dt, int variant);
+
+struct TunedCfg {
+  int cfg[3];
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TunedCfg> g_tune;  // the process's cache
+bool g_tune_file_read = false;
+
+const char *tune_file() {
+  const char *p = std::getenv("IGG_AUTOTUNE_CACHE");
+  return p && *p ? p : nullptr;
+}
+
+// FNV-1a over the problem sizes
+unsigned long long sizes_hash(const std::vector<std::array<int, 3>> &sizes) {
+  unsigned long long h = 1469598103934665603ull;
+  for (const auto &s : sizes)
+    for (int v : s)
+      for (int k = 0; k < 4; ++k) {
+        h ^= (unsigned long long)((unsigned)v >> (8 * k) & 0xFFu);
+        h *= 1099511628211ull;
+      }
+  return h;
+}
+
+// key: GPU name (spaces as '_'), dtype, problem count, hash of the sizes
+std::string tune_key(int device, igg_dtype dt, const std::vector<std::array<int, 3>> &sizes) {
+  cudaDeviceProp prop;
+  std::string name = cudaGetDeviceProperties(&prop, device) == cudaSuccess ? prop.name : "unknown";
+  for (char &c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  char buf[96];
+  snprintf(buf, sizeof buf, "|dt%d|n%zu|%016llx", (int)dt, sizes.size(), sizes_hash(sizes));
+  return name + buf;
+}
+
+// the file's entries into the process cache, once (caller holds the lock)
+void read_tune_file() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char *path = tune_file();
+  if (!path) return;
+  FILE *f = std::fopen(path, "r");
+  if (!f) return;
+  char key[256];
+  TunedCfg t;
+  while (std::fscanf(f, "%255s %d %d %d %f", key, &t.cfg[0], &t.cfg[1], &t.cfg[2], &t.ms) == 5)
+    g_tune[key] = t;
+  std::fclose(f);
+}
+
+bool tune_lookup(const std::string &key, TunedCfg *out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  read_tune_file();
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_store(const std::string &key, const TunedCfg &t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  read_tune_file();
+  g_tune[key] = t;
+  if (const char *path = tune_file()) {
+    if (FILE *f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), t.cfg[0], t.cfg[1], t.cfg[2], t.ms);
+      std::fclose(f);
+    }
+  }
+}
 
 }  // namespace
 
@@ -443,8 +525,19 @@ int igg_batch_autotune(igg_batch *b, void *T2, const void *T, const void *Ci, in
   clear_error();
   if (!b) return set_error(IGG_EINVAL, "batch is NULL");
   if (int rc = check_fields(b, T2, T, Ci)) return rc;
-  if (reps <= 0) reps = 3;
   DevGuard g(b->device);
+  const std::string key = tune_key(b->device, b->dtype, b->sizes);
+  TunedCfg hit;
+  if (reps >= 0 && tune_lookup(key, &hit)) {
+    b->variant = hit.cfg[0];
+    b->zb = hit.cfg[1];
+    b->ctas_per_sm = hit.cfg[2];
+    if (int rc = build_tiles(b)) return rc;
+    if (best_cfg) std::memcpy(best_cfg, hit.cfg, sizeof hit.cfg);
+    if (best_ms) *best_ms = hit.ms;
+    return IGG_OK;
+  }
+  if (reps <= 0) reps = 3;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
@@ -501,6 +594,7 @@ int igg_batch_autotune(igg_batch *b, void *T2, const void *T, const void *Ci, in
     best_cfg[2] = bc;
   }
   if (best_ms) *best_ms = best;
+  tune_store(key, TunedCfg{{bv, bz, bc}, best});
   return IGG_OK;
 }
 

@@ -112,9 +112,13 @@ __global__ void __launch_bounds__(256) k_halo_gather(E *__restrict__ f, const Ha
     bool moved = false;
     gather_step(h, 2, s, cz, moved);
     gather_step(h, 1, s, cy, moved);
-    E *dst = f + (long long)s0 * h.nloc + sy * y + sz * z;
-    const E *src = f + (long long)s * h.nloc + sy * cy + sz * cz;
-    if (moved) {
+    const long long di = (long long)s0 * h.nloc + sy * y + sz * z;
+    const long long si = (long long)s * h.nloc + sy * cy + sz * cz;
+    E *dst = f + di;
+    const E *src = f + si;
+    const long long total = h.nloc * h.nsub;
+    if (moved && in_bounds(di, total) && in_bounds(di + nx - 1, total) && in_bounds(si, total) &&
+        in_bounds(si + nx - 1, total)) {
       if (VEC) {
         const int nv = nx * (int)sizeof(E) / 16;
         for (int i = threadIdx.x; i < nv; i += blockDim.x)
@@ -129,7 +133,8 @@ __global__ void __launch_bounds__(256) k_halo_gather(E *__restrict__ f, const Ha
       int ss = s, cx = x;
       bool mx = false;
       gather_step(h, 0, ss, cx, mx);
-      if (mx) dst[x] = f[(long long)ss * h.nloc + cx + sy * cy + sz * cz];
+      const long long xi = (long long)ss * h.nloc + cx + sy * cy + sz * cz;
+      if (mx && in_bounds(di + x, total) && in_bounds(xi, total)) dst[x] = f[xi];
     }
   } else {
     // an x face column: x = 0 or nx - 1, z inner, y = 1 .. ny - 2
@@ -139,9 +144,13 @@ __global__ void __launch_bounds__(256) k_halo_gather(E *__restrict__ f, const Ha
     bool moved = false;
     gather_step(h, 0, s, cx, moved);
     if (!moved) return;
-    E *dst = f + (long long)s0 * h.nloc + x + sz * z;
-    const E *src = f + (long long)s * h.nloc + cx + sz * z;
-    for (int y = 1 + threadIdx.x; y <= ny - 2; y += blockDim.x) dst[sy * y] = src[sy * y];
+    const long long di = (long long)s0 * h.nloc + x + sz * z;
+    const long long si = (long long)s * h.nloc + cx + sz * z;
+    const long long total = h.nloc * h.nsub;
+    E *dst = f + di;
+    const E *src = f + si;
+    for (int y = 1 + threadIdx.x; y <= ny - 2; y += blockDim.x)
+      if (in_bounds(di + sy * y, total) && in_bounds(si + sy * y, total)) dst[sy * y] = src[sy * y];
   }
 }
 
@@ -217,5 +226,7 @@ cudaError_t launch_halo_gather(size_t elem_size, void *field, const HaloGather &
   }
   return cudaGetLastError();
 }
+
+cudaError_t halo_bounds_flag(unsigned *out, bool clear) { return read_bounds_flag(out, clear); }
 
 }  // namespace igg

@@ -44,6 +44,9 @@ struct Coef {
   // in T (boundary cells keep them; halo cells are overwritten by the halo
   // update), so that every row store covers whole 32-byte sectors
   int ends;
+  // points of the field the launch writes (all subdomains), set by the TMA
+  // launcher; the bounds-checked build tests global indices against it
+  long long npts;
 };
 
 Coef make_coef(double lam, double dt, double dx, double dy, double dz);
@@ -210,6 +213,37 @@ cudaError_t launch_gp_half(igg_dtype dt, int which, int nsub, int nx, int ny, in
 // (fields of different sizes: each job its own plane table and geometry as
 // for launch_halo; vec is set by the launch).
 constexpr int kMaxHaloJobs = 16;
+
+// Bounds-checked build (compiled with -DIGG_BOUNDS_CHECK into a library of its
+// own): the kernels of the default step (the TMA stencil's stores, the fix-up
+// launch, the one-launch halo update) test each global index against the
+// extent of its field before the access. A failing test skips the access
+// and sets the translation unit's flag, which igg_bounds_status reads: the
+// kernel does not trap and the context stays usable. In the release build
+// the tests compile to nothing.
+#ifdef IGG_BOUNDS_CHECK
+static __device__ unsigned g_bounds_flag;
+__device__ __forceinline__ bool in_bounds(long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&g_bounds_flag, 1u);
+  return false;
+}
+static inline cudaError_t read_bounds_flag(unsigned *out, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_bounds_flag, sizeof(unsigned));
+  const unsigned zero = 0u;
+  if (e == cudaSuccess && clear) e = cudaMemcpyToSymbol(g_bounds_flag, &zero, sizeof zero);
+  return e;
+}
+#else
+__device__ __forceinline__ bool in_bounds(long long, long long) { return true; }
+static inline cudaError_t read_bounds_flag(unsigned *out, bool) {
+  *out = 0u;
+  return cudaSuccess;
+}
+#endif
+// the flags of the translation units with checked kernels
+cudaError_t tma_bounds_flag(unsigned *out, bool clear);
+cudaError_t halo_bounds_flag(unsigned *out, bool clear);
 struct HaloJob {
   const PlaneCopy *copies;
   void *field;

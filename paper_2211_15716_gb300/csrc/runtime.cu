@@ -55,6 +55,7 @@ Coef make_coef(double lam, double dt, double dx, double dy, double dz) {
   c.wc = -2.0 * (c.wx + c.wy + c.wz);
   c.f64_emu = 0;
   c.ends = 0;
+  c.npts = 0;
   return c;
 }
 
@@ -1519,6 +1520,25 @@ int igg_phase_times(igg_grid *g, double ms[3], int *steps) {
     ms[2] += (double)a + b;
   }
   if (e != cudaSuccess) return cuda_error(e, "phase times");
+  return IGG_OK;
+}
+
+int igg_bounds_checked(void) {
+#ifdef IGG_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int igg_bounds_status(unsigned *status, int clear) {
+  clear_error();
+  if (!status) return set_error(IGG_EINVAL, "status is NULL");
+  unsigned a = 0u, b = 0u;
+  cudaError_t e = tma_bounds_flag(&a, clear != 0);
+  if (e == cudaSuccess) e = halo_bounds_flag(&b, clear != 0);
+  if (e != cudaSuccess) return cuda_error(e, "bounds status");
+  *status = (a | b) ? IGG_DEV_ERR_BOUNDS : 0u;
   return IGG_OK;
 }
 

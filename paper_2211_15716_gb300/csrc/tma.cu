@@ -372,8 +372,11 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
         if (comp[j]) {
           // every point of the box is stored; points the fast path did not
           // take are stored again by the fix-up launch
-          S *dst = T2 + t.base + xs + srow * (t.r0 + r) + smarch * m;
-          if (full_st) {
+          const long long di = t.base + xs + srow * (t.r0 + r) + smarch * m;
+          S *dst = T2 + di;
+          if (!BATCH && !(in_bounds(di, c0.npts) && in_bounds(di + V - 1, c0.npts))) {
+            // bounds-checked build only: the store is skipped
+          } else if (full_st) {
             if (endm) {
 #pragma unroll
               for (int i = 0; i < V; ++i)
@@ -458,7 +461,8 @@ __global__ void __launch_bounds__(256)
     if (e + warps < count) nxt = fl.e[e + warps];
     segs += 1u;
     pts += __popc(en.bits);
-    if (en.bits >> lane & 1u) {
+    if (en.bits >> lane & 1u && in_bounds(en.p + lane - sz, c0.npts) &&
+        in_bounds(en.p + lane + sz, c0.npts)) {
       const long long p = en.p + lane;
       const double tc = __ldg(T + p);
       const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
@@ -510,13 +514,15 @@ cudaError_t launch_t(const TmaTile *tiles, int ntiles, void *T2, const void *T, 
                        : encode<S>(&mT, T, nx, ny, nzt, Sh::BW, Sh::BH, 1) &&
                              encode<S>(&mC, Ci, nx, ny, nzt, Sh::W, Sh::H, 1);
   if (!ok) return cudaErrorInvalidValue;
+  Coef cc = c;
+  cc.npts = (long long)nx * ny * nzt;
   k_stencil_tma<S, Shp::LPR, Shp::H, SWAP, MODE>
-      <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, c,
+      <<<ntiles, 32 * (Sh::CONSUMERS + 1), Sh::SMEM, s>>>(mT, mC, tiles, (S *)T2, nx, ny, cc,
                                                           dev_err, fix.p, fix.cap);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && is_emu(MODE)) {
     k_fixup_f64<<<kFixupBlocks, 256, 0, s>>>(fix.p, fix.cap, (double *)T2, (const double *)T,
-                                            (const double *)Ci, nx, ny, c);
+                                            (const double *)Ci, nx, ny, cc);
     e = cudaGetLastError();
   }
   return e;
@@ -733,5 +739,7 @@ cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, 
   }
   return cudaErrorInvalidValue;
 }
+
+cudaError_t tma_bounds_flag(unsigned *out, bool clear) { return read_bounds_flag(out, clear); }
 
 }  // namespace igg

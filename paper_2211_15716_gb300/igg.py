@@ -35,7 +35,9 @@ class IggError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library the binding loads: the bounds-checked build when the
+    environment has IGG_BOUNDS_CHECK=1, else the release build."""
+    return _build.LIB_CHECKED if os.environ.get("IGG_BOUNDS_CHECK") == "1" else _build.LIB
 
 
 def lib():
@@ -43,7 +45,7 @@ def lib():
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = library_path()
     if not os.path.exists(path):
         raise ImportError(f"{path} is not built: run paper_2211_15716_gb300.build.build() "
                           "(the library has no CPU fallback)")
@@ -71,12 +73,15 @@ def lib():
     L.igg_grid_set_option.argtypes = [P, I, I]
     L.igg_phase_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), IP]
     L.igg_fixup_stats.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong), I]
+    L.igg_bounds_checked.argtypes = []
+    L.igg_bounds_status.argtypes = [ctypes.POINTER(ctypes.c_uint), I]
     for name in ("igg_init_global_grid", "igg_finalize_global_grid", "igg_global_size",
                  "igg_grid_shape", "igg_subdomain_info", "igg_update_halo",
                  "igg_update_halo_staggered", "igg_update_halo_fields",
                  "igg_acoustic_step", "igg_gp_step", "igg_step",
                  "igg_step_hidden", "igg_run", "igg_run_host", "igg_reduce", "igg_device_status",
-                 "igg_grid_set_option", "igg_phase_times", "igg_fixup_stats"):
+                 "igg_grid_set_option", "igg_phase_times", "igg_fixup_stats",
+                 "igg_bounds_checked", "igg_bounds_status"):
         getattr(L, name).restype = I
     _lib = L
     return L
@@ -330,6 +335,14 @@ class Grid:
                                   _stream(stream)))
 
 
+def bounds_status(clear: bool = False) -> int:
+    """igg_bounds_status: DEV_ERR_BOUNDS when a bounds-checked kernel skipped
+    an out-of-range access (always 0 in the release build)."""
+    st = ctypes.c_uint(0)
+    _check(lib().igg_bounds_status(ctypes.byref(st), int(clear)))
+    return int(st.value)
+
+
 def selftest_bounded_wait() -> int:
     """igg_selftest_bounded_wait: the device error bits recorded by a kernel
     whose bounded wait on an mbarrier that never completes runs out (expected
@@ -485,7 +498,10 @@ class Batch:
 
     def autotune(self, T2, T, Ci, reps=3, stream=None):
         """Time every (tile shape, z depth, CTAs/SM) candidate on these fields
-        and keep the fastest. Writes T2's inner points; synchronises."""
+        and keep the fastest. Writes T2's inner points; synchronises. The
+        choice is cached per (GPU name, dtype, problem sizes), in the process
+        and in the file named by IGG_AUTOTUNE_CACHE: a cached key applies
+        its tiling without timing (T2 untouched); reps < 0 re-tunes."""
         cfg = _ints((0, 0, 0))
         ms = ctypes.c_float()
         _check(_batch_sigs().igg_batch_autotune(self._h, self._p(T2, "T2"), self._p(T, "T"), self._p(Ci, "Ci"),

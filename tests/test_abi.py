@@ -83,3 +83,18 @@ def test_null_arguments(L):
     out = ctypes.c_double()
     assert L.igg_reduce(9, None, None, 0, 0, ctypes.byref(out), None) == -1
     assert L.igg_reduce(0, None, None, 0, 7, ctypes.byref(out), None) == -1
+
+
+def test_bounds_checked_build_loads_and_reports_itself(L):
+    """The bounds-checked library builds beside the release one, exports the
+    same functions and says which build it is; both reject a NULL status."""
+    path = igg_build.build(checked=True)
+    assert path == igg_build.LIB_CHECKED and path != igg_build.LIB
+    C = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(C, name), name
+    assert C.igg_bounds_checked() == 1
+    assert L.igg_bounds_checked() == 0
+    for lib in (C, L):
+        lib.igg_bounds_status.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        assert lib.igg_bounds_status(None, 0) == -1

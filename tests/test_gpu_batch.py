@@ -168,3 +168,54 @@ def test_batch_full_workload_sampled():
             ref = oracle.run(T0, np.full(T0.shape, float(ci[b])), nt, float(lam[b]), dt[b], *dd[b])
             gpu = B.view(res, b).double().cpu().numpy()
             assert np.abs(gpu - ref).max() <= (1 + nt) * 2 * 2.0 ** -24 * np.abs(ref).max()
+
+
+_CACHE_SCRIPT = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+import paper_2211_15716_gb300 as igg
+sizes = [(8 + 3 * i, 9 + i, 7 + 2 * i) for i in range(12)]
+B = igg.Batch(sizes, torch.float32)
+n = len(sizes)
+B.set_coefs([1.0] * n, [1e-4] * n, [0.1] * n, [0.1] * n, [0.1] * n)
+T = B.empty().fill_(1.5)
+C = B.empty().fill_(0.5)
+T2 = B.empty().fill_(-7.0)
+best = B.autotune(T2, T, C, reps=2)
+untouched = bool((T2 == -7.0).all())
+print(best["variant"], best["zb"], best["ctas_per_sm"], int(untouched))
+B.destroy()
+"""
+
+
+def test_autotune_cache_in_process_and_file(tmp_path):
+    """A second batch of the same shapes takes the cached tiling without
+    timing (T2 untouched), in the same process and, through the file named
+    by IGG_AUTOTUNE_CACHE, in a new one; reps < 0 times again."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, IGG_AUTOTUNE_CACHE=str(cache))
+    outs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", _CACHE_SCRIPT.format(root=root)], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(list(map(int, r.stdout.split()[-4:])))
+    assert outs[0][3] == 0  # tuned: T2 written
+    assert outs[1][:3] == outs[0][:3] and outs[1][3] == 1  # from the file: nothing timed
+    lines = cache.read_text().split("\n")
+    assert len([ln for ln in lines if ln.strip()]) == 1 and "|dt1|n12|" in lines[0]
+    # in-process: the first call tunes, the second is cached, reps < 0 re-tunes
+    sizes, lam, ci = small_batch(count=7, nmin=8, nmax=30, seed=11)
+    refs = oracle_run(sizes, lam, ci, 0)
+    B, T, T2, Ci = gpu_batch(sizes, lam, ci, refs, torch.float32)
+    with B:
+        a = B.autotune(T2, T, Ci, reps=1)
+        T2.fill_(-3.0)
+        b = B.autotune(T2, T, Ci, reps=1)
+        assert bool((T2 == -3.0).all()) and (a["variant"], a["zb"]) == (b["variant"], b["zb"])
+        B.autotune(T2, T, Ci, reps=-1)
+        assert not bool((T2 == -3.0).all())
