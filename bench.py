@@ -519,7 +519,8 @@ def profile_case(which):
     """Short fixed workloads for ncu captures of one kernel (not bench lines):
     'stencil': four hidden steps (stencil launch, fix-up launch, halo update)
     of the 2x2x2 x 256x128x128 FP64 workload, the same launches as the
-    benchmark's steps at one eighth of the points; 'adjoint': 13 adjoint
+    benchmark's steps at one eighth of the points; 'stencil_signed': the same
+    on its sign-changing field; 'adjoint': 13 adjoint
     steps at 256^3 on FP64 fields (T_n the Gaussian bump, sigma 0.15), then 13
     on FP32 fields; 'gp': three Gross-Pitaevskii steps on 2x2x2 x 128^3, FP64
     then FP32; 'stencil_groups': three plain steps of the 2x2x2 x 256x128x128
@@ -531,8 +532,8 @@ def profile_case(which):
     from paper_2211_15716_gb300 import autograd as ag
     from paper_2211_15716_gb300 import workloads as wl
 
-    if which == "stencil":
-        w = wl.WORKLOADS["decomposed_2x2x2_256x128x128"]
+    if which in ("stencil", "stencil_signed"):
+        w = wl.WORKLOADS["decomposed_2x2x2_256x128x128" + ("_signed" if which == "stencil_signed" else "")]
         g = igg.Grid(w.n, dims=w.dims, overlap=w.overlap, periods=w.periods)
         T, T2, Ci = wl.make_fields(w, g)
         dx, dy, dz, dt = wl.setup(w, g, Ci)
@@ -541,7 +542,7 @@ def profile_case(which):
             g.step_hidden(w.widths, T2, T, Ci, w.lam, dt, dx, dy, dz)
             T, T2 = T2, T
         a, b, tot, k = g.phase_times()
-        print(json.dumps({"profile": "stencil", "stencil_phase_ms": round(a / k, 4),
+        print(json.dumps({"profile": which, "stencil_phase_ms": round(a / k, 4),
                           "halo_ms": round(b / k, 4), "device_status": g.device_status()}))
         g.finalize()
     elif which == "stencil_groups":
@@ -759,7 +760,7 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--forms", action="store_true",
                     help="only measure the reshaped forms (one JSON line each)")
-    ap.add_argument("--profile", choices=["stencil", "stencil_groups", "adjoint", "gp"],
+    ap.add_argument("--profile", choices=["stencil", "stencil_signed", "stencil_groups", "adjoint", "gp"],
                     help="run a short fixed workload of one kernel for an ncu capture")
     ap.add_argument("--record-traffic", metavar="CSV",
                     help="write profiles/traffic.json from an ncu raw CSV export (no GPU)")

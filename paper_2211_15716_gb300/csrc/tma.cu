@@ -60,7 +60,10 @@ struct TmaShape {
   static constexpr int TBA = (TB + 127) / 128 * 128;
   static constexpr int CB = W * H * (int)sizeof(S);     // Ci box bytes
   static constexpr int STAGE = (TBA + CB + 127) / 128 * 128;
-  static constexpr int SMEM = NS * STAGE + 2 * NS * 8 + 64;  // + flags
+  // FP64 (emulated cell): per consumer warp, kFixPend fix-up entries staged
+  // before they are appended to the tile set's list
+  static constexpr int PEND = NS * STAGE + 2 * NS * 8 + 64;
+  static constexpr int SMEM = PEND + (sizeof(S) == 8 ? CONSUMERS * 16 * 16 : 0);  // + flags, staging
   static_assert(H % ROWS_PER_PASS == 0, "rows per tile");
   static_assert(BW <= 256 && BH <= 256, "TMA box dims");
 };
@@ -76,6 +79,10 @@ struct FixEntry {
   unsigned bits;  // bit l: point p + l left to the fix-up
   unsigned pad;
 };
+// Entries a consumer warp stages in shared memory before it reserves their
+// slots in the list with one atomic (a warp waited for each atomic's
+// return, row after row, on fields with many such points).
+constexpr unsigned kFixPend = 16;
 struct FixList {
   FixEntry *e;
   unsigned *count, *done;
@@ -322,6 +329,22 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       if (lane == 0) mbar_arrive(empty0);
     }
     int consumed = 2;
+    // the warp's staged fix-up entries (emulated FP64 cell)
+    FixEntry *pend = reinterpret_cast<FixEntry *>(smem + Sh::PEND) + warp * kFixPend;
+    unsigned npend = 0u;  // warp-uniform
+    auto flush = [&]() {
+      __syncwarp();
+      if (npend) {
+        const FixList fl = fix_list(fix, fix_cap);
+        unsigned base = 0u;
+        if (lane == 0) base = atomicAdd(fl.count, npend);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        // always within fix_cap: one entry per segment, plane and row at most
+        if (lane < npend && base + lane < fix_cap) fl.e[base + lane] = pend[lane];
+        npend = 0u;
+      }
+      __syncwarp();
+    };
     // FP64: two march steps per iteration (the z-plane registers alternate
     // instead of being copied; measured faster by a few percent)
     constexpr int kUnroll = sizeof(S) == 8 ? 2 : 1;
@@ -398,19 +421,21 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
           if (__any_sync(0xffffffffu, defm != 0u)) {
             const unsigned b0 = __ballot_sync(0xffffffffu, defm & 1u);
             const unsigned b1 = __ballot_sync(0xffffffffu, defm & 2u);
-            if (lane < 2) {
-              // points 32*lane .. 32*lane + 31: lanes 16*lane .. 16*lane + 15
-              const unsigned h0 = (b0 >> (16 * lane)) & 0xFFFFu, h1 = (b1 >> (16 * lane)) & 0xFFFFu;
-              const unsigned word = spread16(h0) | (spread16(h1) << 1);
-              if (word) {
-                const FixList fl = fix_list(fix, fix_cap);
-                const unsigned k = atomicAdd(fl.count, 1u);
-                if (k < fix_cap) {  // always: one entry per segment, plane and row at most
-                  fl.e[k].p = t.base + t.x0 + 32 * lane + srow * (t.r0 + r) + smarch * m;
-                  fl.e[k].bits = word;
-                }
-              }
+            // points 32*lane .. 32*lane + 31 (lanes 0, 1): lanes 16*lane ..
+            // 16*lane + 15 of the row
+            const unsigned h0 = (b0 >> (16 * (lane & 1))) & 0xFFFFu;
+            const unsigned h1 = (b1 >> (16 * (lane & 1))) & 0xFFFFu;
+            const unsigned word = lane < 2 ? spread16(h0) | (spread16(h1) << 1) : 0u;
+            const unsigned has = __ballot_sync(0xffffffffu, word != 0u);  // bits 0, 1
+            if (word) {
+              FixEntry en;
+              en.p = t.base + t.x0 + 32 * lane + srow * (t.r0 + r) + smarch * m;
+              en.bits = word;
+              en.pad = 0u;
+              pend[npend + __popc(has & ((1u << lane) - 1u))] = en;
             }
+            npend += __popc(has);
+            if (npend > kFixPend - 2) flush();
           }
         }
         zm[j] = c;
@@ -418,6 +443,7 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
       __syncwarp();
       if (lane == 0) mbar_arrive(empty0 + 8 * s);
     }
+    if constexpr (is_emu(MODE)) flush();
     if (warp == 0 && lane == 0) flags[2] = consumed;
   }
   __syncthreads();
