@@ -463,11 +463,13 @@ __global__ void __launch_bounds__(32 * 9, IGG_TMA_MIN_BLOCKS)
 // did not take get what cell() gives them (the same choice and arithmetic
 // as every kernel: the aligned path for stencils across powers of two or
 // zero, else the FP64 cell). The kernel listed every 32-point row segment
-// with such points (its first point and a bit mask); the fix-up's warps take
-// the entries in turn, lane l updating point p + l when bit l is set, each
-// warp loading its next entry while it works on the current one. Each block adds
-// its segments and points to the list's totals; the last block to finish
-// resets the list.
+// with such points (its first point and a bit mask). Each warp takes
+// kFixBatch entries at a time (one per lane of lanes 0..kFixBatch-1) and
+// deals their listed points out to its lanes, 32 at a time, in the order of
+// the entries and their bits, so that lanes are not left idle by sparse
+// masks. Each block adds its segments and points to the list's totals; the
+// last block to finish resets the list.
+constexpr unsigned kFixBatch = 4;
 __global__ void __launch_bounds__(256)
     k_fixup_f64(void *__restrict__ fix, size_t cap, double *__restrict__ T2,
                 const double *__restrict__ T, const double *__restrict__ Ci, int nx, int ny,
@@ -478,24 +480,53 @@ __global__ void __launch_bounds__(256)
   const long long sy = nx, sz = (long long)nx * ny;
   const int lane = threadIdx.x & 31;
   const unsigned warps = gridDim.x * (blockDim.x >> 5);
-  unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  FixEntry en = {};
-  if (e < count) en = fl.e[e];
+  const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   unsigned segs = 0u, pts = 0u;
-  for (; e < count; e += warps) {
-    FixEntry nxt = {};
-    if (e + warps < count) nxt = fl.e[e + warps];
-    segs += 1u;
-    pts += __popc(en.bits);
-    if (en.bits >> lane & 1u && in_bounds(en.p + lane - sz, c0.npts) &&
-        in_bounds(en.p + lane + sz, c0.npts)) {
-      const long long p = en.p + lane;
-      const double tc = __ldg(T + p);
-      const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
-                            __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
-      T2[p] = cell_emu_not_fast(tc, tn, __ldg(Ci + p), w);
+  for (unsigned b = gw * kFixBatch; b < count; b += warps * kFixBatch) {
+    FixEntry en = {};
+    if (lane < (int)kFixBatch && b + lane < count) en = fl.e[b + lane];
+    // inclusive prefix of the entries' point counts over lanes 0..kFixBatch-1
+    unsigned pre = __popc(en.bits);
+#pragma unroll
+    for (unsigned d = 1; d < kFixBatch; d <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, pre, d);
+      if ((unsigned)lane >= d) pre += v;
     }
-    en = nxt;
+    const unsigned total = __shfl_sync(0xffffffffu, pre, kFixBatch - 1);
+    segs += __popc(__ballot_sync(0xffffffffu, en.bits != 0u));
+    pts += total;
+    unsigned pk[kFixBatch], bk[kFixBatch];
+    long long qk[kFixBatch];
+#pragma unroll
+    for (unsigned q = 0; q < kFixBatch; ++q) {
+      pk[q] = __shfl_sync(0xffffffffu, pre, q);
+      bk[q] = __shfl_sync(0xffffffffu, en.bits, q);
+      qk[q] = __shfl_sync(0xffffffffu, en.p, q);
+    }
+    for (unsigned r = 0; r < total; r += 32u) {
+      const unsigned rank = r + lane;
+      if (rank >= total) break;
+      // the entry holding the point of this rank and the point's bit
+      unsigned q = 0u;
+#pragma unroll
+      for (unsigned k = 0; k + 1 < kFixBatch; ++k) q += rank >= pk[k] ? 1u : 0u;
+      unsigned bits = bk[0], excl = 0u;
+      long long p0 = qk[0];
+#pragma unroll
+      for (unsigned k = 1; k < kFixBatch; ++k)
+        if (q == k) {
+          bits = bk[k];
+          excl = pk[k - 1];
+          p0 = qk[k];
+        }
+      const long long p = p0 + __fns(bits, 0u, (int)(rank - excl + 1u));
+      if (in_bounds(p - sz, c0.npts) && in_bounds(p + sz, c0.npts)) {
+        const double tc = __ldg(T + p);
+        const double tn[6] = {__ldg(T + p - 1),  __ldg(T + p + 1),  __ldg(T + p - sy),
+                              __ldg(T + p + sy), __ldg(T + p - sz), __ldg(T + p + sz)};
+        T2[p] = cell_emu_not_fast(tc, tn, __ldg(Ci + p), w);
+      }
+    }
   }
   __shared__ unsigned bsum[2];
   if (threadIdx.x == 0) bsum[0] = bsum[1] = 0u;
