@@ -195,7 +195,7 @@ int igg_selftest_bounded_wait(unsigned *status);
  *     instructions per point). On the TMA kernel the points outside the
  *     one-FMA path go to a fix-up launch, so fields where many stencils
  *     change sign or exponent step about three times slower (a field that
- *     changes sign: 3.3 x the time of a smooth one, still below the FP64
+ *     changes sign: 3.0 x the time of a smooth one, below the FP64
  *     cell's 3.6 x; see igg_fixup_stats).
  *   IGG_OPT_FUSED_HALO (default 1): igg_step_hidden (and igg_run with
  *     widths) run as the full step launch followed by the one-launch halo
