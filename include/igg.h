@@ -208,11 +208,23 @@ int igg_selftest_bounded_wait(unsigned *status);
  *     records three CUDA events on its stream: at its start, after its
  *     stencil launches (with the emulated FP64 cell's fix-up launch), at its
  *     end; igg_phase_times reads them. Steps inside igg_run's graphs are not
- *     timed. Setting the option drops the steps recorded so far. */
+ *     timed. Setting the option drops the steps recorded so far.
+ *   IGG_OPT_HIDE_HALO (default 0): with IGG_OPT_FUSED_HALO = 1, 3-D grids
+ *     on the TMA kernel run a step followed by its halo update as two sets
+ *     of the full step's tiles: the face tiles (those that read a halo cell
+ *     or compute a point of a sent plane) and then the halo update on the
+ *     library's high-priority stream, the inner tiles meanwhile on its
+ *     low-priority stream; `stream` waits for both. The inner tiles neither
+ *     read nor write what the halo update touches, so the result is the
+ *     same bit for bit; 0 runs the tiles as one launch and then the halo
+ *     update on `stream`. Measured slower on the GB300: the two concurrent
+ *     tile sets take longer than the one launch by more than the halo
+ *     update they hide (FP64 bench step 1.179 against 1.146 ms). */
 #define IGG_OPT_TMA 1
 #define IGG_OPT_F64_EMU 2
 #define IGG_OPT_FUSED_HALO 3
 #define IGG_OPT_PHASE_TIMES 4
+#define IGG_OPT_HIDE_HALO 5
 int igg_grid_set_option(igg_grid *grid, int option, int value);
 
 /* Per-phase device time of the steps recorded under IGG_OPT_PHASE_TIMES
@@ -266,9 +278,12 @@ int igg_step(igg_grid *grid, void *T2, const void *T, const void *Ci,
              double dz, void *stream);
 
 /* Fig. 1 @hide_communication widths begin step!(T2,T,...); update_halo!(T2)
- * end. By default (IGG_OPT_FUSED_HALO = 1) this is the full step launch
- * followed by the one-launch halo update of T2, on `stream`. With the option
- * 0 it is the paper's split: the step on the boundary set of every subdomain (inner points whose
+ * end. By default (IGG_OPT_FUSED_HALO = 1) this is the full step's tiles
+ * followed by the one-launch halo update of T2 on `stream`; with
+ * IGG_OPT_HIDE_HALO = 1 on 3-D TMA grids the tiles next to the faces go
+ * first and the halo update runs beside the inner tiles (two streams of the
+ * library, joined into `stream`). With IGG_OPT_FUSED_HALO 0 it is the
+ * paper's split: the step on the boundary set of every subdomain (inner points whose
  * 1-based index i has i <= w or i >= n - w + 1 in some dimension, w =
  * widths[d]) runs first on the library's high-priority stream, followed
  * there by the halo update of T2; the inner block runs concurrently on the

@@ -93,6 +93,12 @@ struct SplitTiles {
   TileSet inner;
 };
 
+// The full step's TMA tiles in two sets: face tiles (reading a halo cell or
+// computing a point of a sent plane) and the rest (IGG_OPT_HIDE_HALO).
+struct PartTiles {
+  TileSet face, inner;
+};
+
 using GraphKey = std::tuple<const void *, const void *, const void *, int, int, int, int, int,
                             double, double, double, double>;
 
@@ -356,8 +362,9 @@ struct igg_grid {
   long long nloc = 0;
   std::vector<int> left, right;  // [nsub*3]
   cudaStream_t hi = nullptr, lo = nullptr, cap = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr, ev_face = nullptr;
   std::map<int, TileSet> full;                     // keyed by V (1 = scalar tiles)
+  std::map<int, PartTiles> part;                   // keyed by V (TMA tiles only)
   std::map<std::array<int, 4>, SplitTiles> split;  // keyed by widths and V
   PlaneCopy *copies[3] = {nullptr, nullptr, nullptr};
   int ncopies[3] = {0, 0, 0};
@@ -372,7 +379,8 @@ struct igg_grid {
   int *nbr = nullptr;           // device copy of left/right per subdomain and dimension
   bool tma_enabled = true;      // TMA kernel for the regular boxes when available
   int f64_emu = 1;              // FP64 fields: emulated FP64 cell (1) or FP64 cell (0)
-  bool fused_halo = true;       // hidden steps: halo update fused into one step launch
+  bool fused_halo = true;       // hidden steps: full-step tiles (else the boundary/inner split)
+  bool hide_halo = false;       // full-step tiles in face/inner sets, halo update beside the inner
   // IGG_OPT_PHASE_TIMES: three events per step queued outside graph
   // capture (start, end of the stencil launches, end of the step)
   bool phase_times = false;
@@ -436,6 +444,37 @@ int grid_vec(const igg_grid *g, igg_dtype dt) {
 }
 
 // Tiles of one box per subdomain, for the full step.
+// The full step's TMA tiles of every subdomain. Tile order: for each (z
+// chunk, row block) the tiles of the subdomains that are neighbours in x
+// side by side (measured faster than subdomain after subdomain).
+void full_tma_list(const igg_grid *g, int V, int zbt, int Wt, int Ht, std::vector<TmaTile> &out) {
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  std::vector<std::vector<TmaTile>> per(g->nsub);
+  for (int s = 0; s < g->nsub; ++s)
+    add_box_tma(per[s], (long long)s * g->nloc, (long long)s * nz, 1, nx - 1, 1, ny - 1, 1,
+                nz - 1, zbt, V, Wt, Ht);
+  const int nrow = (int)((nx - 1 + Wt - 1) / Wt);  // tiles per row block (x0 = 0 .. nx - 2)
+  const int dx = g->dims[0];
+  for (int syz = 0; syz < g->nsub / dx; ++syz)
+    for (size_t b = 0; b < per[syz * dx].size(); b += nrow)
+      for (int sx = 0; sx < dx; ++sx) {
+        const std::vector<TmaTile> &p = per[sx + dx * syz];
+        out.insert(out.end(), p.begin() + b, p.begin() + std::min(p.size(), b + nrow));
+      }
+}
+
+// Whether a full-step tile reads a halo cell or computes a point of a sent
+// plane in a dimension with exchanges: computed range [lo, hi) of a
+// dimension of n points, overlap o; the halo cells are 0 and n - 1, the
+// sent planes o - 1 and n - o.
+bool touches_faces(const igg_grid *g, const TmaTile &t) {
+  auto side = [](int lo, int hi, int n, int o) { return lo <= o - 1 || hi > n - o; };
+  const bool ex[3] = {g->ncopies[0] > 0, g->ncopies[1] > 0, g->ncopies[2] > 0};
+  return (ex[0] && side(t.xb, t.xe, g->n[0], g->overlap[0])) ||
+         (ex[1] && side(t.r0, t.re, g->n[1], g->overlap[1])) ||
+         (ex[2] && side(t.m0, t.m1, g->n[2], g->overlap[2]));
+}
+
 int build_full_tiles(igg_grid *g, int V, TileSet **out) {
   auto it = g->full.find(V);
   if (it != g->full.end()) {
@@ -453,23 +492,7 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
                                       nz - 2, tma_slots(V))
                       : 0;
   if (tma) {
-    // Tile order: for each (z chunk, row block) the tiles of the subdomains
-    // that are neighbours in x side by side, so that the halo cells a tile
-    // stores into its x neighbour share their 32-byte sectors with points
-    // that the neighbour's tiles store at about the same time (the L2 then
-    // merges the partial writes instead of reading the sectors back).
-    std::vector<std::vector<TmaTile>> per(g->nsub);
-    for (int s = 0; s < g->nsub; ++s)
-      add_box_tma(per[s], (long long)s * g->nloc, (long long)s * nz, 1, nx - 1, 1, ny - 1, 1,
-                  nz - 1, zbt, V, Wt, Ht);
-    const int nrow = (int)((nx - 1 + Wt - 1) / Wt);  // tiles per row block (x0 = 0 .. nx - 2)
-    const int dx = g->dims[0];
-    for (int syz = 0; syz < g->nsub / dx; ++syz)
-      for (size_t b = 0; b < per[syz * dx].size(); b += nrow)
-        for (int sx = 0; sx < dx; ++sx) {
-          const std::vector<TmaTile> &p = per[sx + dx * syz];
-          v.tma.insert(v.tma.end(), p.begin() + b, p.begin() + std::min(p.size(), b + nrow));
-        }
+    full_tma_list(g, V, zbt, Wt, Ht, v.tma);
   } else {
     for (int s = 0; s < g->nsub; ++s)
       add_tiles(v, V, (long long)s * g->nloc, nx, ny, 1, nx - 1, lo_in(ny), hi_in(ny), lo_in(nz),
@@ -479,6 +502,33 @@ int build_full_tiles(igg_grid *g, int V, TileSet **out) {
   TileSet ts;
   if (int rc = upload_tiles(v, V, &ts, tma ? TMA_WIDE : -1)) return rc;
   *out = &g->full.emplace(V, ts).first->second;
+  return IGG_OK;
+}
+
+// The full step's TMA tiles split into face and inner sets (same tiles, same
+// order within each set). Requires use_tma(g, V).
+int build_part_tiles(igg_grid *g, int V, PartTiles **out) {
+  auto it = g->part.find(V);
+  if (it != g->part.end()) {
+    *out = &it->second;
+    return IGG_OK;
+  }
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const int Wt = tma_tile_width(dtype_of_vec(V), TMA_WIDE);
+  const int Ht = tma_tile_rows(dtype_of_vec(V), TMA_WIDE);
+  const int zbt = choose_zb_tma(tma_xy_tiles(1, nx - 1, 1, ny - 1, V, Wt, Ht) * g->nsub, nz - 2,
+                                tma_slots(V));
+  std::vector<TmaTile> all;
+  full_tma_list(g, V, zbt, Wt, Ht, all);
+  TileLists f, in;
+  for (const TmaTile &t : all) (touches_faces(g, t) ? f : in).tma.push_back(t);
+  PartTiles pt;
+  if (int rc = upload_tiles(f, V, &pt.face, TMA_WIDE)) return rc;
+  if (int rc = upload_tiles(in, V, &pt.inner, TMA_WIDE)) {
+    free_tiles(pt.face);
+    return rc;
+  }
+  *out = &g->part.emplace(V, pt).first->second;
   return IGG_OK;
 }
 
@@ -718,6 +768,14 @@ bool any_halo(const igg_grid *g) { return g->ncopies[0] + g->ncopies[1] + g->nco
 // update (the option; the alternative is the boundary/inner split).
 bool use_fused_halo(const igg_grid *g) { return g->fused_halo; }
 
+// Whether a step with its halo update runs the full step's TMA tiles as face
+// and inner sets with the halo update beside the inner set (3-D grids on
+// the TMA kernel, with the grid's option).
+bool hide_applies(const igg_grid *g, int V, bool with_halo) {
+  return with_halo && g->hide_halo && use_fused_halo(g) && !low_dim(g) && use_tma(g, V) &&
+         any_halo(g);
+}
+
 // NVTX range over a host scope: the enqueue of one phase of the step (the
 // profiler places the GPU work it launches beneath it).
 struct NvtxRange {
@@ -765,6 +823,47 @@ int enqueue_step(igg_grid *g, const int *widths, void *T2, const void *T, const 
   NvtxRange step_range(with_halo ? "igg step + halo" : "igg step");
   cudaEvent_t p0 = phase_event(g, s, 0);
   if (p0 && (e = cudaEventRecord(p0, s)) != cudaSuccess) return cuda_error(e, "record");
+  if (!widths && hide_applies(g, V, with_halo)) {
+    // face tiles, then the halo update, on the high-priority stream; the
+    // inner tiles (which neither read halo cells nor compute sent points)
+    // beside them on the low-priority stream; s joins both
+    PartTiles *pt = nullptr;
+    if (int rc = build_part_tiles(g, V, &pt)) return rc;
+    c.ends = 1;
+    if ((e = cudaEventRecord(g->ev_fork, s)) != cudaSuccess) return cuda_error(e, "record");
+    if ((e = cudaStreamWaitEvent(g->hi, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
+    if ((e = cudaStreamWaitEvent(g->lo, g->ev_fork, 0)) != cudaSuccess) return cuda_error(e, "wait");
+    {
+      NvtxRange r("face tiles (high priority)");
+      if (pt->face.n > 0 && (e = launch_tiles(g, V, dt, pt->face, T2, T, Ci, c, g->hi)) != cudaSuccess)
+        return cuda_error(e, "face tiles launch");
+    }
+    cudaEvent_t pf = p0 ? g->ev_face : nullptr;
+    if (pf && (e = cudaEventRecord(pf, g->hi)) != cudaSuccess) return cuda_error(e, "record");
+    {
+      NvtxRange r("inner tiles (low priority)");
+      if (pt->inner.n > 0 && (e = launch_tiles(g, V, dt, pt->inner, T2, T, Ci, c, g->lo)) != cudaSuccess)
+        return cuda_error(e, "inner tiles launch");
+    }
+    {
+      NvtxRange r("halo update (high priority)");
+      if ((e = enqueue_halo(g, T2, dtype_size(dt), g->hi)) != cudaSuccess)
+        return cuda_error(e, "halo launch");
+    }
+    if ((e = cudaEventRecord(g->ev_hi, g->hi)) != cudaSuccess) return cuda_error(e, "record");
+    if ((e = cudaEventRecord(g->ev_lo, g->lo)) != cudaSuccess) return cuda_error(e, "record");
+    if (pf) {  // phase events: the end of both tile sets, then the end of the step
+      if ((e = cudaStreamWaitEvent(s, pf, 0)) != cudaSuccess) return cuda_error(e, "wait");
+      if ((e = cudaStreamWaitEvent(s, g->ev_lo, 0)) != cudaSuccess) return cuda_error(e, "wait");
+      if (cudaEvent_t p1 = phase_event(g, s, 1))
+        if ((e = cudaEventRecord(p1, s)) != cudaSuccess) return cuda_error(e, "record");
+    }
+    if ((e = cudaStreamWaitEvent(s, g->ev_hi, 0)) != cudaSuccess) return cuda_error(e, "wait");
+    if ((e = cudaStreamWaitEvent(s, g->ev_lo, 0)) != cudaSuccess) return cuda_error(e, "wait");
+    if (cudaEvent_t p2 = p0 ? phase_event(g, s, 2) : nullptr)
+      if ((e = cudaEventRecord(p2, s)) != cudaSuccess) return cuda_error(e, "record");
+    return IGG_OK;
+  }
   if (!widths) {
     TileSet *full = nullptr;
     if (int rc = build_full_tiles(g, V, &full)) return rc;
@@ -835,6 +934,10 @@ void destroy_grid(igg_grid *g) {
     free_tiles(kv.second.inner);
   }
   for (auto &kv : g->full) free_tiles(kv.second);
+  for (auto &kv : g->part) {
+    free_tiles(kv.second.face);
+    free_tiles(kv.second.inner);
+  }
   for (int d = 0; d < 3; ++d) cudaFree(g->copies[d]);
   for (auto &kv : g->staggered)
     for (int d = 0; d < 3; ++d) cudaFree(kv.second.copies[d]);
@@ -842,6 +945,7 @@ void destroy_grid(igg_grid *g) {
   cudaFree(g->nbr);
   for (cudaEvent_t e : g->pev) cudaEventDestroy(e);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_face) cudaEventDestroy(g->ev_face);
   if (g->ev_hi) cudaEventDestroy(g->ev_hi);
   if (g->ev_lo) cudaEventDestroy(g->ev_lo);
   if (g->hi) cudaStreamDestroy(g->hi);
@@ -945,6 +1049,7 @@ int igg_init_global_grid(int nx, int ny, int nz, const int dims_in[3], int nsub,
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_hi, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_lo, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_face, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     destroy_grid(g);
     return cuda_error(e, "stream/event creation");
@@ -1208,6 +1313,9 @@ int igg_run(igg_grid *g, int nt, const int widths[3], void *T, void *T2, const v
     if (widths && !use_fused_halo(g) && !low_dim(g)) {
       SplitTiles *st = nullptr;
       if (int rc = build_split_tiles(g, widths, V, &st)) return rc;
+    } else if (hide_applies(g, V, true)) {
+      PartTiles *pt = nullptr;
+      if (int rc = build_part_tiles(g, V, &pt)) return rc;
     } else {
       TileSet *full = nullptr;
       if (int rc = build_full_tiles(g, V, &full)) return rc;
@@ -1473,7 +1581,7 @@ int igg_grid_set_option(igg_grid *g, int option, int value) {
   clear_error();
   if (int rc = check_grid(g)) return rc;
   if (option != IGG_OPT_TMA && option != IGG_OPT_F64_EMU && option != IGG_OPT_FUSED_HALO &&
-      option != IGG_OPT_PHASE_TIMES)
+      option != IGG_OPT_PHASE_TIMES && option != IGG_OPT_HIDE_HALO)
     return set_error(IGG_EINVAL, "unknown option %d", option);
   DeviceGuard dg(g->device);
   cudaError_t e1 = cudaStreamSynchronize(g->hi), e2 = cudaStreamSynchronize(g->lo);
@@ -1486,6 +1594,7 @@ int igg_grid_set_option(igg_grid *g, int option, int value) {
   }
   if (option == IGG_OPT_TMA) g->tma_enabled = value != 0;
   else if (option == IGG_OPT_F64_EMU) g->f64_emu = value != 0 ? 1 : 0;
+  else if (option == IGG_OPT_HIDE_HALO) g->hide_halo = value != 0;
   else g->fused_halo = value != 0;
   // tile tables and graphs depend on the kernel choice
   for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
@@ -1496,7 +1605,12 @@ int igg_grid_set_option(igg_grid *g, int option, int value) {
   }
   g->split.clear();
   for (auto &kv : g->full) free_tiles(kv.second);
+  for (auto &kv : g->part) {
+    free_tiles(kv.second.face);
+    free_tiles(kv.second.inner);
+  }
   g->full.clear();
+  g->part.clear();
   return IGG_OK;
 }
 
@@ -1551,6 +1665,10 @@ int igg_fixup_stats(igg_grid *g, unsigned long long counts[2], int clear) {
   cudaError_t e = cudaDeviceSynchronize();
   std::vector<FixBuf *> bufs;
   for (auto &kv : g->full) bufs.push_back(&kv.second.fix);
+  for (auto &kv : g->part) {
+    bufs.push_back(&kv.second.face.fix);
+    bufs.push_back(&kv.second.inner.fix);
+  }
   for (auto &kv : g->split) {
     for (auto &b : kv.second.boundary) bufs.push_back(&b.fix);
     bufs.push_back(&kv.second.inner.fix);

@@ -199,6 +199,7 @@ class Grid:
     OPT_F64_EMU = 2
     OPT_FUSED_HALO = 3
     OPT_PHASE_TIMES = 4
+    OPT_HIDE_HALO = 5
 
     def set_option(self, option: int, value: int):
         """igg_grid_set_option (OPT_TMA: 1 = TMA kernel for regular boxes)."""

@@ -197,7 +197,9 @@ def test_phase_times_and_fixup_stats():
             g.step_hidden(w.widths, T2, T, Ci, w.lam, dt, dx, dy, dz)
             g.step(T, T2, Ci, w.lam, dt, dx, dy, dz)
         a, b, tot, n = g.phase_times()
-        assert n == 5 and a > 0 and b > 0 and tot == pytest.approx(a + b)
+        # b: the halo update's tail beyond the tiles (about 0 where it runs
+        # beside the inner tiles)
+        assert n == 5 and a > 0 and b >= 0 and tot == pytest.approx(a + b)
         assert g.phase_times()[3] == 0
         g.set_option(g.OPT_PHASE_TIMES, 0)
         g.step(T2, T, Ci, w.lam, dt, dx, dy, dz)

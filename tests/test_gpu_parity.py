@@ -436,3 +436,33 @@ def test_fused_halo_same_bits_as_split(dtype, n, dims, periods, overlap):
     if dtype == torch.float64:
         ref = oracle.run_decomposed(T0o, Cio, 5, 1.0, dt, *dd, dims, periods, overlap)
         assert rel_err(outs[0].cpu().numpy(), ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("n,dims,periods,overlap", [
+    ((70, 21, 19), (2, 2, 2), (1, 0, 0), (2, 2, 2)),   # faces, edges, corners; periodic in x
+    ((72, 18, 12), (2, 1, 1), (1, 0, 0), (2, 2, 2)),   # exchange in x only
+    ((70, 20, 14), (1, 2, 2), (0, 1, 0), (2, 3, 2)),   # overlap 3: sent planes off the halo
+    ((70, 20, 12), (1, 1, 1), (1, 1, 1), (2, 2, 2)),   # periodic self-neighbours
+    ((200, 40, 36), (2, 2, 2), (0, 0, 1), (2, 2, 2)),  # several tiles per row, inner tiles
+])
+def test_hidden_halo_beside_inner_tiles_same_bits(dtype, n, dims, periods, overlap):
+    """The hidden step with the face tiles first and the halo update beside
+    the inner tiles (IGG_OPT_HIDE_HALO) gives the bits of the full step
+    followed by the halo update, over several steps."""
+    with igg.Grid(n, dims=dims, overlap=overlap, periods=periods) as g:
+        T0, Ci = grid_fields(g, 5, "gaussian_rough")
+        w = wl.Workload("h", n, dims, periods, overlap)
+        Cd = dev(Ci, dtype)
+        dx, dy, dz, dt = wl.setup(w, g, dev(Ci))
+        outs = []
+        for hide in (1, 0):
+            g.set_option(g.OPT_HIDE_HALO, hide)
+            T = dev(T0, dtype)
+            r = g.run(5, T, T.clone(), Cd, 1.0, dt, dx, dy, dz, widths=(16, 4, 4))
+            r2 = T.clone()
+            g.step_hidden((16, 4, 4), r2, r, Cd, 1.0, dt, dx, dy, dz)
+            torch.cuda.synchronize()
+            outs.append((r.view(torch.uint8).cpu().numpy(), r2.view(torch.uint8).cpu().numpy()))
+        assert g.device_status() == 0
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
