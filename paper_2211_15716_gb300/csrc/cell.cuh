@@ -107,9 +107,10 @@ __device__ __forceinline__ double cell_f64(double t, double xm, double xp, doubl
 // ---------------------------------------------------------------------------
 // FP64 update with FP32/integer arithmetic for the differences ("emulated
 // FP64"). GB300 issues about two FP64 instructions per SM and clock, so the
-// 8-instruction FP64 cell caps the step near a quarter of HBM speed; this cell
-// spends two FP64 FMAs per point and does the rest on the FP32, integer and
-// conversion pipes.
+// 8-instruction FP64 cell caps the step near a quarter of HBM speed; the
+// emulated cell spends one FP64 FMA per point on its fast path (two on the
+// aligned path and in the helpers below) and does the rest on the FP32,
+// integer and conversion pipes.
 //
 // When the seven values of a stencil share sign and exponent field E, their
 // IEEE bit patterns, read as 64-bit integers, are K + M with a common K (sign

@@ -1,5 +1,6 @@
 // TMA-pipelined stencil kernel for the regular boxes of the step (the full
-// step and the inner block of the split): a producer warp streams, plane by
+// step, its face and inner tile sets, and the boxes of the split), and the
+// fix-up launch of the emulated FP64 cell: a producer warp streams, plane by
 // plane along z, a tile of T with a one-vector / one-row halo and the
 // matching tile of Ci from HBM into a ring of shared-memory stages with
 // cp.async.bulk.tensor (TMA); eight consumer warps compute from shared
