@@ -25,6 +25,10 @@ What each function follows (section / figure of the paper):
   * adjoint_step / gradient: the transposed step run backward in time, for
     a misfit loss 0.5*sum((T_nt - T_obs)^2) (the differentiated form of the
     Fig. 1 solver).
+  * update_halo_adjoint / gradient_decomposed: the same on a grid of
+    subdomains: the transpose of the halo update (each halo entry added into
+    its source and set to 0, dimensions z, y, x), then the transposed step on
+    every subdomain.
 Readings of points the paper leaves open (overlap 2 with halo width 1,
 global size n_g = dims*(n-o) + o for non-periodic and dims*(n-o) for periodic
 dimensions, subdomain numbering x fastest, the second difference as a
@@ -36,7 +40,8 @@ stationarity, conservation of sum(T/Ci) with periodic boundaries, mirror
 symmetry, a Kronecker-sum sparse Laplacian, a hand-computed 3x3x3 golden
 case, decomposed == undecomposed bit for bit, split == unsplit bit for bit,
 MPI_Dims_create examples, adjoint dot-product identities and central finite
-differences.
+differences (single array and decomposed grids; the decomposed gradient
+equals the single-array one on one subdomain, bit for bit).
 """
 from __future__ import annotations
 
@@ -84,6 +89,7 @@ def _load():
         lib.oracle_step.argtypes = [L, L, L, P, P, P, D, D, D, D, D]
         lib.oracle_step_part.argtypes = [L, L, L, P, P, P, D, D, D, D, D, L, L, L, ctypes.c_int]
         lib.oracle_update_halo.argtypes = [ctypes.c_int, P, P, L, L, L, P, P, L]
+        lib.oracle_update_halo_adjoint.argtypes = [ctypes.c_int, P, P, L, L, L, P, P]
         lib.oracle_adjoint_step.argtypes = [L, L, L, P, P, P, P, P, D, D, D, D, D]
         lib.oracle_acoustic_step.argtypes = [L, L, L, P, P, P, P, D, D, D, D, D, D]
         lib.oracle_gp_half.argtypes = [L, L, L, ctypes.c_int, P, P, P, D, D, D, D, D]
@@ -261,6 +267,21 @@ def update_halo(field: np.ndarray, dims, periods, overlap):
     ov = np.ascontiguousarray(overlap, dtype=np.int64)
     _load().oracle_update_halo(nsub, _ptr(left), _ptr(right), nx, ny, nz, _ptr(ov),
                                _ptr(field), field.dtype.itemsize)
+
+
+def update_halo_adjoint(lam: np.ndarray, dims, periods, overlap):
+    """The transpose of update_halo on an FP64 field [nsub][nz][ny][nx], in
+    place: every halo entry is added into the entry its value came from and
+    set to 0, dimensions z, then y, then x (see oracle.c)."""
+    if not lam.flags.c_contiguous or lam.ndim != 4 or lam.dtype != np.float64:
+        raise ValueError("lam must be a C-contiguous float64 [nsub][nz][ny][nx]")
+    nsub, nz, ny, nx = lam.shape
+    left, right = neighbours(dims, periods)
+    if left.shape[0] != nsub:
+        raise ValueError("field's subdomain count differs from dims")
+    ov = np.ascontiguousarray(overlap, dtype=np.int64)
+    _load().oracle_update_halo_adjoint(nsub, _ptr(left), _ptr(right), nx, ny, nz, _ptr(ov),
+                                       _ptr(lam))
 
 
 def staggered_overlap(n, nf, overlap):
@@ -458,3 +479,41 @@ def bf16_ulp(x: np.ndarray) -> np.ndarray:
     """Spacing of BF16 values at |x| (normal range)."""
     _, e = np.frexp(np.asarray(x, dtype=np.float64))
     return np.ldexp(1.0, e - 8)
+
+
+# --------------------------------------------------------------------------
+# adjoint on a grid of subdomains
+# --------------------------------------------------------------------------
+def forward_states_decomposed(T0, Ci, nt, lam, dt, dx, dy, dz, dims, periods, overlap):
+    """All states T_0..T_nt of run_decomposed (no checkpointing): per step,
+    step! on every subdomain, then update_halo!."""
+    states = [np.array(T0, dtype=np.float64, order="C", copy=True)]
+    for _ in range(nt):
+        T = states[-1]
+        T2 = T.copy()
+        for s in range(T.shape[0]):
+            step(T2[s], T[s], Ci[s], lam, dt, dx, dy, dz)
+        update_halo(T2, dims, periods, overlap)
+        states.append(T2)
+    return states
+
+
+def gradient_decomposed(T0, Ci, T_obs, nt, lam, dt, dx, dy, dz, dims, periods, overlap):
+    """(J, dJ/dT0, dJ/dCi) of J = 0.5*sum((T_nt - T_obs)^2) over every entry
+    of the decomposed fields [nsub][nz][ny][nx] (dt held fixed). One step is
+    T_{n+1} = H(S(T_n)): S the step on every subdomain (the identity off its
+    inner points), H the halo update. Backward in time, lam <- H^T lam
+    (update_halo_adjoint), then lam <- S^T lam and gCi += k lam L(T_n) on
+    every subdomain (adjoint_step)."""
+    states = forward_states_decomposed(T0, Ci, nt, lam, dt, dx, dy, dz, dims, periods, overlap)
+    J = loss(states[-1], T_obs)
+    lam_n = np.ascontiguousarray(states[-1] - T_obs)
+    gCi = np.zeros_like(lam_n)
+    out = np.empty_like(lam_n)
+    C = np.ascontiguousarray(Ci, dtype=np.float64)
+    for n in range(nt - 1, -1, -1):
+        update_halo_adjoint(lam_n, dims, periods, overlap)
+        for s in range(lam_n.shape[0]):
+            adjoint_step(out[s], lam_n[s], states[n][s], C[s], gCi[s], lam, dt, dx, dy, dz)
+        lam_n, out = out, lam_n
+    return J, lam_n.copy(), gCi

@@ -153,6 +153,46 @@ void oracle_update_halo(int nsub, const int *left_nb, const int *right_nb,
   }
 }
 
+/* The adjoint (transpose) of the halo update above on an FP64 field: the
+ * update is a product of plane copies, dimensions x, then y, then z, and
+ * each copy field[dst] = field[src] is the linear map that replaces the
+ * dst entry by the src entry. Its transpose adds the dst entry into the src
+ * entry and sets the dst entry to 0. The transpose of the product takes the
+ * dimensions in the reverse order: z, then y, then x. Within one dimension
+ * the copies' dst planes (0 and n-1) and src planes (o-1 and n-o) are
+ * distinct, so their order does not matter. */
+void oracle_update_halo_adjoint(int nsub, const int *left_nb, const int *right_nb,
+                                long nx, long ny, long nz, const long *overlap,
+                                double *lam) {
+  const long n[3] = {nx, ny, nz};
+  const size_t nloc = (size_t)nx * (size_t)ny * (size_t)nz;
+  for (int d = 2; d >= 0; --d) {
+    const long o = overlap[d];
+    if (o < 2 || n[d] < 2) continue;
+    for (int s = 0; s < nsub; ++s) {
+      for (int side = 0; side < 2; ++side) {
+        int nb = side == 0 ? left_nb[3 * s + d] : right_nb[3 * s + d];
+        if (nb < 0) continue;
+        long dst_plane = side == 0 ? 0 : n[d] - 1;
+        long src_plane = side == 0 ? n[d] - o : o - 1;
+        double *dst = lam + (size_t)s * nloc;
+        double *src = lam + (size_t)nb * nloc;
+        const int da = d == 0 ? 1 : 0, db = d == 2 ? 1 : 2;
+        for (long ib = 0; ib < n[db]; ++ib)
+          for (long ia = 0; ia < n[da]; ++ia) {
+            long c[3], cs[3];
+            c[d] = dst_plane;
+            cs[d] = src_plane;
+            c[da] = cs[da] = ia;
+            c[db] = cs[db] = ib;
+            src[AT(cs[0], cs[1], cs[2])] += dst[AT(c[0], c[1], c[2])];
+            dst[AT(c[0], c[1], c[2])] = 0.0;
+          }
+      }
+    }
+  }
+}
+
 /* One backward step of the discrete adjoint of Fig. 1's step! (the transposed
  * stencil run backward in time; the gradient form of the step).
  * Forward: T_{n+1}[p] = T_n[p] + dt*lam*Ci[p]*(L T_n)[p] on inner p, identity
