@@ -449,12 +449,17 @@ int igg_batch_autotune(igg_batch *batch, void *T2, const void *T,
 /* ---------------------------------------------------------------------------
  * Adjoint form: gradients of a function J(T_nt) of the state after nt steps
  * of Fig. 1's loop with respect to Ci and to the initial state T_0 (the
- * differentiated solver; dt is held fixed). Grids with ONE non-periodic
- * subdomain; F64 or F32 fields; the Ci gradient is accumulated in FP64.
+ * differentiated solver; dt is held fixed). 3-D grids of any topology
+ * (periodic and decomposed included); F64 or F32 fields; the Ci gradient is
+ * accumulated in FP64. J is a function of every entry of the decomposed
+ * field (halo and overlap entries included), and the gradients are per
+ * entry of the decomposed T0 and Ci.
  *
- * Forward step on inner points p: T_{n+1}[p] = T_n[p] + Ci[p]*l(T_n)[p],
- * l(T)[p] = sum_d w_d (T[p-e_d] + T[p+e_d] - 2 T[p]), w_d = dt*lam/dd^2;
- * boundary points are unchanged.
+ * Forward step on the inner points p of every subdomain: T_{n+1}[p] =
+ * T_n[p] + Ci[p]*l(T_n)[p], l(T)[p] = sum_d w_d (T[p-e_d] + T[p+e_d] -
+ * 2 T[p]), w_d = dt*lam/dd^2; the other points are unchanged; then the halo
+ * update. So a step is H(S(T)) and its adjoint S^T(H^T(lam)):
+ * igg_update_halo_adjoint applies H^T, igg_adjoint_step S^T.
  *
  * Arithmetic of a step: F32 fields in F32 with FMAs, the gCi increment in
  * FP64 from the two F32 factors. F64 fields: lam_out is formed in float pairs
@@ -474,19 +479,31 @@ int igg_batch_autotune(igg_batch *batch, void *T2, const void *T,
  *   v = Ci*lam_in on inner points, 0 elsewhere,
  *   lam_out[q] = lam_in[q] + sum_d w_d (v[q-e_d] + v[q+e_d] - 2 v[q])
  * (neighbours outside the array count as 0), and accumulates
- *   gCi[p] += lam_in[p] * l(T_n)[p] on inner points p (gCi: FP64 array).
- * lam_out must not alias lam_in. */
+ *   gCi[p] += lam_in[p] * l(T_n)[p] on inner points p (gCi: FP64 array),
+ * on every subdomain (one launch each; fields of the grid's shape).
+ * lam_out must not alias lam_in. On a grid with halos, apply
+ * igg_update_halo_adjoint to lam_in first for the adjoint of a whole step. */
 int igg_adjoint_step(igg_grid *grid, void *lam_out, const void *lam_in,
                      const void *T_n, const void *Ci, double *gCi,
                      igg_dtype dtype, double lam, double dt, double dx,
                      double dy, double dz, void *stream);
+
+/* The transpose of update_halo! (the halo update of a field of the grid's
+ * own size), in place on an F64 or F32 field lam: the halo update is a
+ * product of plane copies field[dst] = field[src], dimensions x, then y,
+ * then z; its transpose takes the dimensions z, then y, then x and, for each
+ * copy, adds lam[dst] into lam[src] and sets lam[dst] to 0. No counterpart
+ * in the paper, which differentiates nothing: the halo part of the adjoint
+ * of Fig. 1's loop on the implicit global grid. */
+int igg_update_halo_adjoint(igg_grid *grid, void *lam, igg_dtype dtype, void *stream);
 
 /* Number of checkpoints of an nt-step run with one checkpoint every `every`
  * steps: the states T_0, T_every, T_2every, ... before step nt, i.e.
  * ceil(nt/every). Returns the count (> 0) or IGG_EINVAL. */
 int igg_checkpoint_slots(int nt, int every);
 
-/* Forward run that keeps checkpoints: nt steps from T0 (boundary values of
+/* Forward run that keeps checkpoints: nt steps of Fig. 1's loop (step, then
+ * the halo update on grids with halos) from T0 (physical boundary values of
  * T0 stay fixed), storing state T_{k*every} in slot k of `ckpt`
  * (igg_checkpoint_slots fields, contiguous) and T_nt in T_out. `work` holds
  * two fields (scratch of the caller). */
@@ -498,8 +515,9 @@ int igg_forward_checkpointed(igg_grid *grid, int nt, int every, const void *T0,
 /* Backward run: from lam_nt = dJ/dT_nt and the checkpoints of
  * igg_forward_checkpointed, recomputes each segment of `every` states from
  * its checkpoint (into `seg`, every-1 fields; unused when every == 1) and
- * runs the adjoint steps backward in time. Writes gT0 = dJ/dT_0 (dtype
- * field) and gCi = dJ/dCi (FP64 field, overwritten). `work` holds two fields.
+ * runs the adjoint steps backward in time (H^T, then S^T per subdomain).
+ * Writes gT0 = dJ/dT_0 (dtype field) and gCi = dJ/dCi (FP64 field,
+ * overwritten). `work` holds two fields.
  * Memory: (ceil(nt/every) + every + 3) fields instead of nt + 1; F64 fields
  * on the TMA kernel also take, for the run, a scratch of 8 bytes per point
  * (Ci as float pairs) from the stream-ordered allocator on `stream`. */

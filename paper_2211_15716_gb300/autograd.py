@@ -32,6 +32,8 @@ def _L():
         L.igg_adjoint_checkpointed.restype = I
         L.igg_adjoint_step.argtypes = [P, P, P, P, P, P, I, D, D, D, D, D, P]
         L.igg_adjoint_step.restype = I
+        L.igg_update_halo_adjoint.argtypes = [P, P, I, P]
+        L.igg_update_halo_adjoint.restype = I
         L.igg_residual.argtypes = [P, P, P, ctypes.c_size_t, I, P]
         L.igg_residual.restype = I
         _sigs = True
@@ -57,6 +59,13 @@ def adjoint_step(grid: Grid, lam_out, lam_in, Tn, Ci, gCi, lam, dt, dx, dy, dz, 
     _check(_L().igg_adjoint_step(grid._handle(), _p(lam_out), _p(lam_in), _p(Tn), _p(Ci), _p(gCi),
                                  dtype_code(Tn.dtype), float(lam), float(dt), float(dx), float(dy),
                                  float(dz), _stream(stream)))
+
+
+def update_halo_adjoint(grid: Grid, lam, stream=None):
+    """The transpose of the halo update, in place (igg_update_halo_adjoint)."""
+    _check(_L().igg_update_halo_adjoint(grid._handle(), _p(lam), dtype_code(lam.dtype),
+                                        _stream(stream)))
+    return lam
 
 
 def residual(a, b, out=None, stream=None):
@@ -96,8 +105,9 @@ def adjoint_checkpointed(grid, nt, every, ckpt, Ci, lam_nt, lam, dt, dx, dy, dz)
 
 
 class DiffusionSolve(torch.autograd.Function):
-    """T_nt = nt steps of Fig. 1's loop from (T0, Ci) on a single-subdomain
-    grid; differentiable in T0 and Ci."""
+    """T_nt = nt steps of Fig. 1's loop from (T0, Ci) on a 3-D grid of any
+    topology (each step: step!, then update_halo!); differentiable in T0 and
+    Ci (per entry of the decomposed fields)."""
 
     @staticmethod
     def forward(ctx, T0, Ci, grid, nt, lam, dt, dx, dy, dz, every):

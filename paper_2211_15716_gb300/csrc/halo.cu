@@ -154,6 +154,26 @@ __global__ void __launch_bounds__(256) k_halo_gather(E *__restrict__ f, const Ha
   }
 }
 
+// The transpose of one dimension's plane copies (the adjoint of
+// update_halo!, dimension by dimension in the order z, y, x): per (copy,
+// plane row b), every point adds its dst entry into its src entry and sets
+// the dst entry to 0. The copies' dst planes (0, n - 1) are never src planes
+// (o - 1, n - o); a src plane feeds one dst plane, except on a dimension of
+// 2o - 1 points, where o - 1 = n - o feeds both: the adds are atomic.
+template <class E>
+__global__ void __launch_bounds__(256)
+    k_halo_planes_adj(const PlaneCopy *__restrict__ copies, E *__restrict__ f, int na, int nb,
+                      long long sa, long long sb) {
+  const int ci = blockIdx.x / nb, b = blockIdx.x % nb;
+  const PlaneCopy c = copies[ci];
+  const long long rb = (long long)b * sb;
+  for (int a = threadIdx.x; a < na; a += blockDim.x) {
+    const long long i = c.dst + rb + a * sa, j = c.src + rb + a * sa;
+    atomicAdd(f + j, f[i]);
+    f[i] = E(0);
+  }
+}
+
 bool vec_rows(size_t elem_size, int na, long long sa, long long sb, const void *field) {
   return sa == 1 && ((long long)na * (long long)elem_size) % 16 == 0 && sb % na == 0 &&
          reinterpret_cast<uintptr_t>(field) % 16 == 0;
@@ -197,6 +217,21 @@ cudaError_t launch_halo(size_t elem_size, const PlaneCopy *copies, int ncopies,
     case 2: return launch_e<unsigned short>(copies, ncopies, field, na, nb, sa, sb, vec, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_halo_adjoint(size_t elem_size, const PlaneCopy *copies, int ncopies,
+                                void *field, int na, int nb, long long sa, long long sb,
+                                cudaStream_t s) {
+  if (ncopies <= 0) return cudaSuccess;
+  if ((long long)ncopies * nb >= (1ll << 31)) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((long long)ncopies * nb);
+  if (elem_size == 8)
+    k_halo_planes_adj<double><<<blocks, 256, 0, s>>>(copies, (double *)field, na, nb, sa, sb);
+  else if (elem_size == 4)
+    k_halo_planes_adj<float><<<blocks, 256, 0, s>>>(copies, (float *)field, na, nb, sa, sb);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_halo_gather(size_t elem_size, void *field, const HaloGather &h,

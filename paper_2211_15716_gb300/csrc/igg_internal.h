@@ -268,6 +268,11 @@ struct HaloGather {
 };
 cudaError_t launch_halo_gather(size_t elem_size, void *field, const HaloGather &h,
                                cudaStream_t s);
+// The transpose of one dimension's plane copies on an F64 (elem_size 8) or
+// F32 (4) field: field[src] += field[dst], field[dst] = 0 (halo.cu).
+cudaError_t launch_halo_adjoint(size_t elem_size, const PlaneCopy *copies, int ncopies,
+                                void *field, int na, int nb, long long sa, long long sb,
+                                cudaStream_t s);
 
 // Adjoint step over every point of one array, and out = a - b elementwise.
 // With `tma`, fields that allow it take the TMA-pipelined kernel; FP64 fields

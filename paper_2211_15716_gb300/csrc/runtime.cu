@@ -687,6 +687,17 @@ cudaError_t enqueue_halo(PlaneCopy *const copies[3], const int ncopies[3], const
   return e;
 }
 
+// The transpose of the halo update of a field of the grid's own size (F64
+// or F32): the plane copies' transposes, dimensions z, y, x.
+cudaError_t enqueue_halo_adjoint(igg_grid *g, void *field, size_t es, cudaStream_t s) {
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const long long sxy = (long long)nx * ny;
+  cudaError_t e = launch_halo_adjoint(es, g->copies[2], g->ncopies[2], field, nx, ny, 1, nx, s);
+  if (e == cudaSuccess) e = launch_halo_adjoint(es, g->copies[1], g->ncopies[1], field, nx, nz, 1, sxy, s);
+  if (e == cudaSuccess) e = launch_halo_adjoint(es, g->copies[0], g->ncopies[0], field, ny, nz, nx, sxy, s);
+  return e;
+}
+
 // The halo update of a field of the grid's own size: on 3-D grids one
 // gather launch, else the plane copies dimension by dimension.
 cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
@@ -1419,10 +1430,26 @@ int igg_reduce(int op, const void *a, const void *b, size_t n, igg_dtype dt, dou
 // ---------------------------------------------------------------------------
 static int check_adjoint_grid(const igg_grid *g, igg_dtype dt) {
   if (low_dim(g)) return set_error(IGG_EINVAL, "the adjoint needs a 3-D grid");
-  if (g->nsub != 1 || g->periods[0] || g->periods[1] || g->periods[2])
-    return set_error(IGG_EINVAL, "the adjoint needs a single non-periodic subdomain");
   if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "adjoint dtype must be F64 or F32");
   return IGG_OK;
+}
+
+// The transposed step S^T on every subdomain (one launch each); the
+// subdomains' fields are consecutive blocks of nloc points.
+static cudaError_t adjoint_subdomains(igg_grid *g, igg_dtype dt, void *lam_out,
+                                      const void *lam_in, const void *Tn, const void *Ci,
+                                      double *gCi, const Coef &c, cudaStream_t s,
+                                      const void *ci_pairs) {
+  const size_t bytes = (size_t)g->nloc * dtype_size(dt);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < g->nsub && e == cudaSuccess; ++k) {
+    const size_t o = (size_t)k * bytes;
+    e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], (char *)lam_out + o,
+                       (const char *)lam_in + o, (const char *)Tn + o, (const char *)Ci + o,
+                       gCi + (size_t)k * g->nloc, c, g->tma_enabled, g->dev_err, s,
+                       ci_pairs ? (const char *)ci_pairs + (size_t)k * g->nloc * 8 : nullptr);
+  }
+  return e;
 }
 
 int igg_checkpoint_slots(int nt, int every) {
@@ -1442,10 +1469,21 @@ int igg_adjoint_step(igg_grid *g, void *lam_out, const void *lam_in, const void 
   if (lam_out == lam_in) return set_error(IGG_EINVAL, "lam_out aliases lam_in");
   if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
   DeviceGuard dg(g->device);
-  cudaError_t e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], lam_out, lam_in, Tn, Ci, gCi,
-                                 make_coef(lam, dtime, dx, dy, dz), g->tma_enabled, g->dev_err,
-                                 (cudaStream_t)stream);
+  cudaError_t e = adjoint_subdomains(g, dt, lam_out, lam_in, Tn, Ci, gCi,
+                                     make_coef(lam, dtime, dx, dy, dz), (cudaStream_t)stream,
+                                     nullptr);
   if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
+  return IGG_OK;
+}
+
+int igg_update_halo_adjoint(igg_grid *g, void *lam, igg_dtype dt, void *stream) {
+  clear_error();
+  if (int rc = check_grid(g)) return rc;
+  if (dt != IGG_F64 && dt != IGG_F32) return set_error(IGG_EINVAL, "dtype must be F64 or F32");
+  if (int rc = check_field(g, lam, "lam")) return rc;
+  DeviceGuard dg(g->device);
+  cudaError_t e = enqueue_halo_adjoint(g, lam, dtype_size(dt), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "halo adjoint launch");
   return IGG_OK;
 }
 
@@ -1472,7 +1510,8 @@ int igg_forward_checkpointed(igg_grid *g, int nt, int every, const void *T0, con
   if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
   DeviceGuard dg(g->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t es = dtype_size(dt), bytes = (size_t)g->nloc * es;
+  const size_t es = dtype_size(dt), bytes = (size_t)g->nsub * (size_t)g->nloc * es;
+  const bool halo = any_halo(g);  // the steps of Fig. 1's loop: step!, then update_halo!
   char *A = (char *)work, *B = (char *)work + bytes, *K = (char *)ckpt;
   const Coef c = make_coef(lam, dtime, dx, dy, dz);
   cudaError_t e = cudaMemcpyAsync(A, T0, bytes, cudaMemcpyDeviceToDevice, s);
@@ -1482,7 +1521,7 @@ int igg_forward_checkpointed(igg_grid *g, int nt, int every, const void *T0, con
   char *cur = A;
   for (int n = 0; n < nt; ++n) {
     char *nxt = cur == A ? B : A;
-    if (int rc = enqueue_step(g, nullptr, nxt, cur, Ci, dt, c, false, s)) return rc;
+    if (int rc = enqueue_step(g, nullptr, nxt, cur, Ci, dt, c, halo, s)) return rc;
     cur = nxt;
     if ((n + 1) % every == 0 && n + 1 < nt) {
       e = cudaMemcpyAsync(K + (size_t)((n + 1) / every) * bytes, cur, bytes,
@@ -1511,7 +1550,9 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
   if (int rc = check_coef(lam, dtime, dx, dy, dz)) return rc;
   DeviceGuard dg(g->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t es = dtype_size(dt), bytes = (size_t)g->nloc * es;
+  const size_t ntot = (size_t)g->nsub * (size_t)g->nloc;
+  const size_t es = dtype_size(dt), bytes = ntot * es;
+  const bool halo = any_halo(g);
   const char *K = (const char *)ckpt;
   char *S = (char *)seg, *LA = (char *)work, *LB = (char *)work + bytes;
   const Coef c = make_coef(lam, dtime, dx, dy, dz);
@@ -1529,16 +1570,16 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
       adjoint_tma_applies(dt, g->n[0], work, lam_nt, ckpt, Ci, gCi)) {
     // without room for the pairs the adjoint steps take the kernel that
     // reads Ci itself (the same bits): a failed allocation is not an error
-    if (cudaMallocAsync(&ci_pairs.p, (size_t)g->nloc * 8, s) != cudaSuccess) {
+    if (cudaMallocAsync(&ci_pairs.p, ntot * 8, s) != cudaSuccess) {
       ci_pairs.p = nullptr;
       (void)cudaGetLastError();
     } else {
-      cudaError_t ea = launch_pair_ci(Ci, ci_pairs.p, g->nloc, s);
+      cudaError_t ea = launch_pair_ci(Ci, ci_pairs.p, (long long)ntot, s);
       if (ea != cudaSuccess) return cuda_error(ea, "Ci pairs");
     }
   }
   cudaError_t e = cudaMemcpyAsync(LA, lam_nt, bytes, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(gCi, 0, (size_t)g->nloc * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(gCi, 0, ntot * sizeof(double), s);
   // segment buffers carry the fixed boundary values of T0 (steps write inner points only)
   for (int j = 1; j < every && e == cudaSuccess; ++j)
     e = cudaMemcpyAsync(S + (size_t)(j - 1) * bytes, K, bytes, cudaMemcpyDeviceToDevice, s);
@@ -1550,12 +1591,14 @@ int igg_adjoint_checkpointed(igg_grid *g, int nt, int every, const void *ckpt, c
       return j == 0 ? K + (size_t)k * bytes : S + (size_t)(j - 1) * bytes;
     };
     for (int j = 1; j < len; ++j)
-      if (int rc = enqueue_step(g, nullptr, (void *)state(j), state(j - 1), Ci, dt, c, false, s))
+      if (int rc = enqueue_step(g, nullptr, (void *)state(j), state(j - 1), Ci, dt, c, halo, s))
         return rc;
     for (int j = len - 1; j >= 0; --j) {
+      // one step is H(S(T)): lam <- H^T lam (in place), then S^T per subdomain
       char *nxt = cur == LA ? LB : LA;
-      e = launch_adjoint(dt, g->n[0], g->n[1], g->n[2], nxt, cur, state(j), Ci, gCi, c,
-                         g->tma_enabled, g->dev_err, s, ci_pairs.p);
+      if (halo && (e = enqueue_halo_adjoint(g, cur, es, s)) != cudaSuccess)
+        return cuda_error(e, "halo adjoint launch");
+      e = adjoint_subdomains(g, dt, nxt, cur, state(j), Ci, gCi, c, s, ci_pairs.p);
       if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
       cur = nxt;
     }

@@ -142,8 +142,8 @@ def test_fp32_gradient_vs_fp64_oracle():
     assert np.linalg.norm(gT - gT0) <= 1e-3 * np.linalg.norm(gT0)
 
 
-def test_adjoint_rejects_decomposed_grid():
-    with igg.Grid((8, 8, 8), dims=(2, 1, 1)) as g:
+def test_adjoint_rejects_low_dimensional_grid():
+    with igg.Grid((8, 8, 1), dims=(2, 1, 1)) as g:
         t = g.empty()
         with pytest.raises(igg.IggError):
             ag.adjoint_step(g, t.clone(), t, t, t, torch.zeros_like(t), 1.0, 1e-3, 1.0, 1.0, 1.0)
