@@ -526,7 +526,9 @@ def profile_case(which):
     then FP32; 'stencil_groups': three plain steps of the 2x2x2 x 256x128x128
     grid with the workload's spacings (two weight groups), then three with
     equal spacings (one group), on T = 2 + U[0, 5e-4] (one binade) and
-    Ci = 1/U[1.5, 2.5]. Prints each case's ms per launch."""
+    Ci = 1/U[1.5, 2.5]; 'acoustic': three acoustic steps (velocities,
+    pressure, halo update of the four fields) on 2x2x2 x 256^3 cells, FP64
+    then FP32. Prints each case's ms per launch."""
     import synth
     import paper_2211_15716_gb300 as igg
     from paper_2211_15716_gb300 import autograd as ag
@@ -545,6 +547,17 @@ def profile_case(which):
         print(json.dumps({"profile": which, "stencil_phase_ms": round(a / k, 4),
                           "halo_ms": round(b / k, 4), "device_status": g.device_status()}))
         g.finalize()
+    elif which == "acoustic":
+        n = (256, 256, 256)
+        h = (1 / 511, 1 / 511, 1 / 511)
+        dt = 0.3 * h[0] / math.sqrt(2.0)
+        with igg.Grid(n, dims=(2, 2, 2), overlap=(2, 2, 2)) as g:
+            for tdt in (torch.float64, torch.float32):
+                P, Vx, Vy, Vz = g.acoustic_fields(tdt)
+                P.uniform_(-0.5, 0.5)
+                ms = _timed(lambda: g.acoustic_step(P, Vx, Vy, Vz, 1.0, 2.0, dt, *h), 2)
+                print(json.dumps({"profile": "acoustic", "dtype": str(tdt), "ms_per_step": round(ms, 4)}))
+                del P, Vx, Vy, Vz
     elif which == "stencil_groups":
         g = igg.Grid((256, 128, 128), dims=(2, 2, 2), overlap=(2, 2, 2), periods=(1, 0, 0))
         gen = torch.Generator(device="cuda").manual_seed(0)
@@ -762,7 +775,8 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--forms", action="store_true",
                     help="only measure the reshaped forms (one JSON line each)")
-    ap.add_argument("--profile", choices=["stencil", "stencil_signed", "stencil_groups", "adjoint", "gp"],
+    ap.add_argument("--profile",
+                    choices=["stencil", "stencil_signed", "stencil_groups", "adjoint", "gp", "acoustic"],
                     help="run a short fixed workload of one kernel for an ncu capture")
     ap.add_argument("--record-traffic", metavar="CSV",
                     help="write profiles/traffic.json from an ncu raw CSV export (no GPU)")
