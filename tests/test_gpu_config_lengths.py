@@ -132,7 +132,7 @@ def _adjoint_case(n):
 
 
 def _dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a)).cuda().reshape(1, *a.shape)
+    return torch.from_numpy(np.array(a)).cuda().reshape(1, *a.shape)
 
 
 def test_adjoint_32cube_nt200_checkpoint16_matches_oracle():
