@@ -309,10 +309,14 @@ __device__ __forceinline__ bool emu_spread_d(double tc, const unsigned long long
 // differences (as above, negated differences for negative values included),
 //   bits(T2) = bits(T) + Ci * sum_g w_g G_g
 // for as long as T2 stays in T's binade. Each G_g is split exactly into
-// G_g = Gh 2^23 + Gl with |Gl| <= 2^22 (Gh = (G_g + 2^22) >> 23; the fast
-// path requires |Gh| < 2^24, i.e. |G_g| < 2^47, so that both halves are
-// FP32 numbers; Gl is read off its bits as 2^23 + 2^22 + Gl, an FP32 number
-// with exponent 23, minus 1.5 2^23). With the weights as float pairs,
+// G_g = Gh 2^23 + Gl with -2^22 <= Gl < 2^22 (Gh = (G_g + 2^22) >> 23).
+// Both halves are read off bits as FP32 numbers with exponent 23 minus
+// 1.5 2^23: Gl from 2^23 + 2^22 + Gl (the low 23 bits of G_g + 2^22), Gh
+// from the integer sum Gh + 0x4B400000, the bits of 1.5 2^23 + Gh, which is
+// exact while -2^22 <= Gh < 2^22, i.e. -2^45 - 2^22 <= G_g < 2^45 - 2^22
+// (the fast path requires it; the subtraction of 1.5 2^23 is an FP32 add on
+// the FMA pipe instead of an integer-to-float conversion). With the weights
+// as float pairs,
 // S + C = sum_g w_g G_g is formed from error-free FMA products (2^23 wh) Gh,
 // the small terms (2^23 wl) Gh and wh Gl, and a two-sum of the leading
 // products, to about 2^-46 of sum_g |w_g G_g|. Then
@@ -326,7 +330,7 @@ __device__ __forceinline__ bool emu_spread_d(double tc, const unsigned long long
 // same per-point roundings, so both give the same bits.
 //
 // The fast path applies when the seven values share sign and exponent field
-// E in [180, 2008], every |Gh| < 2^24, Ci is positive with its exponent in
+// E in [180, 2008], every Gh in [-2^22, 2^22), Ci is positive with its exponent in
 // the FP32 range, |Ci_f C| < 2^22 and T2 (after the correction) keeps T's
 // sign and exponent. With |w| <= 2^40 (the host's condition for the emulated
 // cell) |S| < 2^90, so |S| u is a normal double for every such E. E, and the
@@ -366,13 +370,14 @@ __device__ __forceinline__ bool emu2_centre_ok(unsigned hc) {
 }
 
 // Integer part of the fast path for one point: the group sums of the bit-
-// pattern second differences, split into Gh (exact FP32 for |Gh| < 2^24)
-// and the bits gm of the FP32 number 1.5 2^23 + Gl. True when the seven
-// values share sign and exponent and every |Gh| < 2^24 (the centre's own
-// test is emu2_centre_ok). nb: x-, x+, y-, y+, z-, z+.
+// pattern second differences, split into the bits gh of the FP32 number
+// 1.5 2^23 + Gh and the bits gm of the FP32 number 1.5 2^23 + Gl. True when
+// the seven values share sign and exponent and every Gh lies in
+// [-2^22, 2^22), i.e. gh in [0x4B000000, 0x4B800000) (the centre's own test
+// is emu2_centre_ok). nb: x-, x+, y-, y+, z-, z+.
 template <int NG>
 __device__ __forceinline__ bool emu2_int(unsigned long long bc, const unsigned long long *nb,
-                                         int *gh, unsigned *gm) {
+                                         unsigned *gh, unsigned *gm) {
   const unsigned hc = (unsigned)(bc >> 32);
   unsigned o = 0u;
 #pragma unroll
@@ -392,11 +397,11 @@ __device__ __forceinline__ bool emu2_int(unsigned long long bc, const unsigned l
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     const unsigned lo = (unsigned)G[g];
-    gh[g] = (int)__funnelshift_r(lo, (unsigned)(G[g] >> 32), 23);
+    gh[g] = __funnelshift_r(lo, (unsigned)(G[g] >> 32), 23) + 0x4B400000u;
     gm[g] = (lo & 0x7FFFFFu) | 0x4B000000u;
-    r |= (unsigned)gh[g] + (1u << 24);
+    r |= gh[g] ^ 0x4B000000u;
   }
-  return o < (1u << 20) && r < (1u << 25);
+  return o < (1u << 20) && r < (1u << 23);
 }
 
 // S + C = sum_g w_g G_g from the FP32 halves (per lane: one point or two);
@@ -464,13 +469,12 @@ template <int NG>
 __device__ __forceinline__ double cell_emu_fast(double tc, const unsigned long long *nb,
                                                 double ci, const W<double> &w, bool &ok) {
   const unsigned long long bc = dbits(tc);
-  int gh[NG];
-  unsigned gm[NG];
+  unsigned gh[NG], gm[NG];
   ok = emu2_int<NG>(bc, nb, gh, gm) && emu2_centre_ok((unsigned)(bc >> 32));
   float fh[NG], fl[NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    fh[g] = __int2float_rn(gh[g]);
+    fh[g] = vadd(__uint_as_float(gh[g]), -kMagic);  // Gh, exact where ok
     fl[g] = __uint_as_float(gm[g]);
   }
   float S, C;

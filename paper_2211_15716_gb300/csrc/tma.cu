@@ -163,8 +163,7 @@ __device__ __forceinline__ void compute_vec_emu(
                                      dbits(yp.v[0]),  dbits(zm.v[0]), dbits(zp.v[0])};
   const unsigned long long nb1[6] = {b0,              dbits(right),   dbits(ym.v[1]),
                                      dbits(yp.v[1]),  dbits(zm.v[1]), dbits(zp.v[1])};
-  int gh0[NG], gh1[NG];
-  unsigned gm0[NG], gm1[NG];
+  unsigned gh0[NG], gh1[NG], gm0[NG], gm1[NG];
   // sign and exponent from the pair's first point (shared by every point of
   // the pair whose stencil passes)
   const unsigned hc = (unsigned)(b0 >> 32);
@@ -175,7 +174,9 @@ __device__ __forceinline__ void compute_vec_emu(
   float2 fh[NG], fl[NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    fh[g] = make_float2(__int2float_rn(gh0[g]), __int2float_rn(gh1[g]));
+    // Gh of both points: 1.5 2^23 + Gh minus 1.5 2^23 (exact where ok)
+    fh[g] = vadd(make_float2(__uint_as_float(gh0[g]), __uint_as_float(gh1[g])),
+                 vset(-kMagic, float2()));
     fl[g] = make_float2(__uint_as_float(gm0[g]), __uint_as_float(gm1[g]));
   }
   float2 S, C;

@@ -64,8 +64,12 @@ def fast_cell(tc, nb, ci, w, ng):
         h = (G + (1 << 22)) >> 23             # floor, i.e. rounded half up
         l = G - (h << 23)                     # in [-2^22, 2^22)
         assert -(1 << 22) <= l < (1 << 22)
-        ok = ok and abs(h) < (1 << 24)
-        gh.append(f32(h))
+        ok = ok and -(1 << 22) <= h < (1 << 22)
+        # the high half read off the bits of the FP32 number 1.5 2^23 + h
+        # (the integer sum h + 0x4B400000), minus 1.5 2^23
+        mh = u2f(h + 0x4B400000) if ok else f32(1.5 * 2 ** 23)
+        gh.append(f32(mh - f32(1.5 * 2 ** 23)))
+        assert not ok or float(gh[-1]) == h
         # the low half read off the bits of the FP32 number 1.5 2^23 + l
         m = u2f((((G + (1 << 22)) & 0x7FFFFF) | 0x4B000000))
         assert float(m) == 1.5 * 2 ** 23 + l
@@ -158,17 +162,48 @@ def test_fast_cell_within_bound_one_and_three_groups():
 
 def test_fast_cell_negative_values_and_rough_stencils():
     """Negative stencils (bit differences carry the opposite sign) and rough
-    ones (group sums near 2^46) stay within the bound; stencils leaving the
-    binade or with |G| >= 2^47 are refused."""
+    ones (group sums near 2^44) stay within the bound; stencils leaving the
+    binade or with a group sum outside [-2^45, 2^45) are refused."""
     rng = np.random.default_rng(3)
     worst, nok = check(2, (0.03, 0.12, 0.12), stencils(rng, 300, 1e-4, sign=-1.0))
     assert nok > 200 and worst <= 1.0
     worst, nok = check(2, (0.03, 0.12, 0.12), stencils(rng, 300, 2e-3, base=(2.3, 3.5)))
     assert worst <= 1.0 and nok > 0
-    # a stencil across 2.0 (two exponents) and one with |G| >= 2^47 are refused
+    # a stencil across 2.0 (two exponents) and one with |G| >= 2^47 are refused,
+    # and so is one with 2^45 <= G < 2^47 (outside the high half's bit-move
+    # range, G < 2^45 - 2^22)
     w = (0.03, 0.12, 0.12)
     assert not fast_cell(2.0000001, (1.9999999,) + (2.0000001,) * 5, 0.5, w, 2)[1]
     assert not fast_cell(3.9, (2.1, 2.2, 3.9, 3.9, 3.9, 3.9), 0.5, w, 2)[1]
+    t = 3.0
+    for k in (45, 46):  # x group sum G = 2^k units of ulp(3.0) = 2^-51
+        nb = (from_bits(bits(t) + (1 << (k - 1))), from_bits(bits(t) + (1 << (k - 1))), t, t, t, t)
+        G = bits(nb[0]) + bits(nb[1]) - 2 * bits(t)
+        assert G == 1 << k
+        assert not fast_cell(t, nb, 0.5, w, 2)[1]
+    d = (1 << 44) - (1 << 21) - 1  # G = 2^45 - 2^22 - 2: the largest even sum taken
+    nb = (from_bits(bits(t) + d), from_bits(bits(t) + d), t, t, t, t)
+    assert fast_cell(t, nb, 0.5, (1e-6, 1e-6, 1e-6), 1)[1]
+
+
+def test_high_half_bit_move_exact():
+    """The high half Gh = (G + 2^22) >> 23 read off the bits Gh + 0x4B400000
+    as an FP32 number minus 1.5 2^23 is exactly Gh for G in
+    [-2^45 - 2^22, 2^45 - 2^22) (Gh in [-2^22, 2^22)), and the range test on
+    those bits accepts exactly that interval."""
+    rng = np.random.default_rng(5)
+    lo, hi = -(2 ** 45) - (1 << 22), 2 ** 45 - (1 << 22)
+    Gs = [int(g) for g in rng.integers(lo, hi, 2000)]
+    Gs += [lo, hi - 1, 0, -1, (1 << 22) - 1, -(1 << 22)]
+    for G in Gs:
+        h = (G + (1 << 22)) >> 23
+        m = (h + 0x4B400000) & 0xFFFFFFFF
+        assert (m ^ 0x4B000000) < (1 << 23)
+        assert float(f32(u2f(m) - f32(1.5 * 2 ** 23))) == h
+    for G in (hi, 2 ** 45, 2 ** 46, lo - 1, -(2 ** 46)):
+        h = (G + (1 << 22)) >> 23
+        m = (h + 0x4B400000) & 0xFFFFFFFF
+        assert (m ^ 0x4B000000) >= (1 << 23)
 
 
 def test_split_halves_exact():
