@@ -33,7 +33,10 @@ struct AcNum<float> {
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
 };
 
-// blockIdx.z = subdomain * zchunks + z chunk
+// blockIdx.z = subdomain * zchunks + z chunk. The z march is software
+// pipelined: the loads of plane k + 1 are issued before the stores of plane
+// k, so that each thread keeps two planes of loads in flight (the launches
+// are bound by memory latency otherwise).
 template <class S>
 __global__ void __launch_bounds__(kAcX *kAcY)
     k_acoustic_v(int nx, int ny, int nz, int zchunks, const S *__restrict__ P, S *__restrict__ Vx,
@@ -45,27 +48,46 @@ __global__ void __launch_bounds__(kAcX *kAcY)
   const int k0 = (int)(blockIdx.z % zchunks) * kAcZ, k1 = min(k0 + kAcZ, nz);
   const S ax = (S)c.ax, ay = (S)c.ay, az = (S)c.az;
   const long long np = (long long)nx * ny * nz;
-  const S *Ps = P + sub * np;
-  S *Vxs = Vx + sub * (long long)(nx + 1) * ny * nz;
-  S *Vys = Vy + sub * (long long)nx * (ny + 1) * nz;
-  S *Vzs = Vz + sub * (long long)nx * ny * (nz + 1);
-  S pzm = k0 > 0 ? Ps[i + (long long)nx * (j + (long long)ny * (k0 - 1))] : S(0);
+  const long long sp = (long long)nx * ny, sx = (long long)(nx + 1) * ny,
+                  sy = (long long)nx * (ny + 1);
+  const S *Ps = P + sub * np + i + (long long)nx * j;
+  S *Vxs = Vx + sub * (long long)(nx + 1) * ny * nz + i + (long long)(nx + 1) * j;
+  S *Vys = Vy + sub * (long long)nx * (ny + 1) * nz + i + (long long)nx * j;
+  S *Vzs = Vz + sub * (long long)nx * ny * (nz + 1) + i + (long long)nx * j;
+  S pzm = k0 > 0 ? Ps[sp * (k0 - 1)] : S(0);
+  // plane k0
+  S pc = Ps[sp * k0];
+  S pxm = i > 0 ? Ps[sp * k0 - 1] : S(0);
+  S pym = j > 0 ? Ps[sp * k0 - nx] : S(0);
+  S vx = i > 0 ? Vxs[sx * k0] : S(0);
+  S vy = j > 0 ? Vys[sy * k0] : S(0);
+  S vz = k0 > 0 ? Vzs[sp * k0] : S(0);
   for (int k = k0; k < k1; ++k) {
-    const long long p = i + (long long)nx * (j + (long long)ny * k);
-    const S pc = Ps[p];
-    if (i > 0) {
-      S *v = Vxs + i + (long long)(nx + 1) * (j + (long long)ny * k);
-      *v = N::fma(-ax, N::sub(pc, Ps[p - 1]), *v);
+    // plane k + 1
+    const bool nxt = k + 1 < k1;
+    S pc1 = S(0), pxm1 = S(0), pym1 = S(0), vx1 = S(0), vy1 = S(0), vz1 = S(0);
+    if (nxt) {
+      pc1 = Ps[sp * (k + 1)];
+      if (i > 0) {
+        pxm1 = Ps[sp * (k + 1) - 1];
+        vx1 = Vxs[sx * (k + 1)];
+      }
+      if (j > 0) {
+        pym1 = Ps[sp * (k + 1) - nx];
+        vy1 = Vys[sy * (k + 1)];
+      }
+      vz1 = Vzs[sp * (k + 1)];
     }
-    if (j > 0) {
-      S *v = Vys + i + (long long)nx * (j + (long long)(ny + 1) * k);
-      *v = N::fma(-ay, N::sub(pc, Ps[p - nx]), *v);
-    }
-    if (k > 0) {
-      S *v = Vzs + p;
-      *v = N::fma(-az, N::sub(pc, pzm), *v);
-    }
+    if (i > 0) Vxs[sx * k] = N::fma(-ax, N::sub(pc, pxm), vx);
+    if (j > 0) Vys[sy * k] = N::fma(-ay, N::sub(pc, pym), vy);
+    if (k > 0) Vzs[sp * k] = N::fma(-az, N::sub(pc, pzm), vz);
     pzm = pc;
+    pc = pc1;
+    pxm = pxm1;
+    pym = pym1;
+    vx = vx1;
+    vy = vy1;
+    vz = vz1;
   }
 }
 
@@ -81,21 +103,39 @@ __global__ void __launch_bounds__(kAcX *kAcY)
   const int k0 = (int)(blockIdx.z % zchunks) * kAcZ, k1 = min(k0 + kAcZ, nz);
   const S bx = (S)c.bx, by = (S)c.by, bz = (S)c.bz;
   const long long np = (long long)nx * ny * nz;
-  S *Ps = P + sub * np;
-  const S *Vxs = Vx + sub * (long long)(nx + 1) * ny * nz;
-  const S *Vys = Vy + sub * (long long)nx * (ny + 1) * nz;
-  const S *Vzs = Vz + sub * (long long)nx * ny * (nz + 1);
-  S vzc = Vzs[i + (long long)nx * (j + (long long)ny * k0)];
+  const long long sp = (long long)nx * ny, sx = (long long)(nx + 1) * ny,
+                  sy = (long long)nx * (ny + 1);
+  S *Ps = P + sub * np + i + (long long)nx * j;
+  const S *Vxs = Vx + sub * (long long)(nx + 1) * ny * nz + i + (long long)(nx + 1) * j;
+  const S *Vys = Vy + sub * (long long)nx * (ny + 1) * nz + i + (long long)nx * j;
+  const S *Vzs = Vz + sub * (long long)nx * ny * (nz + 1) + i + (long long)nx * j;
+  S vzc = Vzs[sp * k0];
+  // plane k0
+  S pc = Ps[sp * k0], x0 = Vxs[sx * k0], x1 = Vxs[sx * k0 + 1], y0 = Vys[sy * k0],
+    y1 = Vys[sy * k0 + nx], vzp = Vzs[sp * (k0 + 1)];
   for (int k = k0; k < k1; ++k) {
-    const long long p = i + (long long)nx * (j + (long long)ny * k);
-    const long long px = i + (long long)(nx + 1) * (j + (long long)ny * k);
-    const long long py = i + (long long)nx * (j + (long long)(ny + 1) * k);
-    const S vzp = Vzs[p + (long long)nx * ny];
-    S div = N::mul(bx, N::sub(Vxs[px + 1], Vxs[px]));
-    div = N::fma(by, N::sub(Vys[py + nx], Vys[py]), div);
+    // plane k + 1
+    const bool nxt = k + 1 < k1;
+    S pc1 = S(0), x01 = S(0), x11 = S(0), y01 = S(0), y11 = S(0), vzp1 = S(0);
+    if (nxt) {
+      pc1 = Ps[sp * (k + 1)];
+      x01 = Vxs[sx * (k + 1)];
+      x11 = Vxs[sx * (k + 1) + 1];
+      y01 = Vys[sy * (k + 1)];
+      y11 = Vys[sy * (k + 1) + nx];
+      vzp1 = Vzs[sp * (k + 2)];
+    }
+    S div = N::mul(bx, N::sub(x1, x0));
+    div = N::fma(by, N::sub(y1, y0), div);
     div = N::fma(bz, N::sub(vzp, vzc), div);
-    Ps[p] = N::sub(Ps[p], div);
+    Ps[sp * k] = N::sub(pc, div);
     vzc = vzp;
+    pc = pc1;
+    x0 = x01;
+    x1 = x11;
+    y0 = y01;
+    y1 = y11;
+    vzp = vzp1;
   }
 }
 
