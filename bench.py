@@ -693,8 +693,9 @@ def _storage(x, tdt):
 def cfg1_other_dtype(args, grid, w, tdt, dd_dt, ref64, T0_64, Ci64, stream):
     """The cfg1 hidden step with FP32 or BF16 fields (the FP64 inputs T0_64,
     Ci64 rounded to the storage type on the device): ms per step for the
-    default form and the split, and the error after E2E_NT steps against the
-    FP64 GPU form (max |dT| / max |T|)."""
+    default form, the split and the halo update beside the inner tiles, and
+    the error after E2E_NT steps against the FP64 GPU form (max |dT| /
+    max |T|)."""
     dx, dy, dz, dt = dd_dt
 
     def fresh():
@@ -711,6 +712,10 @@ def cfg1_other_dtype(args, grid, w, tdt, dd_dt, ref64, T0_64, Ci64, stream):
     _, f = timed_steps(grid, w, f, 2, stream)  # tiles and graph made untimed
     ms_split, f = timed_steps(grid, w, f, steps, stream)
     grid.set_option(grid.OPT_FUSED_HALO, 1)
+    grid.set_option(grid.OPT_HIDE_HALO, 1)
+    _, f = timed_steps(grid, w, f, 2, stream)  # tiles and graph made untimed
+    ms_hide, f = timed_steps(grid, w, f, steps, stream)
+    grid.set_option(grid.OPT_HIDE_HALO, 0)
     s = T.element_size()
     bytes_step = 3 * grid.nsub * grid.nloc * s
     T, T2, Ci = fresh()
@@ -723,6 +728,7 @@ def cfg1_other_dtype(args, grid, w, tdt, dd_dt, ref64, T0_64, Ci64, stream):
             "frac_of_hbm": round(bytes_step / (ms_s * 1e-3) / 1e9 / peaks()[0], 3),
             "stencil_phase_ms": round(a, 4), "halo_ms": round(b, 4),
             "split_ms_per_step": round(ms_split / steps, 4),
+            "halo_beside_inner_tiles_ms_per_step": round(ms_hide / steps, 4),
             f"max_err_rel_vs_fp64_gpu_nt{E2E_NT}": err}
 
 
