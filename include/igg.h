@@ -337,7 +337,11 @@ int igg_run_host(igg_grid *grid, int nt, const int widths[3], void *T_host,
  *   P -= dt*K*((Vx[i+1]-Vx[i])/dx + (Vy[j+1]-Vy[j])/dy + (Vz[k+1]-Vz[k])/dz)
  *   on every cell, with the new velocities;
  * then, if with_halo, update_halo!(P, Vx, Vy, Vz) as igg_update_halo_fields
- * (overlaps o for P and o+1 for each face field in its own dimension). dtype
+ * (overlaps o for P and o+1 for each face field in its own dimension): its x
+ * exchange is done by the two launches themselves (each sent x plane stored
+ * a second time into the neighbour's halo plane, the neighbour's halo cells
+ * not stored by their own threads), then the y and z exchanges, with the
+ * same result as the plane copies in the order x, y, z. dtype
  * F64 or F32. Coefficients dt/(rho*dd) and dt*K/dd are formed in FP64; the
  * kernels use FMAs (results within rounding of the left-to-right formula).
  * ------------------------------------------------------------------------- */

@@ -37,6 +37,38 @@ struct AcNum<float> {
 // pipelined: the loads of plane k + 1 are issued before the stores of plane
 // k, so that each thread keeps two planes of loads in flight (the launches
 // are bound by memory latency otherwise).
+//
+// x sends (AcCoef::xsend): update_halo!'s x exchange done by the launches
+// themselves. A field of x size nf and x overlap of sends its plane nf - of
+// to the right neighbour's plane 0 and its plane of - 1 to the left
+// neighbour's plane nf - 1 (P, Vy, Vz: of = o; Vx: nf = nx + 1, of = o + 1);
+// the thread of a sent column stores every value of it as the launch leaves
+// it (computed, or a wall face it does not compute) a second time into the
+// neighbour, and the threads of receiving columns do not store there. The y
+// and z exchanges run after both launches.
+// The x sends of one thread: sm bit 0 / 1 its column is sent right / left;
+// dr, dl the neighbours' subdomain offsets (xr - sub, xl - sub). The copy of
+// the value at own index q of a field of np points per subdomain and x send
+// distance h = nf - of goes to q + dr np - h (right) and q + dl np + h (left).
+struct AcSend {
+  unsigned sm;
+  int dr, dl;
+};
+
+__device__ __forceinline__ AcSend ac_send(int i, int nf, int of, long long sub, int xl, int xr) {
+  AcSend a;
+  a.sm = (xr >= 0 && i == nf - of ? 1u : 0u) | (xl >= 0 && i == of - 1 ? 2u : 0u);
+  a.dr = xr - (int)sub;
+  a.dl = xl - (int)sub;
+  return a;
+}
+
+template <class S>
+__device__ __forceinline__ void ac_put(S *p, S v, const AcSend &a, long long np, int h) {
+  if (a.sm & 1u) p[(long long)a.dr * np - h] = v;
+  if (a.sm & 2u) p[(long long)a.dl * np + h] = v;
+}
+
 template <class S>
 __global__ void __launch_bounds__(kAcX *kAcY)
     k_acoustic_v(int nx, int ny, int nz, int zchunks, const S *__restrict__ P, S *__restrict__ Vx,
@@ -50,18 +82,32 @@ __global__ void __launch_bounds__(kAcX *kAcY)
   const long long np = (long long)nx * ny * nz;
   const long long sp = (long long)nx * ny, sx = (long long)(nx + 1) * ny,
                   sy = (long long)nx * (ny + 1);
+  const long long npx = sx * nz, npy = sy * nz, npz = sp * (nz + 1);
   const S *Ps = P + sub * np + i + (long long)nx * j;
-  S *Vxs = Vx + sub * (long long)(nx + 1) * ny * nz + i + (long long)(nx + 1) * j;
-  S *Vys = Vy + sub * (long long)nx * (ny + 1) * nz + i + (long long)nx * j;
-  S *Vzs = Vz + sub * (long long)nx * ny * (nz + 1) + i + (long long)nx * j;
+  S *Vxs = Vx + sub * npx + i + (long long)(nx + 1) * j;
+  S *Vys = Vy + sub * npy + i + (long long)nx * j;
+  S *Vzs = Vz + sub * npz + i + (long long)nx * j;
+  // x sends (Vx: nf = nx + 1, of = o + 1; Vy, Vz: nf = nx, of = o; the
+  // send distance nf - of is nx - o for all three) and the receiving columns
+  // (halo cells: Vy and Vz not stored)
+  AcSend ex{0u, 0, 0}, ev = ex;
+  bool keep = true;
+  const int h = nx - c.ox;
+  if (c.xsend) {
+    const int xl = c.nbr[6 * sub], xr = c.nbr[6 * sub + 1];
+    ex = ac_send(i, nx + 1, c.ox + 1, sub, xl, xr);
+    ev = ac_send(i, nx, c.ox, sub, xl, xr);
+    keep = !((i == 0 && xl >= 0) || (i == nx - 1 && xr >= 0));
+  }
+  const bool sv = ev.sm != 0u;  // sends Vy and Vz (wall faces too)
   S pzm = k0 > 0 ? Ps[sp * (k0 - 1)] : S(0);
   // plane k0
   S pc = Ps[sp * k0];
   S pxm = i > 0 ? Ps[sp * k0 - 1] : S(0);
   S pym = j > 0 ? Ps[sp * k0 - nx] : S(0);
   S vx = i > 0 ? Vxs[sx * k0] : S(0);
-  S vy = j > 0 ? Vys[sy * k0] : S(0);
-  S vz = k0 > 0 ? Vzs[sp * k0] : S(0);
+  S vy = (j > 0 || sv) ? Vys[sy * k0] : S(0);
+  S vz = (k0 > 0 || sv) ? Vzs[sp * k0] : S(0);
   for (int k = k0; k < k1; ++k) {
     // plane k + 1
     const bool nxt = k + 1 < k1;
@@ -72,15 +118,30 @@ __global__ void __launch_bounds__(kAcX *kAcY)
         pxm1 = Ps[sp * (k + 1) - 1];
         vx1 = Vxs[sx * (k + 1)];
       }
-      if (j > 0) {
-        pym1 = Ps[sp * (k + 1) - nx];
-        vy1 = Vys[sy * (k + 1)];
-      }
+      if (j > 0) pym1 = Ps[sp * (k + 1) - nx];
+      if (j > 0 || sv) vy1 = Vys[sy * (k + 1)];
       vz1 = Vzs[sp * (k + 1)];
     }
-    if (i > 0) Vxs[sx * k] = N::fma(-ax, N::sub(pc, pxm), vx);
-    if (j > 0) Vys[sy * k] = N::fma(-ay, N::sub(pc, pym), vy);
-    if (k > 0) Vzs[sp * k] = N::fma(-az, N::sub(pc, pzm), vz);
+    if (i > 0) {
+      vx = N::fma(-ax, N::sub(pc, pxm), vx);
+      Vxs[sx * k] = vx;
+    }
+    if (j > 0) {
+      vy = N::fma(-ay, N::sub(pc, pym), vy);
+      if (keep) Vys[sy * k] = vy;
+    }
+    if (k > 0) {
+      vz = N::fma(-az, N::sub(pc, pzm), vz);
+      if (keep) Vzs[sp * k] = vz;
+    }
+    if (ex.sm) ac_put(Vxs + sx * k, vx, ex, npx, h);
+    if (sv) {
+      ac_put(Vys + sy * k, vy, ev, npy, h);
+      ac_put(Vzs + sp * k, vz, ev, npz, h);
+      // the last face row of Vy (y = ny, a wall or halo face no thread
+      // computes)
+      if (j == ny - 1) ac_put(Vys + sy * k + nx, Vys[sy * k + nx], ev, npy, h);
+    }
     pzm = pc;
     pc = pc1;
     pxm = pxm1;
@@ -89,6 +150,8 @@ __global__ void __launch_bounds__(kAcX *kAcY)
     vy = vy1;
     vz = vz1;
   }
+  // the last plane of Vz (z = nz, a wall or halo face no thread computes)
+  if (sv && k1 == nz) ac_put(Vzs + sp * nz, Vzs[sp * nz], ev, npz, h);
 }
 
 template <class S>
@@ -109,6 +172,14 @@ __global__ void __launch_bounds__(kAcX *kAcY)
   const S *Vxs = Vx + sub * (long long)(nx + 1) * ny * nz + i + (long long)(nx + 1) * j;
   const S *Vys = Vy + sub * (long long)nx * (ny + 1) * nz + i + (long long)nx * j;
   const S *Vzs = Vz + sub * (long long)nx * ny * (nz + 1) + i + (long long)nx * j;
+  AcSend ep{0u, 0, 0};
+  bool keep = true;
+  const int h = nx - c.ox;
+  if (c.xsend) {
+    const int xl = c.nbr[6 * sub], xr = c.nbr[6 * sub + 1];
+    ep = ac_send(i, nx, c.ox, sub, xl, xr);
+    keep = !((i == 0 && xl >= 0) || (i == nx - 1 && xr >= 0));
+  }
   S vzc = Vzs[sp * k0];
   // plane k0
   S pc = Ps[sp * k0], x0 = Vxs[sx * k0], x1 = Vxs[sx * k0 + 1], y0 = Vys[sy * k0],
@@ -128,7 +199,9 @@ __global__ void __launch_bounds__(kAcX *kAcY)
     S div = N::mul(bx, N::sub(x1, x0));
     div = N::fma(by, N::sub(y1, y0), div);
     div = N::fma(bz, N::sub(vzp, vzc), div);
-    Ps[sp * k] = N::sub(pc, div);
+    const S pn = N::sub(pc, div);
+    if (keep) Ps[sp * k] = pn;
+    if (ep.sm) ac_put(Ps + sp * k, pn, ep, np, h);
     vzc = vzp;
     pc = pc1;
     x0 = x01;

@@ -193,6 +193,10 @@ cudaError_t launch_stencil_tma(igg_dtype dt, int variant, const TmaTile *tiles, 
 // FP64; one step (velocities, then pressure) on every subdomain.
 struct AcCoef {
   double ax, ay, az, bx, by, bz;
+  // x exchange by the launches (acoustic.cu): the grid's neighbour table
+  // (6 per subdomain: left/right per dimension, -1 none) and x overlap
+  const int *nbr = nullptr;
+  int ox = 2, xsend = 0;
 };
 cudaError_t launch_acoustic(igg_dtype dt, int nsub, int nx, int ny, int nz, void *P, void *Vx,
                             void *Vy, void *Vz, const AcCoef &c, cudaStream_t s);

@@ -741,12 +741,13 @@ int halo_tables(igg_grid *g, const int nf[3], PlaneCopy *const **copies, const i
 // Halo update of several fields (field i of local size nf[3i..3i+2]): per
 // dimension x, y, z one launch for all fields (chunks of kMaxHaloJobs).
 int enqueue_halo_fields(igg_grid *g, void *const fields[], const int *nf, int nfields, size_t es,
-                        cudaStream_t s) {
+                        cudaStream_t s, unsigned dims = 7u) {
   std::vector<PlaneCopy *const *> tc(nfields);
   std::vector<const int *> tn(nfields);
   for (int i = 0; i < nfields; ++i)
     if (int rc = halo_tables(g, nf + 3 * i, &tc[i], &tn[i])) return rc;
   for (int d = 0; d < 3; ++d) {
+    if (!(dims >> d & 1u)) continue;
     HaloJobs jobs;
     int nj = 0;
     for (int i = 0; i <= nfields; ++i) {
@@ -1257,6 +1258,11 @@ int igg_acoustic_step(igg_grid *g, void *P, void *Vx, void *Vy, void *Vz, igg_dt
   c.bx = dtime * K / dx;
   c.by = dtime * K / dy;
   c.bz = dtime * K / dz;
+  // with the halo update, the two launches do its x exchange themselves
+  // (the x-face planes, which are strided), the y and z exchanges follow
+  c.nbr = g->nbr;
+  c.ox = g->overlap[0];
+  c.xsend = with_halo ? 1 : 0;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_acoustic(dt, g->nsub, g->n[0], g->n[1], g->n[2], P, Vx, Vy, Vz, c, s);
   if (e != cudaSuccess) return cuda_error(e, "acoustic launch");
@@ -1264,7 +1270,7 @@ int igg_acoustic_step(igg_grid *g, void *P, void *Vx, void *Vy, void *Vz, igg_dt
   void *const fields[4] = {P, Vx, Vy, Vz};
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   const int sizes[12] = {nx, ny, nz, nx + 1, ny, nz, nx, ny + 1, nz, nx, ny, nz + 1};
-  return enqueue_halo_fields(g, fields, sizes, 4, dtype_size(dt), s);
+  return enqueue_halo_fields(g, fields, sizes, 4, dtype_size(dt), s, 6u);
 }
 
 int igg_step(igg_grid *g, void *T2, const void *T, const void *Ci, igg_dtype dt, double lam,
