@@ -343,7 +343,8 @@ int igg_run_host(igg_grid *grid, int nt, const int widths[3], void *T_host,
  * not stored by their own threads), then the y and z exchanges, with the
  * same result as the plane copies in the order x, y, z. dtype
  * F64 or F32. Coefficients dt/(rho*dd) and dt*K/dd are formed in FP64; the
- * kernels use FMAs (results within rounding of the left-to-right formula).
+ * kernels use one FMA per term (P - bx dVx - by dVy - bz dVz, results within
+ * rounding of the left-to-right formula).
  * ------------------------------------------------------------------------- */
 int igg_acoustic_step(igg_grid *grid, void *P, void *Vx, void *Vy, void *Vz,
                       igg_dtype dtype, double rho, double K, double dt, double dx,

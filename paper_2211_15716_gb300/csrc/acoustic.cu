@@ -196,10 +196,11 @@ __global__ void __launch_bounds__(kAcX *kAcY)
       y11 = Vys[sy * (k + 1) + nx];
       vzp1 = Vzs[sp * (k + 2)];
     }
-    S div = N::mul(bx, N::sub(x1, x0));
-    div = N::fma(by, N::sub(y1, y0), div);
-    div = N::fma(bz, N::sub(vzp, vzc), div);
-    const S pn = N::sub(pc, div);
+    // P - bx dVx - by dVy - bz dVz, one FMA per term (6 FP64 instructions
+    // per cell for FP64 fields, whose launches the FP64 pipe bounds)
+    S pn = N::fma(-bx, N::sub(x1, x0), pc);
+    pn = N::fma(-by, N::sub(y1, y0), pn);
+    pn = N::fma(-bz, N::sub(vzp, vzc), pn);
     if (keep) Ps[sp * k] = pn;
     if (ep.sm) ac_put(Ps + sp * k, pn, ep, np, h);
     vzc = vzp;
