@@ -370,7 +370,10 @@ int igg_acoustic_step(igg_grid *grid, void *P, void *Vx, void *Vy, void *Vz,
  * (|u|, |v|, |V| outside [2^-40, 2^41), |q| outside [2^-36, 2^37), zero
  * allowed) use the FP64 formula. 3-D grids whose rows are a multiple of 16
  * bytes (and 16-byte aligned fields) run a TMA-pipelined kernel unless
- * IGG_OPT_TMA is 0; other grids a column kernel with the same bits.
+ * IGG_OPT_TMA is 0; other grids a column kernel with the same bits. With the
+ * halo update, the TMA kernel does its x exchange itself (the points of the
+ * sent x planes stored a second time into the neighbours' halo columns) and
+ * the halo launch copies the face rows only: the same halo values.
  * ------------------------------------------------------------------------- */
 int igg_gp_step(igg_grid *grid, void *u, void *v, const void *V, igg_dtype dtype,
                 double g, double dt, double dx, double dy, double dz, int with_halo,

@@ -366,6 +366,24 @@ __global__ void __launch_bounds__(32 * GpShape<S>::WARPS, 1)
     bool xyin[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) xyin[i] = yin && xs + i >= 1 && xs + i <= nx - 2;
+    // the halo update's x exchange (GpCoef::xsend): this lane's points of the
+    // sent planes nx - o (bits 0..V-1: to the right neighbour's column 0) and
+    // o - 1 (bits 8..8+V-1: to the left neighbour's column nx - 1), and the
+    // element offsets of their copies
+    unsigned sendm = 0u;
+    long long dr = 0, dl = 0;
+    if (c.xsend) {
+      const int sub = zoff / nz, xl = c.nbr[6 * sub], xr = c.nbr[6 * sub + 1];
+      const long long nloc = sz * nz, h = nx - c.ox;
+      dr = (long long)(xr - sub) * nloc - h;
+      dl = (long long)(xl - sub) * nloc + h;
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        if (!xyin[i]) continue;
+        if (xr >= 0 && xs + i == nx - c.ox) sendm |= 1u << i;
+        if (xl >= 0 && xs + i == c.ox - 1) sendm |= 1u << (8 + i);
+      }
+    }
     int rb[Sh::RPT];
 #pragma unroll
     for (int j = 0; j < Sh::RPT; ++j) {
@@ -499,6 +517,15 @@ __global__ void __launch_bounds__(32 * GpShape<S>::WARPS, 1)
         for (int i = 0; i < V; ++i)
           if (xyin[i]) out[p0 + i] = res[i];
       }
+      if (sendm) {
+        // the sent points stored again into the neighbours' halo columns
+        // (the halo launch then copies the face rows only)
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          if (sendm >> i & 1u) out[p0 + i + dr] = res[i];
+          if (sendm >> (8 + i) & 1u) out[p0 + i + dl] = res[i];
+        }
+      }
       kc = k;
       ++k;
       plm = pln;
@@ -589,20 +616,27 @@ bool tma_fits(int nx, int ny, int nz, const void *u, const void *v, const void *
 
 cudaError_t launch_gp_half(igg_dtype dt, int which, int nsub, int nx, int ny, int nz, void *u,
                            void *v, const void *V, const GpCoef &c, bool tma, unsigned *dev_err,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool *xsent) {
+  *xsent = false;
+  GpCoef cw = c;  // the tiled kernel does no x sends
+  cw.xsend = 0;
   switch (dt) {
     case IGG_F64:
-      if (tma && tma_fits<double>(nx, ny, nz, u, v, V))
+      if (tma && tma_fits<double>(nx, ny, nz, u, v, V)) {
+        *xsent = c.xsend != 0;
         return which == 0 ? launch_tma<double, 0>(nsub, nx, ny, nz, u, v, V, c, dev_err, s)
                           : launch_tma<double, 1>(nsub, nx, ny, nz, u, v, V, c, dev_err, s);
-      return which == 0 ? launch_w<double, 0>(nsub, nx, ny, nz, u, v, V, c, s)
-                        : launch_w<double, 1>(nsub, nx, ny, nz, u, v, V, c, s);
+      }
+      return which == 0 ? launch_w<double, 0>(nsub, nx, ny, nz, u, v, V, cw, s)
+                        : launch_w<double, 1>(nsub, nx, ny, nz, u, v, V, cw, s);
     case IGG_F32:
-      if (tma && tma_fits<float>(nx, ny, nz, u, v, V))
+      if (tma && tma_fits<float>(nx, ny, nz, u, v, V)) {
+        *xsent = c.xsend != 0;
         return which == 0 ? launch_tma<float, 0>(nsub, nx, ny, nz, u, v, V, c, dev_err, s)
                           : launch_tma<float, 1>(nsub, nx, ny, nz, u, v, V, c, dev_err, s);
-      return which == 0 ? launch_w<float, 0>(nsub, nx, ny, nz, u, v, V, c, s)
-                        : launch_w<float, 1>(nsub, nx, ny, nz, u, v, V, c, s);
+      }
+      return which == 0 ? launch_w<float, 0>(nsub, nx, ny, nz, u, v, V, cw, s)
+                        : launch_w<float, 1>(nsub, nx, ny, nz, u, v, V, cw, s);
     default:
       return cudaErrorInvalidValue;
   }

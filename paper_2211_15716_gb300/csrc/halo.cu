@@ -80,6 +80,9 @@ __global__ void __launch_bounds__(256) k_halo_jobs(const HaloJobs jobs) {
 // (2 (nz - 2)), and the x face columns with y, z inner (2 (nz - 2), y along
 // the row). A face row's z and y steps are the same for every x: it is copied
 // as a whole from its source row, then its two end cells take their x step.
+// With HaloGather::skipx the x-face columns are left out (the launch before
+// filled them); the rows do not read them (their end cells' x step reads
+// the source point itself).
 __device__ __forceinline__ void gather_step(const HaloGather &h, int d, int &s, int &c,
                                             bool &moved) {
   const int side = c == 0 ? 0 : (c == h.n[d] - 1 ? 1 : -1);
@@ -94,7 +97,7 @@ __device__ __forceinline__ void gather_step(const HaloGather &h, int d, int &s, 
 template <class E, bool VEC>
 __global__ void __launch_bounds__(256) k_halo_gather(E *__restrict__ f, const HaloGather h) {
   const int nx = h.n[0], ny = h.n[1], nz = h.n[2];
-  const int rows = 2 * ny + 4 * (nz - 2);
+  const int rows = 2 * ny + (h.skipx ? 2 : 4) * (nz - 2);
   const int s0 = (int)(blockIdx.x / rows);
   int row = (int)(blockIdx.x % rows);
   const long long sy = nx, sz = (long long)nx * ny;
@@ -237,7 +240,7 @@ cudaError_t launch_halo_adjoint(size_t elem_size, const PlaneCopy *copies, int n
 cudaError_t launch_halo_gather(size_t elem_size, void *field, const HaloGather &h,
                                cudaStream_t s) {
   if (h.n[0] < 3 || h.n[1] < 3 || h.n[2] < 3) return cudaErrorInvalidValue;
-  const long long blocks = (long long)h.nsub * (2 * h.n[1] + 4 * (h.n[2] - 2));
+  const long long blocks = (long long)h.nsub * (2 * h.n[1] + (h.skipx ? 2 : 4) * (h.n[2] - 2));
   if (blocks <= 0) return cudaSuccess;
   if (blocks >= (1ll << 31)) return cudaErrorInvalidValue;
   const bool vec = ((long long)h.n[0] * (long long)elem_size) % 16 == 0 &&

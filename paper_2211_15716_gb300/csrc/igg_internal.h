@@ -205,11 +205,17 @@ cudaError_t launch_acoustic(igg_dtype dt, int nsub, int nx, int ny, int nz, void
 // dimension), kc = -2 (kx + ky + kz), dt and g, formed on the host in FP64.
 struct GpCoef {
   double kx, ky, kz, kc, dt, g;
+  // x exchange by the TMA half-step launch (gp.cu): the grid's neighbour
+  // table (6 per subdomain, -1 none) and x overlap
+  const int *nbr = nullptr;
+  int ox = 2, xsend = 0;
 };
-// With `tma`, 3-D grids whose rows allow it take the TMA-pipelined kernel.
+// With `tma`, 3-D grids whose rows allow it take the TMA-pipelined kernel;
+// *xsent = true when that kernel ran with c.xsend (it stored the x planes
+// that the halo update sends into the neighbours' halo columns).
 cudaError_t launch_gp_half(igg_dtype dt, int which, int nsub, int nx, int ny, int nz, void *u,
                            void *v, const void *V, const GpCoef &c, bool tma, unsigned *dev_err,
-                           cudaStream_t s);
+                           cudaStream_t s, bool *xsent);
 
 // One dimension of the halo update for one field: ncopies plane copies,
 // each plane having na x nb points with element strides sa, sb.
@@ -269,6 +275,9 @@ struct HaloGather {
   int n[3] = {0, 0, 0}, o[3] = {0, 0, 0};
   long long nloc = 0;
   int nsub = 0;
+  // 1: the x-face columns with y, z inner are already filled (the launch
+  // before stored its sent x planes into them); only the face rows are copied
+  int skipx = 0;
 };
 cudaError_t launch_halo_gather(size_t elem_size, void *field, const HaloGather &h,
                                cudaStream_t s);

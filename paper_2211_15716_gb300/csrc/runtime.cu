@@ -700,9 +700,11 @@ cudaError_t enqueue_halo_adjoint(igg_grid *g, void *field, size_t es, cudaStream
 
 // The halo update of a field of the grid's own size: on 3-D grids one
 // gather launch, else the plane copies dimension by dimension.
-cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s) {
+cudaError_t enqueue_halo(igg_grid *g, void *field, size_t es, cudaStream_t s,
+                         bool skipx = false) {
   if (g->n[0] > 1 && g->n[1] > 1 && g->n[2] > 1) {
     HaloGather h;
+    h.skipx = skipx ? 1 : 0;
     h.nbr = g->nbr;
     for (int d = 0; d < 3; ++d) {
       h.n[d] = g->n[d];
@@ -1226,13 +1228,20 @@ int igg_gp_step(igg_grid *g, void *u, void *v, const void *V, igg_dtype dt, doub
   c.kc = -2.0 * (c.kx + c.ky + c.kz);
   c.dt = dtime;
   c.g = gnl;
+  // with the halo update on a 3-D grid, the TMA half-step launch stores its
+  // sent x planes into the neighbours' halo columns itself, and the halo
+  // launch copies the face rows only
+  c.nbr = g->nbr;
+  c.ox = g->overlap[0];
+  c.xsend = with_halo && any_halo(g) && !low_dim(g) ? 1 : 0;
   cudaStream_t s = (cudaStream_t)stream;
   for (int which = 0; which < 2; ++which) {
+    bool xsent = false;
     cudaError_t e = launch_gp_half(dt, which, g->nsub, g->n[0], g->n[1], g->n[2], u, v, V, c,
-                                   g->tma_enabled && !low_dim(g), g->dev_err, s);
+                                   g->tma_enabled && !low_dim(g), g->dev_err, s, &xsent);
     if (e != cudaSuccess) return cuda_error(e, "Gross-Pitaevskii launch");
     if (with_halo && any_halo(g)) {
-      e = enqueue_halo(g, which == 0 ? u : v, dtype_size(dt), s);
+      e = enqueue_halo(g, which == 0 ? u : v, dtype_size(dt), s, xsent);
       if (e != cudaSuccess) return cuda_error(e, "halo launch");
     }
   }
