@@ -66,6 +66,35 @@ def test_gp_matches_oracle(n, dims, periods, dtype):
         assert np.abs(a - r).max() <= tol * np.abs(r).max()
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n,dims,periods", [
+    ((40, 12, 10), (2, 1, 2), (1, 0, 0)),   # a periodic ring of two in x
+    ((24, 12, 10), (1, 2, 1), (1, 0, 0)),   # its own x neighbour
+    ((32, 10, 12), (3, 1, 1), (0, 0, 1)),   # a middle subdomain with both x neighbours
+])
+def test_gp_overlap3_x_matches_oracle(n, dims, periods, dtype):
+    """Overlap 3 in x on the TMA kernel, whose half steps store the x
+    exchange's planes (n - 3 and 2) into the neighbours' halo columns
+    themselves: halo cells included, the run matches the oracle's decomposed
+    run."""
+    o = (3, 2, 2)
+    g, nt = 0.9, 6
+    dd = (0.1, 0.12, 0.09)
+    dt = 0.3 / (2 * sum(1 / h ** 2 for h in dd) + 1.0 + 2 * g)
+    U, Vv, Pot = inputs(n, dims, periods, o, 9)
+    ru, rv = U.copy(), Vv.copy()
+    oracle.gp_run_decomposed(ru, rv, Pot, nt, g, dt, *dd, dims, periods, o)
+    with igg.Grid(n, dims=dims, overlap=o, periods=periods) as gr:
+        u, v, P = (torch.from_numpy(a).to(dtype).cuda() for a in (U, Vv, Pot))
+        for _ in range(nt):
+            gr.gp_step(u, v, P, g, dt, *dd)
+        torch.cuda.synchronize()
+        gu, gv = u.double().cpu().numpy(), v.double().cpu().numpy()
+    tol = 1e-12 if dtype == torch.float64 else 4e-6 * nt
+    for a, r in ((gu, ru), (gv, rv)):
+        assert np.abs(a - r).max() <= tol * np.abs(r).max()
+
+
 def test_gp_linear_invariant_gpu():
     """g = 0, zero boundary values: ||u^n||^2 + <v^{n+1/2}, v^{n-1/2}> stays
     the same after every step (u^n, v^{n+1/2} after step n)."""
